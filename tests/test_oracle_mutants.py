@@ -1,0 +1,80 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case patches one oracle routine with a plausible error (a dropped
+factor, a wrong sign, a swapped operand) on the CPU and checks that at least
+one pin in ``test_oracle_pins`` then fails.  This shows that the pins constrain
+every part of the oracle rather than agreeing with it by construction.
+"""
+import numpy as np
+import pytest
+
+import oracle.lsplit as L
+from tests import test_oracle_pins as pins
+
+PINS = [
+    pins.test_dft_matrix_against_numpy_fft_and_unitarity,
+    pins.test_grid_potential_closed_form_cos,
+    pins.test_constant_potential_is_global_phase,
+    pins.test_commensurate_fiber_sum_matches_supercell,
+    pins.test_single_layer_reduces_to_bloch_split_step,
+    pins.test_observables_against_dense_quadratic_forms,
+    pins.test_gaussian_packet_reduces_to_paper_initial_state,
+    pins.test_2d_order_against_dense_exponential,
+    pins.test_2d_free_particle_and_mass,
+    pins.test_stochastic_sampled_factor_matches_dense,
+    lambda: pins.test_free_particle_exact_phase("strang"),
+    lambda: pins.test_convergence_order_against_dense_exponential("strang", 2),
+    lambda: pins.test_convergence_order_against_dense_exponential("lie", 1),
+    pins.test_adjoint_matches_central_differences,
+    pins.test_one_step_equals_dense_factor_product,
+]
+
+_orig_dft = L.dft_matrix
+_orig_kin = L.kinetic_energy_diag
+_orig_axis = L._axis_dft
+_orig_grid = L.grid_potential
+_orig_factors = L.scheme_factors
+_orig_P = L.apply_P
+
+
+def _strang_wrong(scheme, tau):
+    f = _orig_factors(scheme, tau)
+    if scheme.startswith("strang") and not scheme.startswith("strang_kp"):
+        f = [(x[0], x[1], x[2] / 2) if x[0] == "P" and x[1] == 2 else x for x in f]
+    return f
+
+
+def _lie_wrong_order(scheme, tau):
+    f = _orig_factors(scheme, tau)
+    if scheme.startswith("lie"):
+        f = [f[1], f[0], f[2]]
+    return f
+
+
+MUTANTS = {
+    "kinetic_missing_half": ("kinetic_energy_diag", lambda p: 2.0 * _orig_kin(p)),
+    "kinetic_wrong_sign": ("kinetic_energy_diag", lambda p: -_orig_kin(p)),
+    "dft_conjugated": ("dft_matrix", lambda q: _orig_dft(q).conj()),
+    "dft_index_off_by_one": ("dft_matrix", lambda q: np.roll(_orig_dft(q), 1, axis=0)),
+    "forward_missing_1_over_q": ("_axis_dft",
+                                 lambda x, q, inverse: _orig_axis(x, q, inverse) * (1.0 if inverse else float(np.prod(q)))),
+    "potential_sign": ("grid_potential", lambda h, c, q: -_orig_grid(h, c, q)),
+    "potential_h_negated": ("grid_potential", lambda h, c, q: _orig_grid(-np.asarray(h), c, q)),
+    "layers_swapped": ("apply_P", lambda p, phi, layer, s, slices=None, _v=None:
+                       _orig_P(p, phi, 3 - layer, s, slices, None)),
+    "strang_wrong_duration": ("scheme_factors", _strang_wrong),
+    "lie_wrong_order": ("scheme_factors", _lie_wrong_order),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, monkeypatch):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(L, attr, fn)
+    caught = 0
+    for pin in PINS:
+        try:
+            pin()
+        except (AssertionError, ValueError, IndexError):
+            caught += 1
+    assert caught > 0, f"no pin caught mutant {name}"

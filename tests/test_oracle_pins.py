@@ -1,0 +1,478 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's own formulas: each compares it with an
+independent construction (dense Hamiltonians built from Fourier coefficients,
+closed forms, a supercell solve, a textbook split-step per Bloch slice,
+library FFTs, high-precision arithmetic, published generator values).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+def small_1d(n1=4, n2=3, a1=3.0, a2=2.0, L1=5.0, ratio=W.GOLDEN):
+    return W.bilayer_1d(n1, n2, a1, a2, L1=L1, L2=L1 * ratio, ecut=1e9)
+
+
+def circulant_from_coeffs(h, c, q):
+    """C[m, m'] = sum_{h = m - m' mod q} vhat_h, built straight from the Fourier
+    coefficients (the Galerkin V^j of Eq. (3.6) with periodic wrap)."""
+    C = np.zeros((q, q), dtype=np.complex128)
+    for hh, cc in zip(np.asarray(h).reshape(-1), c):
+        for m in range(q):
+            C[m, (m - hh) % q] += cc
+    return C
+
+
+def dense_H_1d(prob):
+    """H = D + I (x) C1 + C2 (x) I (Eq. (3.4)-(3.7)) with [n][m] ordering."""
+    m = np.arange(prob.q1[0]) + prob.lo1[0]
+    n = np.arange(prob.q2[0]) + prob.lo2[0]
+    b1, b2 = prob.B1[0, 0], prob.B2[0, 0]
+    k = b1 * m[None, :] + b2 * n[:, None]
+    D = np.diag(0.5 * (k ** 2).reshape(-1))
+    C1 = circulant_from_coeffs(prob.v1_h, prob.v1_c, prob.q1[0])
+    C2 = circulant_from_coeffs(prob.v2_h, prob.v2_c, prob.q2[0])
+    return D + np.kron(np.eye(prob.q2[0]), C1) + np.kron(C2, np.eye(prob.q1[0]))
+
+
+def expm_herm(H, t):
+    w, V = np.linalg.eigh(H)
+    return (V * np.exp(-1j * t * w)) @ V.conj().T
+
+
+def rand_state(prob, seed=0):
+    return W.random_state((prob.M2, prob.M1), seed)
+
+
+# ---------------------------------------------------------------- transforms
+def test_dft_matrix_against_numpy_fft_and_unitarity():
+    for q in (1, 2, 7, 64, 65, 129):
+        Wm = O.dft_matrix(q)
+        x = np.random.default_rng(q).standard_normal(q) + 0j
+        # W maps coefficients to grid values: q * ifft (positive exponent).
+        np.testing.assert_allclose(x @ Wm, q * np.fft.ifft(x), atol=1e-11 * q)
+        # Appendix B normalisation: forward = conj(W)/q inverts it exactly.
+        np.testing.assert_allclose(Wm.conj() @ Wm / q, np.eye(q), atol=1e-12)
+
+
+def test_grid_potential_closed_form_cos():
+    h, c = W._cos_coeffs(1.7)
+    q = 65
+    v = O.grid_potential(h, c, (q,))
+    np.testing.assert_allclose(v, 1.7 * np.cos(2 * np.pi * np.arange(q) / q), atol=1e-14)
+
+
+def test_2d_separable_transform_equals_kronecker_matrix():
+    q = (4, 3)
+    x = np.random.default_rng(1).standard_normal((5, 12)) + 1j
+    K2 = np.kron(O.dft_matrix(q[1]), O.dft_matrix(q[0]))
+    np.testing.assert_allclose(O.lsplit._axis_dft(x, q, True), x @ K2, atol=1e-12)
+    np.testing.assert_allclose(O.lsplit._axis_dft(x @ K2, q, False), x, atol=1e-12)
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("scheme", O.SCHEMES)
+def test_free_particle_exact_phase(scheme):
+    """V = 0: every scheme is exact, phi(T) = exp(-i T |k|^2 / 2) phi0."""
+    p = W.bilayer_1d(6, 5, 0.0, 0.0, ecut=1e9)
+    phi0 = rand_state(p, 3)
+    tau, n = 0.013, 7
+    out = O.step(p, phi0, tau, scheme, n, seed=5)
+    m = np.arange(-6, 7)
+    nn = np.arange(-5, 6)
+    k = 2 * np.pi * m[None, :] + 2 * np.pi / W.GOLDEN * nn[:, None]
+    np.testing.assert_allclose(out, np.exp(-0.5j * n * tau * k ** 2) * phi0, atol=1e-12)
+
+
+def test_free_particle_large_k_argument():
+    """Large tau|k|^2 (reduction of the phase argument): 2049-box kinetic extremes."""
+    p = W.bilayer_1d(1024, 2, 0.0, 0.0, ecut=1e12)
+    phi0 = rand_state(p, 4)
+    out = O.step(p, phi0, 5e-4, "strang", 1)
+    m = np.arange(-1024, 1025)
+    nn = np.arange(-2, 3)
+    k = 2 * np.pi * m[None, :] + 2 * np.pi / W.GOLDEN * nn[:, None]
+    np.testing.assert_allclose(out, np.exp(-0.5j * 5e-4 * k ** 2) * phi0, atol=1e-10)
+
+
+def test_constant_potential_is_global_phase():
+    """v_j = const c_j: each P_j(s) = exp(-i s c_j) I (checks the 1/M of the
+    forward transform and the sign of the exponent)."""
+    p = W.bilayer_1d(5, 4, 0.0, 0.0, ecut=1e9).with_potentials(
+        v1_h=[[0]], v1_c=[0.7], v2_h=[[0]], v2_c=[-0.3])
+    phi0 = rand_state(p, 5)
+    for scheme in ("lie", "strang", "strang_kp"):
+        out = O.step(p, phi0, 0.02, scheme, 3)
+        free = O.step(W.bilayer_1d(5, 4, 0.0, 0.0, ecut=1e9), phi0, 0.02, scheme, 3)
+        np.testing.assert_allclose(out, np.exp(-1j * 0.06 * (0.7 - 0.3)) * free, atol=1e-13)
+
+
+# ---------------------------------------------------------------- conservation
+@pytest.mark.parametrize("scheme", O.SCHEMES)
+def test_mass_conservation(scheme):
+    """Theorem 4.6: the Fourier splitting conserves sum |phi|^2 exactly."""
+    p = W.bilayer_1d(8, 7, 1.3, 0.9, ecut=1e9)
+    phi0 = rand_state(p, 6)
+    out = O.step(p, phi0, 0.01, scheme, 20, seed=11)
+    assert abs(np.linalg.norm(out) - 1.0) < 1e-13
+
+
+def test_layer_factors_commute():
+    """Kronecker structure (Eq. (3.7)): P1(s) P2(t) = P2(t) P1(s)."""
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 7)
+    a = O.apply_P(p, O.apply_P(p, x, 1, 0.3), 2, 0.2)
+    b = O.apply_P(p, O.apply_P(p, x, 2, 0.2), 1, 0.3)
+    np.testing.assert_allclose(a, b, atol=1e-13)
+
+
+def test_strang_time_reversible():
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 8)
+    y = O.step(p, O.step(p, x, 0.01, "strang", 5), -0.01, "strang", 5)
+    np.testing.assert_allclose(y, x, atol=1e-13)
+
+
+# ---------------------------------------------------------------- dense exponential
+def _errors(prob, scheme, T, ns, phi0, exact):
+    return [np.linalg.norm(O.step(prob, phi0, T / n, scheme, n) - exact) for n in ns]
+
+
+@pytest.mark.parametrize("scheme,order", [("lie", 1), ("strang", 2), ("strang_kp", 2)])
+def test_convergence_order_against_dense_exponential(scheme, order):
+    """Theorem 4.5 (order 1 for the Lie form of Algorithm 3) and Strang order 2
+    (Appendix A), against exp(-i T H) of the dense lifted H from coefficients."""
+    p = small_1d()
+    H = dense_H_1d(p)
+    phi0 = rand_state(p, 9)
+    T = 0.2
+    exact = (expm_herm(H, T) @ phi0.reshape(-1)).reshape(phi0.shape)
+    ns = [16, 32, 64, 128]
+    err = _errors(p, scheme, T, ns, phi0, exact)
+    slope = np.polyfit(np.log([T / n for n in ns]), np.log(err), 1)[0]
+    assert abs(slope - order) < 0.1, (scheme, slope, err)
+    assert err[-1] < (1e-2 if order == 1 else 1e-4)
+
+
+def test_one_step_equals_dense_factor_product():
+    """One step equals the product of exact dense exponentials of D, V^1, V^2
+    (Eq. (4.8) sub-problems) in the order Algorithm 3 fixes (K, then V^1, then
+    V^2) for the Lie form, and in the Strang compositions of Appendix A."""
+    p = small_1d()
+    M1, M2 = p.q1[0], p.q2[0]
+    H = dense_H_1d(p)
+    Dm = np.diag(np.diag(H).real - np.diag(np.kron(np.eye(M2), circulant_from_coeffs(p.v1_h, p.v1_c, M1))).real
+                 - np.diag(np.kron(circulant_from_coeffs(p.v2_h, p.v2_c, M2), np.eye(M1))).real)
+    V1 = np.kron(np.eye(M2), circulant_from_coeffs(p.v1_h, p.v1_c, M1))
+    V2 = np.kron(circulant_from_coeffs(p.v2_h, p.v2_c, M2), np.eye(M1))
+    E = lambda A, t: expm_herm(A, t)
+    t = 0.03
+    ref = {
+        "lie": E(V2, t) @ E(V1, t) @ E(Dm, t),
+        "strang": (E(Dm, t / 8) @ E(V1, t / 2) @ E(Dm, t / 8)) @ (E(Dm, t / 4) @ E(V2, t) @ E(Dm, t / 4))
+                  @ (E(Dm, t / 8) @ E(V1, t / 2) @ E(Dm, t / 8)),
+        "strang_kp": E(Dm, t / 2) @ E(V2, t) @ E(V1, t) @ E(Dm, t / 2),
+    }
+    x = rand_state(p, 30)
+    for scheme, U in ref.items():
+        out = O.step(p, x, t, scheme, 1)
+        np.testing.assert_allclose(out.reshape(-1), U @ x.reshape(-1), atol=1e-12, err_msg=scheme)
+
+
+def test_stochastic_converges_in_mean_structure():
+    """Full sampling (p = S) reproduces the deterministic scheme exactly."""
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 10)
+    for base in ("lie", "strang"):
+        a = O.step(p, x, 0.01, base + "_stoch", 4, seed=3, frac_den=1)
+        b = O.step(p, x, 0.01, base, 4)
+        np.testing.assert_allclose(a, b, atol=1e-14)
+
+
+def test_stochastic_sampled_factor_matches_dense():
+    """One stochastic potential factor equals the dense exp(-i s S/p C1) on the
+    sampled rows and the identity elsewhere."""
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 12)
+    sl = np.array([1, 4, 7])
+    y = O.apply_P(p, x, 1, 0.37, sl)
+    C1 = circulant_from_coeffs(p.v1_h, p.v1_c, p.q1[0])
+    U = expm_herm(C1, 0.37)
+    ref = x.copy()
+    ref[sl] = (U @ x[sl].T).T
+    np.testing.assert_allclose(y, ref, atol=1e-13)
+
+
+# ---------------------------------------------------------------- physics pins
+def test_commensurate_fiber_sum_matches_supercell():
+    """L2 = 2/3: k = pi (2m + 3n).  The fiber sum c_j = sum_{2m+3n=j} phi_mn of
+    the lifted Strang solution equals a period-2 supercell split-step solve
+    with the same factor sequence (textbook FFT split step)."""
+    a1, a2 = 1.1, 0.7
+    N = 14
+    p = W.bilayer_1d(N, N, a1, a2, L1=1.0, L2=2.0 / 3.0, ecut=1e9)
+    m = np.arange(-N, N + 1)
+    n = np.arange(-N, N + 1)
+    phi0 = np.exp(-0.35 * (m[None, :] ** 2 + n[:, None] ** 2)) * (1 + 0.3j * m[None, :])
+    tau, nsteps = 0.01, 10
+    lifted = O.step(p, phi0, tau, "strang", nsteps)
+    J = 256
+    j = np.fft.fftfreq(J, 1.0 / J).astype(int)          # plane waves e^{i pi j x}
+    c = np.zeros(J, dtype=np.complex128)
+    for ii, mm in enumerate(m):
+        for jj, nn in enumerate(n):
+            c[(2 * mm + 3 * nn) % J] += phi0[jj, ii]
+    x = 2.0 * np.arange(J) / J
+    v1 = a1 * np.cos(2 * np.pi * x)
+    v2 = a2 * np.cos(2 * np.pi * x / (2.0 / 3.0))
+    kin = 0.5 * (np.pi * j) ** 2
+
+    def K(c, s):
+        return c * np.exp(-1j * s * kin)
+
+    def P(c, v, s):
+        return np.fft.fft(np.fft.ifft(c) * np.exp(-1j * s * v))
+
+    for _ in range(nsteps):
+        for s, v in ((tau / 2, v1), (tau, v2), (tau / 2, v1)):
+            c = K(P(K(c, s / 4), v, s), s / 4)
+    cl = np.zeros(J, dtype=np.complex128)
+    for ii, mm in enumerate(m):
+        for jj, nn in enumerate(n):
+            cl[(2 * mm + 3 * nn) % J] += lifted[jj, ii]
+    np.testing.assert_allclose(cl, c, atol=1e-10)
+
+
+def test_single_layer_reduces_to_bloch_split_step():
+    """a2 = 0: each layer-1 slice n is a periodic problem at quasi-momentum
+    kappa = B2 n, advanced by the textbook split-step Fourier method."""
+    p = W.bilayer_1d(10, 4, 1.5, 0.0, ecut=1e9)
+    x = rand_state(p, 13)
+    tau, nsteps = 0.004, 6
+    out = O.step(p, x, tau, "strang", nsteps)
+    b1, b2 = 2 * np.pi, 2 * np.pi / W.GOLDEN
+    Q = 21
+    mm = np.arange(-10, 11)
+    grid = np.arange(Q) / Q
+    v = 1.5 * np.cos(2 * np.pi * grid)
+    for r, nn in enumerate(range(-4, 5)):
+        u = x[r].copy()
+        kin = 0.5 * (b1 * mm + b2 * nn) ** 2
+        # fft ordering: slice index i <-> m = i - 10; a shift is a real-space
+        # modulation that commutes with the potential multiplication.
+        for _ in range(nsteps):
+            for s, pot in ((tau / 2, True), (tau, False), (tau / 2, True)):
+                u = u * np.exp(-1j * s / 4 * kin)
+                if pot:
+                    u = np.fft.fft(np.fft.ifft(u) * np.exp(-1j * s * v))
+                u = u * np.exp(-1j * s / 4 * kin)
+        np.testing.assert_allclose(out[r], u, atol=1e-12)
+
+
+# ---------------------------------------------------------------- observables
+def test_observables_against_dense_quadratic_forms():
+    p = W.bilayer_1d(5, 4, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 14)
+    H = dense_H_1d(p)
+    o = O.observables(p, x, chi=rand_state(p, 15))
+    v = x.reshape(-1)
+    assert abs(o["norm"] - 1.0) < 1e-14
+    assert abs(o["energy"] - np.vdot(v, H @ v).real) < 1e-10
+    m = np.arange(-5, 6)
+    nn = np.arange(-4, 5)
+    k = 2 * np.pi * m[None, :] + 2 * np.pi / W.GOLDEN * nn[:, None]
+    assert abs(o["kmean"][0] - float((k * np.abs(x) ** 2).sum())) < 1e-11
+    assert abs(o["overlap"] - np.vdot(rand_state(p, 15), x)) < 1e-14
+
+
+def test_strang_energy_error_second_order():
+    """Energy is not conserved exactly by the splitting, but its error after a
+    fixed time shrinks like tau^2 (Strang, Appendix A)."""
+    p = W.bilayer_1d(8, 8, 1.0, 0.8, ecut=200.0 * (8 / 32) ** 2 * 16)
+    x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+    e0 = O.observables(p, x)["energy"]
+    d = [abs(O.observables(p, O.step(p, x, 0.1 / n, "strang", n))["energy"] - e0)
+         for n in (50, 100)]
+    assert d[0] < 1e-3 and 3.0 < d[0] / d[1] < 5.0, d
+
+
+# ---------------------------------------------------------------- initial state
+def test_gaussian_packet_reduces_to_paper_initial_state():
+    """x0 = 0, k0 = 0: phi = exp(-gamma |k|^2) with gamma = w^2/2 (Sec. 5)."""
+    p = W.config_small_1d()
+    w = 2.0
+    phi = O.gaussian_packet(p, [0.0], w, [0.0])
+    m = np.arange(-32, 33)
+    nn = np.arange(-32, 33)
+    k = 2 * np.pi * m[None, :] + 2 * np.pi / W.GOLDEN * nn[:, None]
+    ref = np.exp(-(w * w / 2) * k ** 2) * (0.5 * k ** 2 <= 200.0)
+    np.testing.assert_allclose(phi, ref / np.linalg.norm(ref), atol=1e-15)
+
+
+# ---------------------------------------------------------------- index set
+def _exact_mask_mp(prob, idx):
+    import mpmath as mp
+    mp.mp.dps = 60
+    b1 = 2 * mp.pi / mp.mpf(1)
+    b2 = 2 * mp.pi / ((mp.sqrt(5) - 1) / 2)
+    out, margin = [], mp.inf
+    for (n, m) in idx:
+        e = (b1 * m + b2 * n) ** 2 / 2
+        out.append(e <= prob.ecut)
+        margin = min(margin, abs(e - prob.ecut) / prob.ecut)
+    return np.array(out), float(margin)
+
+
+@pytest.mark.parametrize("cfg", ["small", "scale"])
+def test_index_mask_matches_exact_predicate(cfg):
+    """The FP64 joint-cutoff mask equals the exact real predicate with the true
+    lattice L2 = (sqrt5 - 1)/2, with a certified relative margin (Sec. 3)."""
+    pytest.importorskip("mpmath")
+    p = W.config_small_1d() if cfg == "small" else W.config_scale_1d()
+    mask = O.index_mask(p)
+    e = O.kinetic_energy_diag(p)
+    near = np.argwhere(np.abs(e - p.ecut) < 2e-3 * p.ecut)
+    rows = near[:, 0] + p.lo2[0]
+    cols = near[:, 1] + p.lo1[0]
+    ex, margin = _exact_mask_mp(p, list(zip(rows, cols)))
+    assert np.array_equal(ex, mask[near[:, 0], near[:, 1]])
+    assert margin > 1e-9
+    if cfg == "small":
+        # Every element of the box, not just the near-boundary ones.
+        allidx = [(n, m) for n in range(-32, 33) for m in range(-32, 33)]
+        ex_all, _ = _exact_mask_mp(p, allidx)
+        assert np.array_equal(ex_all.reshape(65, 65), mask)
+
+
+# ---------------------------------------------------------------- sampling
+def test_splitmix64_known_answers():
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            vals = [int(t) for t in line.split()]
+            s = vals[0]
+            for want in vals[1:]:
+                s, r = O.splitmix64_next(s)
+                assert r == want
+
+
+def test_sample_slices_properties():
+    for S, p, seed, g in [(2049, 256, 7, 0), (2049, 256, 7, 1), (65, 8, 1, 5), (10, 10, 0, 0)]:
+        s = O.sample_slices(S, p, seed, g)
+        assert len(s) == p and len(set(s.tolist())) == p
+        assert np.all(np.diff(s) > 0) and s[0] >= 0 and s[-1] < S
+    assert not np.array_equal(O.sample_slices(2049, 256, 7, 0), O.sample_slices(2049, 256, 7, 1))
+    # Uniformity: each slice is chosen with probability p/S.
+    cnt = np.zeros(40)
+    for g in range(4000):
+        cnt[O.sample_slices(40, 5, 3, g)] += 1
+    assert np.all(np.abs(cnt / 4000 - 5 / 40) < 0.03)
+
+
+# ---------------------------------------------------------------- adjoint
+def test_adjoint_matches_central_differences():
+    th1 = np.array([0.6, -0.3, 0.2])
+    th2 = np.array([0.4, 0.25])
+    base = W.bilayer_1d(6, 5, 0.0, 0.0, ecut=1e9)
+
+    def prob(t1, t2):
+        h1, c1 = W.cos_series_coeffs(t1)
+        h2, c2 = W.cos_series_coeffs(t2)
+        return base.with_potentials(c1, c2, h1, h2)
+
+    phi0 = O.gaussian_packet(base, [0.0], 0.8, [1.0])
+    chi = O.gaussian_packet(base, [0.3], 0.8, [1.2])
+    tau, n = 0.02, 6
+    lossfn = lambda phi: O.overlap_loss(chi, phi)
+    for scheme in ("strang", "lie"):
+        L, _, g1, g2 = O.adjoint(prob(th1, th2), phi0, tau, scheme, n, lossfn)
+        cg1 = O.coefficient_gradient(g1, np.array([[h] for h in (1, -1, 2, -2, 3, -3)]), (13,))
+        # d/dtheta_h of theta_h cos = chain through the +h and -h halves (each /2).
+        grad = [0.5 * (cg1[2 * i, 0] + cg1[2 * i + 1, 0]) for i in range(3)]
+        h = 1e-4
+        for i in range(3):
+            tp, tm = th1.copy(), th1.copy()
+            tp[i] += h
+            tm[i] -= h
+            Lp = lossfn(O.step(prob(tp, th2), phi0, tau, scheme, n))[0]
+            Lm = lossfn(O.step(prob(tm, th2), phi0, tau, scheme, n))[0]
+            fd = (Lp - Lm) / (2 * h)
+            assert abs(fd - grad[i]) < 1e-7 * max(1.0, abs(fd)) + 1e-9, (scheme, i, fd, grad[i])
+        # Layer 2, grid gradient direct: perturb v2 by a single cosine mode.
+        for i in range(2):
+            tp, tm = th2.copy(), th2.copy()
+            tp[i] += h
+            tm[i] -= h
+            fd = (lossfn(O.step(prob(th1, tp), phi0, tau, scheme, n))[0]
+                  - lossfn(O.step(prob(th1, tm), phi0, tau, scheme, n))[0]) / (2 * h)
+            q = 11
+            an = float(np.sum(g2 * np.cos(2 * np.pi * (i + 1) * np.arange(q) / q)))
+            assert abs(fd - an) < 1e-7 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_adjoint_dot_product():
+    """<U x, y> = <x, U^H y> with U^H applied as the reverse sweep (-tau)."""
+    p = W.bilayer_1d(6, 5, 1.2, 0.7, ecut=1e9)
+    x, y = rand_state(p, 20), rand_state(p, 21)
+    Ux = O.step(p, x, 0.01, "strang", 4)
+    UHy = O.step(p, y, -0.01, "strang", 4)   # symmetric scheme: U^H = U(-tau)
+    assert abs(np.vdot(Ux, y) - np.vdot(x, UHy)) < 1e-13
+
+
+# ---------------------------------------------------------------- 2D
+def _dense_H_2d(prob):
+    m = O.box_indices(prob.lo1, prob.q1).astype(float)
+    n = O.box_indices(prob.lo2, prob.q2).astype(float)
+    k = (m @ prob.B1.T)[None, :, :] + (n @ prob.B2.T)[:, None, :]
+    D = np.diag(0.5 * (k ** 2).sum(-1).reshape(-1))
+
+    def circ2(h, c, q):
+        M = q[0] * q[1]
+        C = np.zeros((M, M), dtype=np.complex128)
+        for (h0, h1), cc in zip(h, c):
+            for i1 in range(q[1]):
+                for i0 in range(q[0]):
+                    j0, j1 = (i0 - h0) % q[0], (i1 - h1) % q[1]
+                    C[i1 * q[0] + i0, j1 * q[0] + j0] += cc
+        return C
+
+    C1 = circ2(prob.v1_h, prob.v1_c, prob.q1)
+    C2 = circ2(prob.v2_h, prob.v2_c, prob.q2)
+    return D + np.kron(np.eye(prob.M2), C1) + np.kron(C2, np.eye(prob.M1))
+
+
+def test_2d_order_against_dense_exponential():
+    p = W.twisted_2d(q=4, theta_deg=5.0, hmax=1)
+    p.B1 = p.B1 / 4.0
+    p.B2 = p.B2 / 4.0
+    H = _dense_H_2d(p)
+    phi0 = W.random_state((p.M2, p.M1), 22)
+    T = 0.2
+    exact = (expm_herm(H, T) @ phi0.reshape(-1)).reshape(phi0.shape)
+    ns = [16, 32, 64]
+    err = _errors(p, "strang", T, ns, phi0, exact)
+    slope = np.polyfit(np.log([T / n for n in ns]), np.log(err), 1)[0]
+    assert abs(slope - 2) < 0.15, (slope, err)
+
+
+def test_2d_free_particle_and_mass():
+    p = W.twisted_2d(q=4, hmax=1)
+    phi0 = W.random_state((p.M2, p.M1), 23)
+    z = p.with_potentials(v1_c=np.zeros(len(p.v1_c)), v2_c=np.zeros(len(p.v2_c)))
+    out = O.step(z, phi0, 0.003, "strang", 3)
+    m = O.box_indices(p.lo1, p.q1).astype(float)
+    n = O.box_indices(p.lo2, p.q2).astype(float)
+    k = (m @ p.B1.T)[None, :, :] + (n @ p.B2.T)[:, None, :]
+    np.testing.assert_allclose(out, np.exp(-0.5j * 0.009 * (k ** 2).sum(-1)) * phi0, atol=1e-12)
+    out = O.step(p, phi0, 0.003, "strang", 3)
+    assert abs(np.linalg.norm(out) - 1) < 1e-13
