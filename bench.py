@@ -1,0 +1,338 @@
+"""Throughput of the layer-split step on one GB300 (or N replicas).
+
+Workload: the 2049 x 2049 lifted 1D incommensurate bilayer (L1 = 1,
+L2 = (sqrt5-1)/2, v_j = a_j cos(2 pi x / L_j), a_j ~ U(0.5, 2) seed 2,
+joint cutoff Ec = 204800), complex64 with FP64-derived tables, Gaussian packet
+(x0 = 0, w = 2, k0 = 1), tau = 5e-4, second-order (Strang) layer split.
+
+One bench step = one time step of the scheme (3 fused slice passes) through
+ls_step on device-resident data.  psi (33.8 MB) fits in L2, so a 512 MB buffer
+is written between timed steps (L2 flush, untimed).  Metric: lifted
+DOF-steps/s = (M1 * M2 * steps) / seconds.
+
+Also reported: the same metric for the plain FP64 (complex128) GPU form, the
+end-to-end figure through the C ABI with host buffers (H2D copy, step, D2H
+copy inside the timed region), the roofline of the pass kernel, the accuracy
+gate against the oracle, and the FP64 CPU oracle on the host cores.
+
+--impl reference: times the FP64 CPU oracle (the reference arm of this
+repository) on the same workload.
+Multi-GPU: the workload does not shard (one lifted array), so N ranks run N
+independent replicas ("replicas only"); value sums all ranks' DOF-steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "lifted DOF-steps/s (FP32 vs plain FP64, one GB300) at rel-L2<=1e-5; % HBM roofline"
+TAU = 5e-4
+BYTES_PER_DOF_PASS = 16  # complex64 read + write
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def oracle_step_rate(prob, x, steps, scheme="strang"):
+    import oracle as O
+    O.use_fft(True)
+    try:
+        t0 = time.perf_counter()
+        y = O.step(prob, x, TAU, scheme, steps)
+        dt = time.perf_counter() - t0
+    finally:
+        O.use_fft(False)
+    return prob.dof * steps / dt, dt, y
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    p = W.config_scale_1d()
+    x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+    for _ in range(args.warmup):
+        oracle_step_rate(p, x, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt, x = oracle_step_rate(p, x, 1)
+        times.append(dt)
+    tot = sum(times)
+    val = p.dof * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF-steps/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "bilayer1d-2049x2049 strang tau=5e-4", "box": [2049, 2049],
+                   "scheme": "strang", "tau": TAU, "l2_flush": "n/a (host)"},
+        "cpu_baseline": {"value": val, "unit": "DOF-steps/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} full Strang steps of the 2049x2049 box, FP64 NumPy "
+                                   "oracle with its FFT transform backend"},
+        "e2e": {"value": val, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, lr = dist_env()
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(lr)
+    import __graft_entry__ as G
+    G.build()
+    import oracle as O
+    import paper_2103_14897_gb300 as P
+
+    p = W.config_scale_1d()
+    scheme = args.scheme
+    ctx = P.Context(p, "c64")
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+
+    # accuracy gate: one step against the oracle (FFT backend), FP64 reference
+    x0 = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+    chk = ctx.from_dense(x0)
+    ctx.step(chk, 1, TAU, scheme, seed=7)
+    O.use_fft(True)
+    try:
+        ref1 = O.step(p, x0, TAU, scheme, 1, seed=7)
+    finally:
+        O.use_fft(False)
+    got1 = ctx.to_dense(chk)
+    relerr = float(np.linalg.norm(got1 - ref1) / np.linalg.norm(ref1))
+    del chk
+
+    for k in range(args.warmup):
+        ctx.step(psi, 1, TAU, scheme, seed=7, step0=k)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(lr) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(st)
+            ctx.step(psi, 1, TAU, scheme, seed=7, step0=args.warmup + k)
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    per = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(sum(per))
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    obs = ctx.observables(psi)
+    value = world * p.dof * args.steps / (t_ms / 1e3)
+
+    # plain FP64 GPU form (same kernels in complex128)
+    ctx64 = P.Context(p, "c128")
+    psi64 = ctx64.empty()
+    ctx64.init_gaussian(psi64, [0.0], 2.0, [1.0])
+    for _ in range(2):
+        ctx64.step(psi64, 1, TAU, scheme)
+    n64 = max(3, args.steps // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t64 = 0.0
+    for k in range(n64):
+        flush.fill_(float(k))
+        e0.record(st)
+        ctx64.step(psi64, 1, TAU, scheme)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t64 += e0.elapsed_time(e1)
+    fp64_value = p.dof * n64 / (t64 / 1e3)
+    del psi64, ctx64
+
+    # end to end through the C ABI with host buffers (pinned)
+    host = torch.empty((ctx.rows, ctx.pitch), dtype=torch.complex64, pin_memory=True)
+    host.copy_(psi)
+    nbytes = host.numel() * host.element_size()
+    dev = ctx.empty()
+    ne = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(ne):
+        dev.copy_(host, non_blocking=True)
+        ctx.step(dev, 1, TAU, scheme, seed=7, step0=k)
+        host.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    e2e = world * p.dof * ne / te
+
+    # roofline of the pass kernel: every launch in a step is a pass (3 for
+    # Strang, 2 for Lie / kinetic-potential Strang)
+    npass = 3 if scheme.startswith("strang") and scheme != "strang_kp" else 2
+    if scheme.endswith("_stoch"):
+        npass_eff = None
+    else:
+        npass_eff = npass
+    hbm, src = peaks()
+    ms_launch = t_ms / args.steps / npass
+    algo_bytes = BYTES_PER_DOF_PASS * p.dof
+    achieved = algo_bytes / (ms_launch / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            traffic = json.load(f).get(f"pass_kernel:{scheme}")
+    except Exception:
+        pass
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        xs = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+        rate, dt, _ = oracle_step_rate(p, xs, args.cpu_steps, scheme)
+        cpu = {"value": rate, "unit": "DOF-steps/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{args.cpu_steps} full {scheme} steps of the 2049x2049 box ({dt:.1f} s), "
+                         "FP64 NumPy oracle, FFT transform backend"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic",
+            "config": {"workload": f"bilayer1d-2049x2049 {scheme} tau=5e-4", "box": [2049, 2049],
+                       "dof": p.dof, "scheme": scheme, "tau": TAU,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2_flush": "512 MB buffer written between timed steps"},
+            "accuracy": {"rel_l2_1step_vs_oracle": relerr, "norm_minus_1": obs["norm"] - 1.0,
+                         "gate_rel_l2": 1e-5, "pass": relerr <= 1e-5},
+            "fp64_gpu": {"value": fp64_value, "unit": "DOF-steps/s", "dtype": "c128",
+                         "speedup_fp32_over_fp64": value / world / fp64_value},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "note": f"pass_kernel, {algo_bytes} algorithmic bytes/launch, {src} peak; "
+                                 "psi is L2-resident between passes"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e, "unit": "DOF-steps/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": npass * args.steps if npass_eff else None,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scheme", default="strang")
+    ap.add_argument("--cpu-steps", type=int, default=5)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,181 @@
+/*
+ * lsplit.h -- C ABI of the GB300 layer-split time stepper for the lifted
+ * plane-wave Schroedinger equation of incommensurate bilayers
+ * (Wang, Chen, Zhou & Zhou, arXiv 2103.14897).
+ *
+ * Model.  Two periodic layers with reciprocal lattices B_j = 2 pi A_j^{-T}
+ * (Sec. 2).  The wave function is lifted to coefficients phi[n][m] of the
+ * plane waves exp(i (B1 m + B2 n) . x) (Sec. 3, Eq. (3.3)); the semidiscrete
+ * problem is d phi/dt = -i (D + V^1 + V^2) phi (Eq. (3.4)-(3.7)) with D
+ * diagonal, V^1 = I (x) Vc^1 acting on m, V^2 = Vc^2 (x) I acting on n.
+ *
+ * One step splits exp(-i tau H) into the kinetic factor K(s) = exp(-i s D)
+ * and the layer factors P_j(s) = F_j diag(exp(-i s v_j(x_p))) F_j^{-1}
+ * along layer j's index for every slice (fixed index of the other layer)
+ * (Eq. (4.8), Algorithm 3).  Compositions: Lie (Algorithm 3 order), Strang
+ * over H = H1 + H2 (Appendix A), kinetic/potential Strang, and the random
+ * batch (Algorithm 4) slice-sampling variants.
+ *
+ * Conventions for every entry point:
+ *   - Return value: LS_OK (0) or a negative LS_ERR_* code; nothing aborts,
+ *     no C++ exception crosses the ABI.  ls_last_error() gives a message
+ *     (thread-local, valid until the next call on that thread).
+ *   - "_dev" pointers are CUDA device memory owned by the caller; "_host"
+ *     pointers are host memory owned by the caller.  The library never frees
+ *     caller memory and never allocates the wave-function arrays.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued asynchronously unless the function says it syncs.
+ *   - Wave-function layout: complex interleaved (re, im), float (LS_C64) or
+ *     double (LS_C128).  Element (m, n) is at n_lin * pitch + m_lin, where
+ *     m_lin / n_lin are linear box indices with the first component fastest
+ *     (m_lin = (m_1 - lo1_1) + q1_1 * (m_2 - lo1_2) in 2D), and pitch >= M1
+ *     is given by ls_layout().  Elements in the pitch padding are neither
+ *     read nor written.
+ */
+#ifndef LSPLIT_H
+#define LSPLIT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LS_OK = 0,
+  LS_ERR_INVALID = -1, /* bad argument or unsupported problem */
+  LS_ERR_NOMEM = -2,   /* device or host allocation failed */
+  LS_ERR_CUDA = -3,    /* a CUDA runtime call failed */
+  LS_ERR_TIMEOUT = -4, /* a bounded device wait expired */
+  LS_ERR_STATE = -5    /* call out of order (e.g. destroyed context) */
+};
+
+enum { LS_C64 = 0, LS_C128 = 1 };
+
+/* Schemes (one time step tau, factors in application order):
+ *   LS_LIE          K(tau), P1(tau), P2(tau)                  (Algorithm 3)
+ *   LS_STRANG       L1(tau/2) L2(tau) L1(tau/2),  L_j(s) = K(s/4) P_j(s) K(s/4)
+ *                   (Strang over H = H1 + H2, H_j = D/2 + V^j; Appendix A)
+ *   LS_STRANG_KP    K(tau/2), P1(tau), P2(tau), K(tau/2)
+ *   LS_LIE_STOCH, LS_STRANG_STOCH: as above, but every layer factor acts on
+ *                   p = max(1, S/frac_den) seeded random slices out of S with
+ *                   duration s*S/p (Algorithm 4); kinetic factors act on all. */
+enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_STOCH = 4 };
+
+/* Problem description (Sec. 2-3).  All arrays are read during ls_create only
+ * and stay owned by the caller.
+ *   d             1 or 2
+ *   B1, B2        row-major d x d reciprocal-lattice matrices; k = B1 m + B2 n
+ *   lo1, q1       layer-1 box: m_i in [lo1[i], lo1[i] + q1[i]), q1[i] >= 1
+ *   lo2, q2       layer-2 box
+ *   ecut          energy cutoff Ec of the joint mask |k|^2/2 <= Ec (Sec. 3)
+ *   nv1, v1_h, v1_c  nv1 reciprocal indices h (int32, nv1*d) and complex
+ *                 Fourier coefficients vhat (re, im pairs, 2*nv1 doubles) of
+ *                 v_1 (Eq. (2.2)); v_1(x_p) = Re sum_h vhat_h e^{2 pi i h.p/q1}
+ *   nv2, v2_h, v2_c  same for v_2
+ *   dtype         LS_C64 (complex float, FP64 phase arithmetic) or LS_C128
+ *   frac_den      stochastic sampling denominator (p = max(1, S/frac_den)), >= 1
+ * Supported slice shapes: 1D any length (powers of two use a direct radix FFT,
+ * others a Bluestein transform of power-of-two length >= 2q-2, at most 8192);
+ * 2D slices need power-of-two extents with q_1 * q_2 <= 4096. */
+typedef struct ls_problem {
+  int32_t d;
+  double B1[4];
+  double B2[4];
+  int32_t lo1[2], q1[2];
+  int32_t lo2[2], q2[2];
+  double ecut;
+  int32_t nv1;
+  const int32_t* v1_h;
+  const double* v1_c;
+  int32_t nv2;
+  const int32_t* v2_h;
+  const double* v2_c;
+  int32_t dtype;
+  int32_t frac_den;
+} ls_problem;
+
+/* Observables (Eq. (2.4)-(2.5) in the lifted basis, Eq. (3.2) orthonormality),
+ * all accumulated in FP64:
+ *   norm = sum |phi|^2;  ekin = sum |k|^2/2 |phi|^2;
+ *   epot1/epot2 = sum over slices of (1/M_j) sum_p v_j(x_p) |psi(x_p)|^2;
+ *   energy = ekin + epot1 + epot2;  kmean[i] = sum k_i |phi|^2;
+ *   overlap = sum conj(chi) phi (0 if chi is NULL). */
+typedef struct ls_obs {
+  double norm, ekin, epot1, epot2, energy;
+  double kmean[2];
+  double overlap_re, overlap_im;
+} ls_obs;
+
+typedef struct ls_ctx ls_ctx;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* ls_last_error(void);
+
+/* Build the index set, device tables (potential grids, transform tables,
+ * fixed-point kinetic coefficients) and per-context scratch on the current
+ * CUDA device.  *out receives the context.  Errors: LS_ERR_INVALID for an
+ * unsupported shape or bad field; LS_ERR_NOMEM / LS_ERR_CUDA. */
+int ls_create(const ls_problem* prob, ls_ctx** out);
+
+/* Release the context's device tables and scratch.  Safe on NULL. */
+int ls_destroy(ls_ctx* ctx);
+
+/* Layout of the wave-function array: *pitch (elements per layer-1 slice row,
+ * >= M1), *rows (= M2), *bytes (pitch * M2 * element size). */
+int ls_layout(const ls_ctx* ctx, int64_t* pitch, int64_t* rows, int64_t* bytes);
+
+/* Joint-cutoff index set (Sec. 3 index sets with the joint predicate
+ * fl(0.5 * fl(sum_i fl(u_i^2))) <= Ec, u_i = sum_j fl(B1[i][j] m_j) + sum_j
+ * fl(B2[i][j] n_j) evaluated left to right in IEEE binary64 without FMA).
+ * mask_host: M2*M1 bytes (row n, column m, no padding), may be NULL;
+ * *count: number of members. */
+int ls_index_set(const ls_ctx* ctx, uint8_t* mask_host, int64_t* count);
+
+/* Initial state (Sec. 5, shifted and scaled): phi = exp(-w^2 |k-k0|^2 / 2)
+ * exp(-i k.x0) on the joint mask, zero elsewhere, normalised to unit l2 norm.
+ * x0, k0: d doubles (host).  Enqueued on stream. */
+int ls_init_gaussian(ls_ctx* ctx, void* psi_dev, const double* x0_host, double w,
+                     const double* k0_host, void* stream);
+
+/* Advance psi_dev in place by nsteps steps of tau with the given scheme.
+ * seed and step0 fix the stochastic samples (sub-step g = (step0 + k) *
+ * factors_per_step + factor index).  Adjacent kinetic factors are merged; each
+ * layer factor is one fused pass over the array.  Stochastic schemes apply
+ * kinetic factors lazily and finish with a settle pass, so psi_dev is complete
+ * on return.  Enqueued on stream (replays a cached CUDA graph). */
+int ls_step(ls_ctx* ctx, void* psi_dev, int64_t nsteps, double tau, int32_t scheme,
+            uint64_t seed, uint64_t step0, void* stream);
+
+/* Observables of psi_dev (and overlap with chi_dev if not NULL).  Synchronises
+ * the stream and writes *out (host). */
+int ls_observables(ls_ctx* ctx, const void* psi_dev, const void* chi_dev, ls_obs* out,
+                   void* stream);
+
+/* Slice samples of the stochastic variant (Algorithm 4) as drawn on the device:
+ * for sub-steps g0 .. g0+count-1 of the given layer (1 or 2) writes count * p
+ * sorted slice indices to out_host (int32), p = max(1, S/frac_den).
+ * Synchronises the stream. */
+int ls_samples(ls_ctx* ctx, int32_t layer, uint64_t seed, uint64_t g0, int32_t count,
+               int32_t* out_host, int32_t* p_out, void* stream);
+
+/* Reverse sweep for gradients of a real loss L(phi_T) (no stored trajectory).
+ * Inputs: psi_dev = phi_T, lam_dev = dL/d conj(phi_T) (Wirtinger).  Runs the
+ * inverse of each factor in reverse order on both arrays (the factors are
+ * unitary, so phi_T is rebuilt back to phi_0 while lambda is pulled back), and
+ * at every layer factor accumulates dL/dv_j(x_p) = 2 s Im(conj(mu_p) psi_p)
+ * (mu, psi: unitary grid transforms of lambda and phi after the factor).
+ * grad_v1_host (M1 doubles) and grad_v2_host (M2 doubles) receive the grid
+ * gradients; grad_c1_host / grad_c2_host (2*nv doubles, may be NULL) receive
+ * (dL/dRe vhat_h, dL/dIm vhat_h) for every coefficient.  On return psi_dev
+ * holds the rebuilt phi_0 and lam_dev the gradient with respect to
+ * conj(phi_0).  Deterministic schemes only.  Synchronises the stream. */
+int ls_adjoint(ls_ctx* ctx, void* psi_dev, void* lam_dev, int64_t nsteps, double tau,
+               int32_t scheme, double* grad_v1_host, double* grad_v2_host,
+               double* grad_c1_host, double* grad_c2_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSPLIT_H */

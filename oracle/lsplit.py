@@ -38,7 +38,8 @@ __all__ = [
     "box_indices", "wavevectors", "kinetic_energy_diag", "index_mask", "mask_count",
     "dft_matrix", "grid_potential", "apply_K", "apply_P", "scheme_factors", "step",
     "splitmix64_next", "sample_slices", "observables", "gaussian_packet",
-    "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient",
+    "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient", "use_fft",
+    "TRANSFORM", "sample_count", "expanded_factors",
 ]
 
 SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch")
@@ -128,6 +129,16 @@ def grid_potential(h: np.ndarray, c: np.ndarray, q: Sequence[int]) -> np.ndarray
     return acc.real.copy()
 
 
+# Transform backend: "dft" (dense matrices, the definition) or "fft" (NumPy's
+# FFT as a library primitive for the same transform, used for large arrays;
+# pinned against "dft" in the tests).
+TRANSFORM = {"kind": "dft"}
+
+
+def use_fft(on: bool = True) -> None:
+    TRANSFORM["kind"] = "fft" if on else "dft"
+
+
 def _axis_dft(x: np.ndarray, q: Sequence[int], inverse: bool) -> np.ndarray:
     """Apply the (separable) DFT of a layer along axis 1 of x (shape (R, prod q)).
     inverse=True: coefficients -> grid values, W (unnormalised).
@@ -135,6 +146,13 @@ def _axis_dft(x: np.ndarray, q: Sequence[int], inverse: bool) -> np.ndarray:
     For d = 2 the transform matrix is the Kronecker product W(q1) (x) W(q0);
     it is applied one factor at a time."""
     R = x.shape[0]
+    if TRANSFORM["kind"] == "fft":
+        M = int(np.prod(q))
+        y = np.asarray(x).reshape((R,) + tuple(q[::-1]))
+        axes = tuple(range(1, len(q) + 1))
+        if inverse:
+            return (np.fft.ifftn(y, axes=axes) * M).reshape(R, M)
+        return (np.fft.fftn(y, axes=axes) / M).reshape(R, M)
     if len(q) == 1:
         W = dft_matrix(q[0])
         return x @ W if inverse else (x @ W.conj()) / q[0]

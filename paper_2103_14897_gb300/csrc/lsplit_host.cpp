@@ -1,0 +1,919 @@
+// Host side of the layer-split stepper: the C ABI of include/lsplit.h.
+//
+// Compiled with -ffp-contract=off: the joint-cutoff predicate and every FP64
+// table are evaluated in a fixed IEEE binary64 operation order.
+//
+// Responsibilities:
+//   * validate the problem and build the joint-cutoff index set (Sec. 3);
+//   * FP64 tables: potentials on the layer grids (Eq. (2.2)), potential phase
+//     tables exp(-i s v_j(x_p)) / M_j (Algorithm 3 step 3/4), transform
+//     twiddles and Bluestein kernels;
+//   * 64-bit fixed-point coefficients of the kinetic phase s |k|^2 / 2;
+//   * compose the passes of a step (Lie, Strang, kinetic/potential Strang,
+//     stochastic), merging adjacent kinetic factors, and replay them as
+//     cached CUDA graphs;
+//   * observables, the stochastic sampler and the reverse (adjoint) sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lsplit.h"
+#include "lsplit_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct CudaError {
+  cudaError_t e;
+  std::string where;
+};
+
+#define LS_CUDA(call)                                                             \
+  do {                                                                            \
+    cudaError_t _e = (call);                                                      \
+    if (_e != cudaSuccess) throw CudaError{_e, std::string(#call) + " @" + std::to_string(__LINE__)}; \
+  } while (0)
+
+using cd = std::complex<double>;
+constexpr double kPi = 3.14159265358979323846;
+
+// x mod 1 as a 64-bit fixed-point fraction (2^-64 turns), truncated.
+uint64_t to_fixed(double x) {
+  const bool neg = x < 0;
+  double a = neg ? -x : x;
+  a = a - std::floor(a);  // exact
+  const double s1 = a * 4294967296.0;
+  const double hi = std::floor(s1);
+  const double s2 = (s1 - hi) * 4294967296.0;  // exact
+  const double lo = std::floor(s2);
+  uint64_t v = ((uint64_t)hi << 32) + (uint64_t)lo;
+  return neg ? (uint64_t)0 - v : v;
+}
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int log2i(int64_t x) {
+  int l = 0;
+  while ((int64_t(1) << l) < x) ++l;
+  return l;
+}
+
+// Iterative radix-2 FP64 FFT (forward: exp(-2 pi i jk/n)); used for tables only.
+void fft64(std::vector<cd>& a, bool inverse) {
+  const size_t n = a.size();
+  for (size_t i = 1, j = 0; i < n; ++i) {
+    size_t bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (size_t len = 2; len <= n; len <<= 1) {
+    for (size_t i = 0; i < n; i += len) {
+      for (size_t k = 0; k < len / 2; ++k) {
+        const double ang = 2.0 * kPi * (double)k / (double)len * (inverse ? 1.0 : -1.0);
+        const cd w(std::cos(ang), std::sin(ang));
+        const cd u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+    }
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  void alloc(size_t b) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (b == 0) return;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw CudaError{e, "cudaMalloc(" + std::to_string(b) + ")"};
+    }
+    bytes = b;
+  }
+};
+
+struct PassSpec {
+  int layer;      // 1 or 2
+  double s;       // duration of the layer factor
+  int64_t pre, post;  // kinetic units before / after (deterministic)
+  int32_t now;    // kinetic clock at the layer factor (lazy)
+  int pidx;       // index of the layer factor within its step
+  int64_t step;   // step index within the call
+};
+
+struct GraphEntry {
+  void* psi;
+  int scheme;
+  double tau;
+  int64_t n;
+  cudaGraphExec_t exec = nullptr;
+  std::shared_ptr<DevBuf> lists;
+  ~GraphEntry() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+}  // namespace
+
+struct ls_ctx {
+  ls_problem p{};
+  std::vector<int32_t> h1, h2;
+  std::vector<double> c1, c2;
+  int d = 1;
+  int64_t M1 = 0, M2 = 0, pitch = 0;
+  int dtype = LS_C64;
+  size_t esize = 8;
+  int device = 0;
+  int frac_den = 8;
+  lsk::LayerGeom geom[2]{};
+  int W[2] = {1, 1}, bpt[2] = {2, 2}, nt[2] = {64, 64};
+  DevBuf tw[2], twb[2], bm[2], bp[2], vgrid[2];
+  std::vector<double> vhost[2];
+  std::map<std::pair<int, uint64_t>, std::shared_ptr<DevBuf>> ttab;  // (layer, bits(s)) -> table
+  DevBuf partials, result, touch_row, touch_col, seedbuf, grad[2];
+  int nblk_elem = 0;
+  size_t partial_count = 0;
+  std::list<std::unique_ptr<GraphEntry>> graphs;
+  cudaStream_t cap = nullptr;
+  lsk::ElemArgs ea{};
+  ~ls_ctx() {
+    graphs.clear();
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------- tables
+std::vector<double> grid_potential(const std::vector<int32_t>& h, const std::vector<double>& c, int d,
+                                   const int32_t* q) {
+  const int64_t M = (int64_t)q[0] * (d > 1 ? q[1] : 1);
+  const size_t nh = c.size() / 2;
+  std::vector<double> v(M, 0.0);
+  for (int64_t p = 0; p < M; ++p) {
+    const int64_t pa = p % q[0], pb = p / q[0];
+    double acc = 0.0;
+    for (size_t t = 0; t < nh; ++t) {
+      // e^{2 pi i (h_a p_a / q_a + h_b p_b / q_b)}, integer-reduced per component
+      int64_t ra = (((int64_t)h[t * d] * pa) % q[0] + q[0]) % q[0];
+      double ang = 2.0 * kPi * (double)ra / (double)q[0];
+      cd ph(std::cos(ang), std::sin(ang));
+      if (d > 1) {
+        int64_t rb = (((int64_t)h[t * d + 1] * pb) % q[1] + q[1]) % q[1];
+        double angb = 2.0 * kPi * (double)rb / (double)q[1];
+        ph *= cd(std::cos(angb), std::sin(angb));
+      }
+      acc += (cd(c[2 * t], c[2 * t + 1]) * ph).real();
+    }
+    v[p] = acc;
+  }
+  return v;
+}
+
+template <typename Real>
+void upload_complex(DevBuf& buf, const std::vector<cd>& h) {
+  std::vector<Real> tmp(2 * h.size());
+  for (size_t i = 0; i < h.size(); ++i) {
+    tmp[2 * i] = (Real)h[i].real();
+    tmp[2 * i + 1] = (Real)h[i].imag();
+  }
+  buf.alloc(tmp.size() * sizeof(Real));
+  LS_CUDA(cudaMemcpy(buf.p, tmp.data(), tmp.size() * sizeof(Real), cudaMemcpyHostToDevice));
+}
+
+void upload_c(ls_ctx* c, DevBuf& buf, const std::vector<cd>& h) {
+  if (c->dtype == LS_C64) upload_complex<float>(buf, h);
+  else upload_complex<double>(buf, h);
+}
+
+std::vector<cd> twiddles(int n) {
+  std::vector<cd> t(n);
+  for (int x = 0; x < n; ++x) {
+    const double ang = -2.0 * kPi * (double)x / (double)n;
+    t[x] = cd(std::cos(ang), std::sin(ang));
+  }
+  return t;
+}
+
+// FFT_np of the wrapped chirp b_j = exp(sign i pi j^2 / q), divided by np.
+std::vector<cd> bluestein_kernel(int q, int np, double sign) {
+  std::vector<cd> b(np, cd(0, 0));
+  for (int j = 0; j < q; ++j) {
+    const int64_t r = ((int64_t)j * j) % (2 * (int64_t)q);
+    const double ang = sign * kPi * (double)r / (double)q;
+    const cd v(std::cos(ang), std::sin(ang));
+    b[j] = v;
+    if (j > 0) b[np - j] = v;
+  }
+  fft64(b, false);
+  for (auto& x : b) x /= (double)np;
+  return b;
+}
+
+const void* phase_table(ls_ctx* c, int layer, double s) {
+  uint64_t bits;
+  std::memcpy(&bits, &s, 8);
+  auto key = std::make_pair(layer, bits);
+  auto it = c->ttab.find(key);
+  if (it != c->ttab.end()) return it->second->p;
+  const std::vector<double>& v = c->vhost[layer - 1];
+  const double M = (double)v.size();
+  std::vector<cd> T(v.size());
+  for (size_t p = 0; p < v.size(); ++p) {
+    const double ang = -s * v[p];
+    T[p] = cd(std::cos(ang), std::sin(ang)) / M;
+  }
+  auto buf = std::make_shared<DevBuf>();
+  upload_c(c, *buf, T);
+  c->ttab[key] = buf;
+  return buf->p;
+}
+
+// Kinetic fixed-point coefficients for one unit of duration u: phase in turns
+// of u |k|^2/2 = u/(4 pi) (m^T G11 m + 2 m^T G12 n + n^T G22 n).
+void set_kinetic(ls_ctx* c, double u) {
+  const int d = c->d;
+  double G11[2][2] = {{0, 0}, {0, 0}}, G12[2][2] = {{0, 0}, {0, 0}}, G22[2][2] = {{0, 0}, {0, 0}};
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b)
+      for (int i = 0; i < d; ++i) {
+        G11[a][b] += c->p.B1[i * d + a] * c->p.B1[i * d + b];
+        G12[a][b] += c->p.B1[i * d + a] * c->p.B2[i * d + b];
+        G22[a][b] += c->p.B2[i * d + a] * c->p.B2[i * d + b];
+      }
+  const double f = u / (4.0 * kPi);
+  for (int L = 0; L < 2; ++L) {
+    lsk::LayerGeom& g = c->geom[L];
+    const double(*Go)[2] = (L == 0) ? G11 : G22;   // own
+    const double(*Gt)[2] = (L == 0) ? G22 : G11;   // other
+    g.A_aa = to_fixed(f * Go[0][0]);
+    g.A_ab = d > 1 ? to_fixed(f * 2.0 * Go[0][1]) : 0;
+    g.A_bb = d > 1 ? to_fixed(f * Go[1][1]) : 0;
+    g.C_aa = to_fixed(f * Gt[0][0]);
+    g.C_ab = d > 1 ? to_fixed(f * 2.0 * Gt[0][1]) : 0;
+    g.C_bb = d > 1 ? to_fixed(f * Gt[1][1]) : 0;
+    // cross term 2 m^T G12 n; own index first
+    auto X = [&](int own, int oth) { return L == 0 ? G12[own][oth] : G12[oth][own]; };
+    g.X_aa = to_fixed(f * 2.0 * X(0, 0));
+    g.X_ab = d > 1 ? to_fixed(f * 2.0 * X(0, 1)) : 0;
+    g.X_ba = d > 1 ? to_fixed(f * 2.0 * X(1, 0)) : 0;
+    g.X_bb = d > 1 ? to_fixed(f * 2.0 * X(1, 1)) : 0;
+  }
+}
+
+// ---------------------------------------------------------------- validation
+int validate(const ls_problem* p) {
+  if (!p) return fail(LS_ERR_INVALID, "problem is NULL");
+  if (p->d != 1 && p->d != 2) return fail(LS_ERR_INVALID, "d must be 1 or 2");
+  if (p->dtype != LS_C64 && p->dtype != LS_C128) return fail(LS_ERR_INVALID, "dtype must be LS_C64 or LS_C128");
+  if (p->frac_den < 1) return fail(LS_ERR_INVALID, "frac_den must be >= 1");
+  for (int i = 0; i < p->d; ++i) {
+    if (p->q1[i] < 1 || p->q2[i] < 1) return fail(LS_ERR_INVALID, "box extents must be >= 1");
+  }
+  if (!(p->ecut >= 0) || !std::isfinite(p->ecut)) return fail(LS_ERR_INVALID, "ecut must be finite and >= 0");
+  for (int i = 0; i < p->d * p->d; ++i)
+    if (!std::isfinite(p->B1[i]) || !std::isfinite(p->B2[i])) return fail(LS_ERR_INVALID, "non-finite lattice");
+  if (p->nv1 < 0 || p->nv2 < 0) return fail(LS_ERR_INVALID, "negative coefficient count");
+  if ((p->nv1 > 0 && (!p->v1_h || !p->v1_c)) || (p->nv2 > 0 && (!p->v2_h || !p->v2_c)))
+    return fail(LS_ERR_INVALID, "coefficient arrays are NULL");
+  for (int L = 0; L < 2; ++L) {
+    const int32_t* q = L == 0 ? p->q1 : p->q2;
+    if (p->d == 1) {
+      const int64_t n = q[0];
+      const int64_t np = is_pow2(n) ? n : (int64_t(1) << log2i(2 * n - 2));
+      if (np > 8192) return fail(LS_ERR_INVALID, "1D slice length too large (transform length > 8192)");
+    } else {
+      if (!is_pow2(q[0]) || !is_pow2(q[1]))
+        return fail(LS_ERR_INVALID, "2D slices need power-of-two extents");
+      if ((int64_t)q[0] * q[1] > 4096) return fail(LS_ERR_INVALID, "2D slice larger than 4096 elements");
+      if (q[0] < 2 || q[1] < 2) return fail(LS_ERR_INVALID, "2D slice extents must be >= 2");
+    }
+  }
+  return LS_OK;
+}
+
+void build_geometry(ls_ctx* c) {
+  const ls_problem& p = c->p;
+  const int d = c->d;
+  for (int L = 0; L < 2; ++L) {
+    lsk::LayerGeom& g = c->geom[L];
+    std::memset(&g, 0, sizeof(g));
+    const int32_t* q = L == 0 ? p.q1 : p.q2;
+    const int32_t* lo = L == 0 ? p.lo1 : p.lo2;
+    const int32_t* oq = L == 0 ? p.q2 : p.q1;
+    const int32_t* olo = L == 0 ? p.lo2 : p.lo1;
+    g.d = d;
+    g.qa = q[0];
+    g.qb = d > 1 ? q[1] : 1;
+    g.M = g.qa * g.qb;
+    g.lo_a = lo[0];
+    g.lo_b = d > 1 ? lo[1] : 0;
+    g.oqa = oq[0];
+    g.olo_a = olo[0];
+    g.olo_b = d > 1 ? olo[1] : 0;
+    g.nslices = L == 0 ? c->M2 : c->M1;
+    if (d == 1) {
+      g.bluestein = is_pow2(g.qa) ? 0 : 1;
+      g.np = g.bluestein ? (1 << log2i(2 * (int64_t)g.qa - 2)) : g.qa;
+      g.npb = 1;
+      g.buf = g.np;
+      g.two_q = 2 * g.qa;
+      g.chirp_unit = g.bluestein ? (uint64_t)(~0ull / (uint64_t)g.two_q) : 0;
+    } else {
+      g.bluestein = 0;
+      g.np = g.qa;
+      g.npb = g.qb;
+      g.buf = g.M;
+    }
+    g.sb = g.buf + (g.buf >> 4) + 1;
+    if (c->dtype == LS_C64 && (g.sb & 1)) g.sb += 1;  // keep 16-byte alignment per slice
+    if (L == 0) {
+      g.slice_stride = c->pitch;
+      g.ea = 1;
+      g.eb = g.qa;
+    } else {
+      g.slice_stride = 1;
+      g.ea = c->pitch;
+      g.eb = (int64_t)p.q2[0] * c->pitch;
+    }
+  }
+}
+
+template <typename Real>
+void choose_launch(ls_ctx* c) {
+  for (int L = 0; L < 2; ++L) {
+    lsk::LayerGeom& g = c->geom[L];
+    int W = L == 0 ? std::max(1, std::min(lsk::kMaxTileSlices, 4096 / g.buf))
+                   : std::max(1, std::min(lsk::kMaxTileSlices, 8192 / g.buf));
+    if (L == 1 && W < 2 && g.nslices > 1) W = 2;
+    if ((int64_t)W > g.nslices) W = (int)g.nslices;
+    int bpt = 2, nt = 0;
+    for (;;) {
+      nt = lsk::pass_threads(g, W, 2);
+      if (nt <= lsk::pass_max_threads<Real>(2)) { bpt = 2; break; }
+      nt = lsk::pass_threads(g, W, 4);
+      if (nt <= lsk::pass_max_threads<Real>(4)) { bpt = 4; break; }
+      if (W == 1) throw CudaError{cudaErrorInvalidValue, "slice too large for one CTA"};
+      W = std::max(1, W / 2);
+    }
+    c->W[L] = W;
+    c->bpt[L] = bpt;
+    c->nt[L] = nt;
+  }
+}
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
+  lsk::PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.g = c->geom[L];
+  a.psi = psi;
+  a.W = c->W[L];
+  a.strided = (L == 1) ? 1 : 0;
+  a.pitch = c->pitch;
+  return a;
+}
+
+cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a, int L, int64_t nitems, cudaStream_t st) {
+  const int64_t ntiles = (nitems + a.W - 1) / a.W;
+  if (c->dtype == LS_C64) return lsk::launch_pass<float>(a, c->bpt[L], c->nt[L], ntiles, st);
+  return lsk::launch_pass<double>(a, c->bpt[L], c->nt[L], ntiles, st);
+}
+
+int base_scheme(int scheme) {
+  if (scheme == LS_LIE_STOCH) return LS_LIE;
+  if (scheme == LS_STRANG_STOCH) return LS_STRANG;
+  return scheme;
+}
+
+// Kinetic unit u and the pass list of nsteps steps (adjacent kinetic factors
+// merged; every kinetic unit is applied exactly once).
+double build_passes(int scheme, double tau, int64_t n, std::vector<PassSpec>& out, int32_t& end_time) {
+  out.clear();
+  const int b = base_scheme(scheme);
+  if (b == LS_LIE) {
+    for (int64_t k = 0; k < n; ++k) {
+      out.push_back({1, tau, 1, 0, (int32_t)(k + 1), 0, k});
+      out.push_back({2, tau, 0, 0, (int32_t)(k + 1), 1, k});
+    }
+    end_time = (int32_t)n;
+    return tau;
+  }
+  if (b == LS_STRANG) {
+    for (int64_t k = 0; k < n; ++k) {
+      out.push_back({1, tau / 2, k == 0 ? 1 : 0, 3, (int32_t)(8 * k + 1), 0, k});
+      out.push_back({2, tau, 0, 3, (int32_t)(8 * k + 4), 1, k});
+      out.push_back({1, tau / 2, 0, k == n - 1 ? 1 : 2, (int32_t)(8 * k + 7), 2, k});
+    }
+    end_time = (int32_t)(8 * n);
+    return tau / 8;
+  }
+  // LS_STRANG_KP
+  for (int64_t k = 0; k < n; ++k) {
+    out.push_back({1, tau, k == 0 ? 1 : 0, 0, (int32_t)(2 * k + 1), 0, k});
+    out.push_back({2, tau, 0, k == n - 1 ? 1 : 2, (int32_t)(2 * k + 1), 1, k});
+  }
+  end_time = (int32_t)(2 * n);
+  return tau / 2;
+}
+
+int factors_per_step(int scheme) { return base_scheme(scheme) == LS_STRANG ? 3 : 2; }
+
+lsk::SamplerArgs sampler_args(ls_ctx* c, int scheme, int& npf) {
+  lsk::SamplerArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.S1 = (int32_t)c->M2;
+  sa.S2 = (int32_t)c->M1;
+  sa.p1 = std::max<int32_t>(1, sa.S1 / c->frac_den);
+  sa.p2 = std::max<int32_t>(1, sa.S2 / c->frac_den);
+  sa.Smax = std::max(sa.S1, sa.S2);
+  sa.pmax = std::max(sa.p1, sa.p2);
+  npf = factors_per_step(scheme);
+  sa.npf = npf;
+  if (base_scheme(scheme) == LS_STRANG) {
+    sa.pattern[0] = 1; sa.pattern[1] = 2; sa.pattern[2] = 1;
+  } else {
+    sa.pattern[0] = 1; sa.pattern[1] = 2;
+  }
+  return sa;
+}
+
+// Enqueue the whole call on stream st (used both for capture and direct runs).
+void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaStream_t st,
+                  DevBuf* lists) {
+  std::vector<PassSpec> ps;
+  int32_t end_time = 0;
+  const double u = build_passes(scheme, tau, n, ps, end_time);
+  set_kinetic(c, u);
+  const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+  int npf = 0;
+  lsk::SamplerArgs sa = sampler_args(c, scheme, npf);
+  if (stoch) {
+    LS_CUDA(lsk::launch_zero_i32((int32_t*)c->touch_row.p, c->M2, st));
+    LS_CUDA(lsk::launch_zero_i32((int32_t*)c->touch_col.p, c->M1, st));
+    LS_CUDA(lsk::launch_sampler(sa, (const uint64_t*)c->seedbuf.p, (int32_t)(n * npf), (int32_t*)lists->p, st));
+  }
+  for (size_t i = 0; i < ps.size(); ++i) {
+    const PassSpec& q = ps[i];
+    const int L = q.layer - 1;
+    const int64_t S = c->geom[L].nslices;
+    const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
+    lsk::PassArgs a = base_args(c, L, psi);
+    if (!stoch) {
+      a.mode = lsk::MODE_STEP;
+      a.T = phase_table(c, q.layer, q.s);
+      a.units_pre = q.pre;
+      a.units_post = q.post;
+      LS_CUDA(launch(c, a, L, S, st));
+    } else {
+      a.mode = lsk::MODE_LAZY;
+      a.T = phase_table(c, q.layer, q.s * (double)S / (double)p);
+      a.list = (const int32_t*)lists->p + (int64_t)i * sa.pmax;
+      a.nlist = p;
+      a.touch_own = (int32_t*)(L == 0 ? c->touch_row.p : c->touch_col.p);
+      a.touch_other = (const int32_t*)(L == 0 ? c->touch_col.p : c->touch_row.p);
+      a.now = q.now;
+      a.strided = 0;                  // sampled columns are scattered
+      a.W = 1;
+      LS_CUDA(launch(c, a, L, p, st));
+    }
+  }
+  if (stoch) {
+    // settle: every element gets its pending kinetic phase up to end_time
+    lsk::PassArgs a = base_args(c, 0, psi);
+    a.mode = lsk::MODE_KIN;
+    a.touch_own = (int32_t*)c->touch_row.p;
+    a.touch_other = (const int32_t*)c->touch_col.p;
+    a.now = end_time;
+    LS_CUDA(launch(c, a, 0, c->geom[0].nslices, st));
+  }
+}
+
+void prepare_tables(ls_ctx* c, int64_t n, double tau, int scheme) {
+  std::vector<PassSpec> ps;
+  int32_t end_time = 0;
+  build_passes(scheme, tau, std::min<int64_t>(n, 2), ps, end_time);
+  const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+  for (const PassSpec& q : ps) {
+    const int64_t S = c->geom[q.layer - 1].nslices;
+    const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
+    phase_table(c, q.layer, stoch ? q.s * (double)S / (double)p : q.s);
+  }
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const CudaError& e) {
+    if (e.e == cudaErrorMemoryAllocation) return fail(LS_ERR_NOMEM, e.where + ": " + cudaGetErrorString(e.e));
+    return fail(LS_ERR_CUDA, e.where + ": " + cudaGetErrorString(e.e));
+  } catch (const std::bad_alloc&) {
+    return fail(LS_ERR_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(LS_ERR_INVALID, e.what());
+  } catch (...) {
+    return fail(LS_ERR_INVALID, "unknown error");
+  }
+}
+
+void elem_args(ls_ctx* c) {
+  lsk::ElemArgs& e = c->ea;
+  std::memset(&e, 0, sizeof(e));
+  e.d = c->d;
+  e.q1a = c->p.q1[0];
+  e.q1b = c->d > 1 ? c->p.q1[1] : 1;
+  e.lo1a = c->p.lo1[0];
+  e.lo1b = c->d > 1 ? c->p.lo1[1] : 0;
+  e.q2a = c->p.q2[0];
+  e.q2b = c->d > 1 ? c->p.q2[1] : 1;
+  e.lo2a = c->p.lo2[0];
+  e.lo2b = c->d > 1 ? c->p.lo2[1] : 0;
+  e.M1 = c->M1;
+  e.M2 = c->M2;
+  e.pitch = c->pitch;
+  for (int i = 0; i < 4; ++i) {
+    e.B1[i] = c->p.B1[i];
+    e.B2[i] = c->p.B2[i];
+  }
+  e.ecut = c->p.ecut;
+}
+
+int64_t reduce_into(ls_ctx* c, int nparts, double* out_dev, cudaStream_t st) {
+  LS_CUDA(lsk::launch_reduce((const double*)c->partials.p, nparts, lsk::kObsQ, out_dev, st));
+  return 0;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* ls_last_error(void) { return g_last_error.c_str(); }
+
+int ls_create(const ls_problem* prob, ls_ctx** out) {
+  g_last_error.clear();
+  if (!out) return fail(LS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int v = validate(prob);
+  if (v != LS_OK) return v;
+  return guarded([&]() -> int {
+    std::unique_ptr<ls_ctx> c(new ls_ctx());
+    c->p = *prob;
+    c->d = prob->d;
+    c->dtype = prob->dtype;
+    c->esize = prob->dtype == LS_C64 ? 8 : 16;
+    c->frac_den = prob->frac_den;
+    c->h1.assign(prob->v1_h, prob->v1_h + (size_t)prob->nv1 * prob->d);
+    c->h2.assign(prob->v2_h, prob->v2_h + (size_t)prob->nv2 * prob->d);
+    c->c1.assign(prob->v1_c, prob->v1_c + 2 * (size_t)prob->nv1);
+    c->c2.assign(prob->v2_c, prob->v2_c + 2 * (size_t)prob->nv2);
+    c->p.v1_h = nullptr; c->p.v1_c = nullptr; c->p.v2_h = nullptr; c->p.v2_c = nullptr;
+    c->M1 = (int64_t)prob->q1[0] * (prob->d > 1 ? prob->q1[1] : 1);
+    c->M2 = (int64_t)prob->q2[0] * (prob->d > 1 ? prob->q2[1] : 1);
+    c->pitch = (c->M1 + 15) / 16 * 16;
+    LS_CUDA(cudaGetDevice(&c->device));
+    build_geometry(c.get());
+    if (c->dtype == LS_C64) choose_launch<float>(c.get());
+    else choose_launch<double>(c.get());
+    for (int L = 0; L < 2; ++L) {
+      lsk::LayerGeom& g = c->geom[L];
+      upload_c(c.get(), c->tw[L], twiddles(g.np));
+      g.tw = c->tw[L].p;
+      if (g.d > 1) {
+        upload_c(c.get(), c->twb[L], twiddles(g.npb));
+        g.twb = c->twb[L].p;
+      }
+      if (g.bluestein) {
+        upload_c(c.get(), c->bm[L], bluestein_kernel(g.qa, g.np, -1.0));
+        upload_c(c.get(), c->bp[L], bluestein_kernel(g.qa, g.np, +1.0));
+        g.bm = c->bm[L].p;
+        g.bp = c->bp[L].p;
+      }
+      c->vhost[L] = grid_potential(L == 0 ? c->h1 : c->h2, L == 0 ? c->c1 : c->c2, c->d,
+                                   L == 0 ? prob->q1 : prob->q2);
+      c->vgrid[L].alloc(c->vhost[L].size() * sizeof(double));
+      LS_CUDA(cudaMemcpy(c->vgrid[L].p, c->vhost[L].data(), c->vhost[L].size() * sizeof(double),
+                         cudaMemcpyHostToDevice));
+      g.vgrid = (const double*)c->vgrid[L].p;
+    }
+    size_t maxsm = 0;
+    for (int L = 0; L < 2; ++L) {
+      const size_t b = c->dtype == LS_C64 ? lsk::pass_smem_bytes<float>(c->geom[L], c->W[L], lsk::MODE_ADJOINT)
+                                          : lsk::pass_smem_bytes<double>(c->geom[L], c->W[L], lsk::MODE_ADJOINT);
+      maxsm = std::max(maxsm, b);
+    }
+    int dev_max = 0;
+    LS_CUDA(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (maxsm > (size_t)dev_max) {
+      // the adjoint needs two tiles; shrink W until it fits
+      for (int L = 0; L < 2; ++L) {
+        while (c->W[L] > 1 && (c->dtype == LS_C64 ? lsk::pass_smem_bytes<float>(c->geom[L], c->W[L], lsk::MODE_ADJOINT)
+                                                   : lsk::pass_smem_bytes<double>(c->geom[L], c->W[L], lsk::MODE_ADJOINT)) > (size_t)dev_max)
+          c->W[L] /= 2;
+      }
+      maxsm = (size_t)dev_max;
+    }
+    if (c->dtype == LS_C64) LS_CUDA(lsk::pass_prepare<float>((size_t)dev_max));
+    else LS_CUDA(lsk::pass_prepare<double>((size_t)dev_max));
+    const size_t smax = (size_t)std::max(c->M1, c->M2) * 5;
+    if (smax > 48 * 1024) LS_CUDA(lsk::sampler_prepare(std::min(smax, (size_t)dev_max)));
+    if (smax > (size_t)dev_max) throw CudaError{cudaErrorInvalidValue, "too many slices for the sampler"};
+    elem_args(c.get());
+    c->nblk_elem = lsk::kReduceBlocks;
+    int64_t tiles = 0;
+    for (int L = 0; L < 2; ++L) tiles = std::max<int64_t>(tiles, (c->geom[L].nslices + c->W[L] - 1) / c->W[L]);
+    c->partial_count = std::max<size_t>((size_t)c->nblk_elem * lsk::kObsQ, (size_t)tiles * lsk::kObsQ);
+    c->partials.alloc(c->partial_count * sizeof(double));
+    c->result.alloc(32 * sizeof(double));
+    c->touch_row.alloc(c->M2 * sizeof(int32_t));
+    c->touch_col.alloc(c->M1 * sizeof(int32_t));
+    c->seedbuf.alloc(2 * sizeof(uint64_t));
+    LS_CUDA(cudaMemset(c->touch_row.p, 0, c->M2 * sizeof(int32_t)));
+    LS_CUDA(cudaMemset(c->touch_col.p, 0, c->M1 * sizeof(int32_t)));
+    LS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    *out = c.release();
+    return LS_OK;
+  });
+}
+
+int ls_destroy(ls_ctx* ctx) {
+  if (!ctx) return LS_OK;
+  return guarded([&]() -> int {
+    cudaDeviceSynchronize();
+    delete ctx;
+    return LS_OK;
+  });
+}
+
+int ls_layout(const ls_ctx* c, int64_t* pitch, int64_t* rows, int64_t* bytes) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (pitch) *pitch = c->pitch;
+  if (rows) *rows = c->M2;
+  if (bytes) *bytes = c->pitch * c->M2 * (int64_t)c->esize;
+  return LS_OK;
+}
+
+int ls_index_set(const ls_ctx* c, uint8_t* mask, int64_t* count) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  const int d = c->d;
+  const ls_problem& p = c->p;
+  int64_t cnt = 0;
+  for (int64_t r = 0; r < c->M2; ++r) {
+    double nv[2] = {(double)(r % p.q2[0] + p.lo2[0]), d > 1 ? (double)(r / p.q2[0] + p.lo2[1]) : 0.0};
+    for (int64_t col = 0; col < c->M1; ++col) {
+      double mv[2] = {(double)(col % p.q1[0] + p.lo1[0]), d > 1 ? (double)(col / p.q1[0] + p.lo1[1]) : 0.0};
+      double sum = 0.0;
+      for (int i = 0; i < d; ++i) {
+        double u = p.B1[i * d + 0] * mv[0];
+        for (int j = 1; j < d; ++j) u = u + p.B1[i * d + j] * mv[j];
+        for (int j = 0; j < d; ++j) u = u + p.B2[i * d + j] * nv[j];
+        const double uu = u * u;
+        sum = (i == 0) ? uu : sum + uu;
+      }
+      const bool in = 0.5 * sum <= p.ecut;
+      if (mask) mask[r * c->M1 + col] = in ? 1 : 0;
+      cnt += in;
+    }
+  }
+  if (count) *count = cnt;
+  return LS_OK;
+}
+
+int ls_init_gaussian(ls_ctx* c, void* psi, const double* x0, double w, const double* k0, void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (!psi || !x0 || !k0) return fail(LS_ERR_INVALID, "NULL argument");
+  if (!(w > 0) || !std::isfinite(w)) return fail(LS_ERR_INVALID, "width must be positive");
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    double* res = (double*)c->result.p;
+    if (c->dtype == LS_C64) {
+      LS_CUDA(lsk::launch_gaussian<float>(c->ea, psi, x0, w, k0, (double*)c->partials.p, c->nblk_elem, st));
+      reduce_into(c, c->nblk_elem, res, st);
+      LS_CUDA(lsk::launch_scale<float>(c->ea, psi, res, st));
+    } else {
+      LS_CUDA(lsk::launch_gaussian<double>(c->ea, psi, x0, w, k0, (double*)c->partials.p, c->nblk_elem, st));
+      reduce_into(c, c->nblk_elem, res, st);
+      LS_CUDA(lsk::launch_scale<double>(c->ea, psi, res, st));
+    }
+    return LS_OK;
+  });
+}
+
+int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_t seed, uint64_t step0,
+            void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
+  if (n < 0) return fail(LS_ERR_INVALID, "nsteps < 0");
+  if (!std::isfinite(tau)) return fail(LS_ERR_INVALID, "tau is not finite");
+  if (scheme < LS_LIE || scheme > LS_STRANG_STOCH) return fail(LS_ERR_INVALID, "unknown scheme");
+  if (n == 0) return LS_OK;
+  if (n > (1 << 26) / 8) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+    if (stoch) {
+      const uint64_t hp[2] = {seed, step0 * (uint64_t)factors_per_step(scheme)};
+      // pageable source: staged before the call returns, safe to reuse
+      LS_CUDA(cudaMemcpyAsync(c->seedbuf.p, hp, sizeof(hp), cudaMemcpyHostToDevice, st));
+    }
+    GraphEntry* ge = nullptr;
+    for (auto it = c->graphs.begin(); it != c->graphs.end(); ++it) {
+      GraphEntry* e = it->get();
+      if (e->psi == psi && e->scheme == scheme && e->tau == tau && e->n == n) {
+        ge = e;
+        c->graphs.splice(c->graphs.begin(), c->graphs, it);
+        break;
+      }
+    }
+    if (!ge) {
+      std::unique_ptr<GraphEntry> e(new GraphEntry());
+      e->psi = psi;
+      e->scheme = scheme;
+      e->tau = tau;
+      e->n = n;
+      e->lists = std::make_shared<DevBuf>();
+      if (stoch) {
+        int npf = 0;
+        lsk::SamplerArgs sa = sampler_args(c, scheme, npf);
+        e->lists->alloc((size_t)n * npf * sa.pmax * sizeof(int32_t));
+      }
+      // Tables are built (and uploaded) before capture: no allocation or
+      // synchronous copy may happen while the stream is being captured.
+      prepare_tables(c, n, tau, scheme);
+      cudaGraph_t graph = nullptr;
+      LS_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+      try {
+        enqueue_step(c, psi, n, tau, scheme, c->cap, e->lists.get());
+      } catch (...) {
+        cudaStreamEndCapture(c->cap, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      LS_CUDA(cudaStreamEndCapture(c->cap, &graph));
+      cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) throw CudaError{ie, "cudaGraphInstantiate"};
+      c->graphs.push_front(std::move(e));
+      while (c->graphs.size() > 8) c->graphs.pop_back();
+      ge = c->graphs.front().get();
+    }
+    LS_CUDA(cudaGraphLaunch(ge->exec, st));
+    return LS_OK;
+  });
+}
+
+int ls_observables(ls_ctx* c, const void* psi, const void* chi, ls_obs* out, void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (!psi || !out) return fail(LS_ERR_INVALID, "NULL argument");
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    double* res = (double*)c->result.p;
+    if (c->dtype == LS_C64) LS_CUDA(lsk::launch_elem_obs<float>(c->ea, psi, chi, (double*)c->partials.p, c->nblk_elem, st));
+    else LS_CUDA(lsk::launch_elem_obs<double>(c->ea, psi, chi, (double*)c->partials.p, c->nblk_elem, st));
+    reduce_into(c, c->nblk_elem, res, st);
+    for (int L = 0; L < 2; ++L) {
+      lsk::PassArgs a = base_args(c, L, const_cast<void*>(psi));
+      a.mode = lsk::MODE_MEASURE;
+      a.partials = (double*)c->partials.p;
+      const int64_t ntiles = (c->geom[L].nslices + a.W - 1) / a.W;
+      LS_CUDA(launch(c, a, L, c->geom[L].nslices, st));
+      LS_CUDA(lsk::launch_reduce((const double*)c->partials.p, (int)ntiles, 1, res + 8 + L, st));
+    }
+    double h[10];
+    LS_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaStreamSynchronize(st));
+    out->norm = h[0];
+    out->ekin = h[1];
+    out->kmean[0] = h[2];
+    out->kmean[1] = c->d > 1 ? h[3] : 0.0;
+    out->overlap_re = chi ? h[4] : 0.0;
+    out->overlap_im = chi ? h[5] : 0.0;
+    out->epot1 = h[8];
+    out->epot2 = h[9];
+    out->energy = out->ekin + out->epot1 + out->epot2;
+    return LS_OK;
+  });
+}
+
+int ls_samples(ls_ctx* c, int32_t layer, uint64_t seed, uint64_t g0, int32_t count, int32_t* out,
+               int32_t* p_out, void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (layer != 1 && layer != 2) return fail(LS_ERR_INVALID, "layer must be 1 or 2");
+  if (count < 0 || (count > 0 && !out)) return fail(LS_ERR_INVALID, "bad output");
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    int npf = 0;
+    lsk::SamplerArgs sa = sampler_args(c, LS_LIE, npf);
+    sa.npf = 1;
+    sa.pattern[0] = layer;
+    sa.seed = seed;
+    sa.g0 = g0;
+    const int32_t p = layer == 1 ? sa.p1 : sa.p2;
+    if (p_out) *p_out = p;
+    if (count == 0) return LS_OK;
+    DevBuf tmp;
+    tmp.alloc((size_t)count * sa.pmax * sizeof(int32_t));
+    LS_CUDA(lsk::launch_sampler(sa, nullptr, count, (int32_t*)tmp.p, st));
+    std::vector<int32_t> h((size_t)count * sa.pmax);
+    LS_CUDA(cudaMemcpyAsync(h.data(), tmp.p, h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaStreamSynchronize(st));
+    for (int32_t i = 0; i < count; ++i)
+      std::memcpy(out + (size_t)i * p, h.data() + (size_t)i * sa.pmax, (size_t)p * sizeof(int32_t));
+    return LS_OK;
+  });
+}
+
+int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t scheme, double* gv1, double* gv2,
+               double* gc1, double* gc2, void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (!psi || !lam || !gv1 || !gv2) return fail(LS_ERR_INVALID, "NULL argument");
+  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP)
+    return fail(LS_ERR_INVALID, "adjoint supports the deterministic schemes only");
+  if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    for (int L = 0; L < 2; ++L) {
+      const int64_t M = L == 0 ? c->M1 : c->M2;
+      if (c->grad[L].bytes < (size_t)M * sizeof(double)) c->grad[L].alloc((size_t)M * sizeof(double));
+      LS_CUDA(lsk::launch_zero_f64((double*)c->grad[L].p, M, st));
+    }
+    std::vector<PassSpec> ps;
+    int32_t end_time = 0;
+    const double u = build_passes(scheme, tau, n, ps, end_time);
+    set_kinetic(c, u);
+    for (size_t i = ps.size(); i-- > 0;) {
+      const PassSpec& q = ps[i];
+      const int L = q.layer - 1;
+      lsk::PassArgs a = base_args(c, L, psi);
+      a.mode = lsk::MODE_ADJOINT;
+      a.lam = lam;
+      a.T = phase_table(c, q.layer, -q.s);
+      a.units_pre = -q.post;
+      a.units_post = -q.pre;
+      a.grad = (double*)c->grad[L].p;
+      a.sdur = q.s;
+      LS_CUDA(launch(c, a, L, c->geom[L].nslices, st));
+    }
+    LS_CUDA(cudaMemcpyAsync(gv1, c->grad[0].p, c->M1 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaMemcpyAsync(gv2, c->grad[1].p, c->M2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaStreamSynchronize(st));
+    // chain rule to the Fourier coefficients: v_p = Re sum_h c_h e^{2 pi i h.p/q}
+    for (int L = 0; L < 2; ++L) {
+      double* gc = L == 0 ? gc1 : gc2;
+      if (!gc) continue;
+      const double* gv = L == 0 ? gv1 : gv2;
+      const std::vector<int32_t>& h = L == 0 ? c->h1 : c->h2;
+      const int32_t* q = L == 0 ? c->p.q1 : c->p.q2;
+      const int d = c->d;
+      const size_t nh = h.size() / d;
+      const int64_t M = L == 0 ? c->M1 : c->M2;
+      for (size_t t = 0; t < nh; ++t) {
+        double re = 0, im = 0;
+        for (int64_t p = 0; p < M; ++p) {
+          const int64_t pa = p % q[0], pb = p / q[0];
+          int64_t ra = (((int64_t)h[t * d] * pa) % q[0] + q[0]) % q[0];
+          double ang = 2.0 * kPi * (double)ra / (double)q[0];
+          if (d > 1) {
+            int64_t rb = (((int64_t)h[t * d + 1] * pb) % q[1] + q[1]) % q[1];
+            ang += 2.0 * kPi * (double)rb / (double)q[1];
+          }
+          re += gv[p] * std::cos(ang);
+          im -= gv[p] * std::sin(ang);
+        }
+        gc[2 * t] = re;
+        gc[2 * t + 1] = im;
+      }
+    }
+    return LS_OK;
+  });
+}
+
+}  // extern "C"

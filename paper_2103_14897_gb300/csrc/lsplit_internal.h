@@ -1,0 +1,109 @@
+// Internal interface between the host library (lsplit_host.cpp) and the CUDA
+// kernels (lsplit_kernels.cu).  Not part of the public C ABI.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+namespace lsk {
+
+constexpr int kMaxTileSlices = 64;   // W: slices per CTA (upper bound)
+constexpr int kMaxThreads = 1024;
+
+// Geometry of one layer's slice passes (P_j acts along layer j's index).
+// Fixed-point coefficients are in units of 2^-64 turns per kinetic unit.
+struct LayerGeom {
+  int d;              // 1 or 2 (slice dimensionality)
+  int qa, qb;         // slice extents (qb = 1 in 1D)
+  int M;              // qa * qb
+  int np;             // FFT length along a (Bluestein length if bluestein)
+  int npb;            // FFT length along b (2D), 1 in 1D
+  int bluestein;      // 1: 1D slice with q not a power of two
+  int buf;            // logical slice buffer length (np in 1D, M in 2D)
+  int sb;             // padded slice buffer length in SMEM (elements)
+  int64_t nslices;    // number of slices (= size of the other layer's box)
+  int64_t slice_stride;  // global element offset between consecutive slices
+  int64_t ea, eb;     // global element strides along a and b
+  int lo_a, lo_b;     // own box lower bounds: signed index = lo + i
+  int oqa, olo_a, olo_b;  // other box: slice index s -> (s % oqa + olo_a, s / oqa + olo_b)
+  uint64_t A_aa, A_ab, A_bb;           // own quadratic form
+  uint64_t X_aa, X_ab, X_ba, X_bb;     // cross: l_a = X_aa nu_a + X_ab nu_b, l_b = X_ba nu_a + X_bb nu_b
+  uint64_t C_aa, C_ab, C_bb;           // other quadratic form
+  uint64_t chirp_unit;  // floor(2^64 / (2 q)) (Bluestein chirp in turns)
+  int two_q;
+  const void* tw;     // np twiddles exp(-2 pi i x / np)
+  const void* twb;    // npb twiddles (2D)
+  const void* bm;     // Bluestein: FFT_np(b-) / np, b-_j = exp(-i pi j^2 / q)
+  const void* bp;     // Bluestein: FFT_np(b+) / np
+  const double* vgrid;  // v_j(x_p), FP64, M entries
+};
+
+enum PassMode { MODE_STEP = 0, MODE_MEASURE = 1, MODE_ADJOINT = 2, MODE_LAZY = 3, MODE_KIN = 4 };
+
+struct PassArgs {
+  LayerGeom g;
+  void* psi;
+  void* lam;               // adjoint: lambda array (same layout)
+  const void* T;           // exp(-i s v_j(x_p)) / M, M entries (complex Real)
+  int64_t units_pre;       // kinetic units before P (MODE_STEP / MODE_ADJOINT)
+  int64_t units_post;      // kinetic units after P
+  int W;                   // slices per CTA
+  int strided;             // 1: slice index fastest in global access
+  int mode;
+  int64_t pitch;           // row pitch (elements), for touch decoding
+  // lazy stochastic mode
+  const int32_t* list;     // sampled slice indices for this sub-step (sorted)
+  int32_t nlist;
+  int32_t* touch_own;      // last kinetic time of own-layer slices (rows for layer 1)
+  const int32_t* touch_other;  // last kinetic time of the other layer's slices
+  int32_t now;             // kinetic time (units) at which P acts
+  // measure / adjoint outputs
+  double* partials;        // per-CTA partial sums (MODE_MEASURE)
+  double* grad;            // M doubles (MODE_ADJOINT), accumulated atomically
+  double sdur;             // duration s of the factor (MODE_ADJOINT)
+};
+
+struct ElemArgs {          // elementwise kernels over the whole lifted box
+  int d;
+  int q1a, q1b, lo1a, lo1b;   // layer-1 box
+  int q2a, q2b, lo2a, lo2b;   // layer-2 box
+  int64_t M1, M2, pitch;
+  double B1[4], B2[4];
+  double ecut;
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+// BPT: butterflies per thread per radix-4 stage (2 or 4); nthreads from
+// pass_threads().  MODE_KIN (settle) runs the pass kernel without transforms.
+template <typename Real> cudaError_t launch_pass(const PassArgs& a, int bpt, int nthreads,
+                                                 int64_t ntiles, cudaStream_t st);
+template <typename Real> size_t pass_smem_bytes(const LayerGeom& g, int W, int mode);
+template <typename Real> cudaError_t pass_prepare(size_t max_smem);
+int pass_threads(const LayerGeom& g, int W, int bpt);
+template <typename Real> cudaError_t launch_gaussian(const ElemArgs& e, void* psi, const double* x0,
+                                                     double w, const double* k0, double* partials,
+                                                     int nblocks, cudaStream_t st);
+template <typename Real> cudaError_t launch_scale(const ElemArgs& e, void* psi, const double* sumsq,
+                                                  cudaStream_t st);
+template <typename Real> cudaError_t launch_elem_obs(const ElemArgs& e, const void* psi,
+                                                     const void* chi, double* partials, int nblocks,
+                                                     cudaStream_t st);
+cudaError_t launch_reduce(const double* partials, int nparts, int nq, double* out, cudaStream_t st);
+// Stochastic slice sampler: block b draws the sample of sub-step g0 + b, whose
+// layer is pattern[b % npf].  seed/g0 come from seed_g0_dev[0..1] when that
+// pointer is not NULL (so a captured graph can be replayed with new seeds).
+struct SamplerArgs {
+  int32_t S1, p1, S2, p2, Smax, pmax, npf;
+  int32_t pattern[4];
+  uint64_t seed, g0;
+};
+cudaError_t launch_sampler(const SamplerArgs& sa, const uint64_t* seed_g0_dev, int32_t count,
+                           int32_t* out, cudaStream_t st);
+cudaError_t sampler_prepare(size_t smem);
+template <typename Real> int pass_max_threads(int bpt);
+cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
+cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
+
+constexpr int kObsQ = 8;   // norm, ekin, k0, k1, ovl_re, ovl_im, spare, spare
+constexpr int kReduceBlocks = 1024;
+
+}  // namespace lsk

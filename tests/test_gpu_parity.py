@@ -1,0 +1,286 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (the arithmetic is complex64 with FP64-derived tables and exact
+fixed-point kinetic phases, or complex128):
+  * complex64: rel-L2 <= 1e-5 after one step, <= 1e-4 after 1000 steps,
+    | ||psi|| - 1 | <= 1e-5;
+  * complex128: rel-L2 <= 1e-11;
+  * integer work (index set, slice samples): bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL1 = {"c64": 1e-5, "c128": 1e-11}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_14897_gb300 import build as B
+    B.build()
+    import paper_2103_14897_gb300 as P
+    P.load_library()
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def problems_1d():
+    return [
+        W.bilayer_1d(8, 8, 1.3, 0.9, ecut=1e9),          # q = 17 (Bluestein 32)
+        W.bilayer_1d(16, 5, 1.3, 0.9, ecut=1e9),         # q = 33 x 11
+        W.config_small_1d(),                              # 65 x 65
+        W.bilayer_1d(64, 40, 0.7, 1.9, ecut=1e9).with_potentials(  # even lengths 128 x 81
+            v1_h=[[1], [-1], [3], [-3]], v1_c=[0.5, 0.5, 0.2 + 0.1j, 0.2 - 0.1j]),
+        W.Problem(1, np.array([[2 * np.pi]]), np.array([[2 * np.pi / W.GOLDEN]]), (-32,), (64,),
+                  (-16,), (32,), 1e9, np.array([[1], [-1]]), np.array([0.6, 0.6], dtype=complex),
+                  np.array([[2], [-2]]), np.array([0.3j, -0.3j]), "pow2-64x32"),
+        W.bilayer_1d(256, 12, 1.0, 1.4, ecut=1e9),       # q = 513 (Bluestein 1024)
+    ]
+
+
+def problems_2d():
+    return [W.twisted_2d(q=8, hmax=2), W.twisted_2d(q=16, hmax=3)]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_index_set_bit_exact(P, dtype):
+    for p in [W.config_small_1d(), W.config_scale_1d(), W.twisted_2d(q=16, ecut=50.0),
+              W.bilayer_1d(40, 33, ecut=731.25, L2=0.37)]:
+        ctx = P.Context(p, dtype)
+        mask, cnt = ctx.index_set()
+        ref = O.index_mask(p)
+        assert cnt == int(ref.sum())
+        assert np.array_equal(mask, ref)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_gaussian_initial_state(P, dtype):
+    for p, x0, k0 in [(W.config_small_1d(), [0.0], [1.0]), (W.config_small_1d(), [0.3], [-2.0]),
+                      (W.twisted_2d(q=8, ecut=30.0), [0.1, -0.2], [1.0, 0.0])]:
+        ctx = P.Context(p, dtype)
+        psi = ctx.empty()
+        ctx.init_gaussian(psi, x0, 2.0, k0)
+        got = ctx.to_dense(psi)
+        ref = O.gaussian_packet(p, x0, 2.0, k0)
+        assert rel(got, ref) < TOL1[dtype]
+        assert np.all(got[~O.index_mask(p)] == 0)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
+def test_step_parity_1d(P, dtype, scheme):
+    for p in problems_1d():
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 1)
+        psi = ctx.from_dense(x)
+        for n, tau in [(1, 1e-3), (3, 2e-2)]:
+            psi = ctx.from_dense(x)
+            ctx.step(psi, n, tau, scheme)
+            got = ctx.to_dense(psi)
+            ref = O.step(p, x, tau, scheme, n)
+            assert rel(got, ref) < TOL1[dtype] * (1 if n == 1 else 3), (p.name, n, rel(got, ref))
+            assert np.all(psi[:, p.M1:].cpu().numpy() == 0)   # padding untouched
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
+def test_step_parity_2d(P, dtype, scheme):
+    for p in problems_2d():
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 2)
+        psi = ctx.from_dense(x)
+        ctx.step(psi, 2, 5e-3, scheme)
+        ref = O.step(p, x, 5e-3, scheme, 2)
+        assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, p.name
+
+
+def test_large_kinetic_phase_free_particle(P):
+    """V = 0 at the 2049-box extremes: every element must be the exact phase
+    exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
+    p = W.bilayer_1d(1024, 1024, 0.0, 0.0, ecut=1e12)
+    ctx = P.Context(p, "c64")
+    x = W.random_state((p.M2, p.M1), 3)
+    psi = ctx.from_dense(x)
+    ctx.step(psi, 4, 5e-4, "strang")
+    kin = O.kinetic_energy_diag(p)
+    ref = x * np.exp(-1j * (4 * 5e-4) * kin)
+    assert rel(ctx.to_dense(psi), ref) < 2e-6
+
+
+def test_observables_parity(P):
+    for p in [W.config_small_1d(), W.bilayer_1d(16, 5, 1.3, 0.9, ecut=1e9), W.twisted_2d(q=8, hmax=2)]:
+        for dtype, tol in (("c64", 1e-6), ("c128", 1e-12)):
+            ctx = P.Context(p, dtype)
+            x = W.random_state((p.M2, p.M1), 4)
+            chi = W.random_state((p.M2, p.M1), 5)
+            o = ctx.observables(ctx.from_dense(x), ctx.from_dense(chi))
+            r = O.observables(p, x.astype(np.complex64).astype(np.complex128) if dtype == "c64" else x,
+                              chi.astype(np.complex64).astype(np.complex128) if dtype == "c64" else chi)
+            scale = max(1.0, abs(r["energy"]))
+            for k in ("norm", "ekin", "epot1", "epot2", "energy"):
+                assert abs(o[k] - r[k]) < tol * max(1.0, abs(r[k])) * 10, (p.name, dtype, k, o[k], r[k])
+            for i in range(p.d):
+                assert abs(o["kmean"][i] - r["kmean"][i]) < tol * scale * 10
+            assert abs(o["overlap"] - r["overlap"]) < tol * 10
+
+
+def test_stochastic_samples_bit_exact(P):
+    for p in [W.config_small_1d(), W.config_scale_1d(), W.bilayer_1d(16, 5, ecut=1e9)]:
+        ctx = P.Context(p, "c64")
+        for layer in (1, 2):
+            S = p.M2 if layer == 1 else p.M1
+            got = ctx.samples(layer, seed=7, g0=11, count=5)
+            for i in range(5):
+                ref = O.sample_slices(S, O.sample_count(S), 7, 11 + i)
+                assert np.array_equal(got[i], ref)
+
+
+@pytest.mark.parametrize("scheme", ["lie_stoch", "strang_stoch"])
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_stochastic_step_parity(P, scheme, dtype):
+    for p in [W.bilayer_1d(16, 20, 1.3, 0.9, ecut=1e9), W.config_small_1d(), W.twisted_2d(q=8, hmax=2)]:
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 6)
+        psi = ctx.from_dense(x)
+        ctx.step(psi, 3, 1e-2, scheme, seed=5, step0=2)
+        ref = O.step(p, x, 1e-2, scheme, 3, seed=5, step0=2)
+        assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, (p.name, rel(ctx.to_dense(psi), ref))
+        # second call continues the sample sequence
+        ctx.step(psi, 2, 1e-2, scheme, seed=5, step0=5)
+        ref = O.step(p, ref, 1e-2, scheme, 2, seed=5, step0=5)
+        assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 5
+
+
+def test_full_sampling_equals_deterministic(P):
+    p = W.bilayer_1d(16, 20, 1.3, 0.9, ecut=1e9)
+    c1 = P.Context(p, "c128", frac_den=1)
+    x = W.random_state((p.M2, p.M1), 7)
+    a = c1.from_dense(x)
+    b = c1.from_dense(x)
+    c1.step(a, 3, 1e-2, "strang_stoch", seed=1)
+    c1.step(b, 3, 1e-2, "strang")
+    assert rel(c1.to_dense(a), c1.to_dense(b)) < 1e-13
+
+
+def test_full_size_one_step_c64(P):
+    """2049 x 2049 box (seeded U(0.5, 2) amplitudes), one Strang step of
+    tau = 5e-4 from the Gaussian packet, against the oracle (FFT backend)."""
+    p = W.config_scale_1d()
+    ctx = P.Context(p, "c64")
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
+    x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+    ctx.step(psi, 1, 5e-4, "strang")
+    O.use_fft(True)
+    try:
+        ref = O.step(p, x, 5e-4, "strang", 1)
+    finally:
+        O.use_fft(False)
+    got = ctx.to_dense(psi)
+    assert rel(got, ref) < 1e-5
+    assert abs(np.linalg.norm(got) - 1) < 1e-5
+
+
+def test_full_size_random_state_c64(P):
+    """Same box with a dense random state (every element significant)."""
+    p = W.config_scale_1d()
+    ctx = P.Context(p, "c64")
+    x = W.random_state((p.M2, p.M1), 8)
+    psi = ctx.from_dense(x)
+    ctx.step(psi, 2, 5e-4, "strang")
+    O.use_fft(True)
+    try:
+        ref = O.step(p, x, 5e-4, "strang", 2)
+    finally:
+        O.use_fft(False)
+    assert rel(ctx.to_dense(psi), ref) < 2e-5
+
+
+def test_long_run_1000_steps(P):
+    """65 x 65, tau = 1e-3, 1000 Strang steps in complex64: rel-L2 <= 1e-4 and
+    norm drift <= 1e-5 against the FP64 oracle."""
+    p = W.config_small_1d()
+    ctx = P.Context(p, "c64")
+    x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+    psi = ctx.from_dense(x)
+    ctx.step(psi, 1000, 1e-3, "strang")
+    ref = O.step(p, x, 1e-3, "strang", 1000)
+    got = ctx.to_dense(psi)
+    assert rel(got, ref) < 1e-4
+    assert abs(np.linalg.norm(got) - 1) < 1e-5
+
+
+def test_fp64_config_small_100_steps(P):
+    """65 x 65 in complex128, 100 Strang steps of 1e-3 (the small FP64 workload)."""
+    p = W.config_small_1d()
+    ctx = P.Context(p, "c128")
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
+    ctx.step(psi, 100, 1e-3, "strang")
+    ref = O.step(p, O.gaussian_packet(p, [0.0], 2.0, [1.0]), 1e-3, "strang", 100)
+    assert rel(ctx.to_dense(psi), ref) < 1e-11
+
+
+def test_twisted_64_slices_one_step(P):
+    """64^4 lifted box (twisted squares, 3 Gaussian wells per layer): one
+    Strang step, compared on sampled output rows computed by the oracle... the
+    step mixes all rows, so the oracle runs the full step with its FFT backend."""
+    p = W.twisted_2d(q=64)
+    ctx = P.Context(p, "c64")
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0, 0.0], 2.0, [1.0, 0.0])
+    x = ctx.to_dense(psi)
+    ctx.step(psi, 1, 1e-3, "strang")
+    O.use_fft(True)
+    try:
+        ref = O.step(p, x, 1e-3, "strang", 1)
+    finally:
+        O.use_fft(False)
+    assert rel(ctx.to_dense(psi), ref) < 1e-5
+
+
+def test_adjoint_parity(P):
+    th1 = np.array([0.6, -0.3, 0.2])
+    th2 = np.array([0.4, 0.25])
+    base = W.bilayer_1d(16, 12, 0.0, 0.0, ecut=1e9)
+    h1, c1 = W.cos_series_coeffs(th1)
+    h2, c2 = W.cos_series_coeffs(th2)
+    p = base.with_potentials(c1, c2, h1, h2)
+    phi0 = O.gaussian_packet(p, [0.0], 0.8, [1.0])
+    chi = O.gaussian_packet(p, [0.3], 0.8, [1.2])
+    for scheme in ("strang", "lie", "strang_kp"):
+        L, phiT, g1, g2 = O.adjoint(p, phi0, 0.02, scheme, 6, lambda f: O.overlap_loss(chi, f))
+        for dtype, tol in (("c64", 2e-5), ("c128", 1e-10)):
+            ctx = P.Context(p, dtype)
+            psi = ctx.from_dense(phiT)
+            lam = ctx.from_dense(O.overlap_loss(chi, phiT)[1])
+            gg1, gg2, gc1, gc2 = ctx.adjoint(psi, lam, 6, 0.02, scheme)
+            sc = max(np.abs(g1).max(), np.abs(g2).max())
+            assert np.abs(gg1 - g1).max() < tol * sc * 10, (scheme, dtype)
+            assert np.abs(gg2 - g2).max() < tol * sc * 10, (scheme, dtype)
+            assert rel(ctx.to_dense(psi), phi0) < tol * 10
+            cg = O.coefficient_gradient(g1, h1, p.q1)
+            assert np.abs(gc1 - cg).max() < tol * max(1, np.abs(cg).max()) * 10
+
+
+def test_error_codes(P):
+    p = W.config_small_1d()
+    ctx = P.Context(p, "c64")
+    psi = ctx.empty()
+    with pytest.raises(P.LsplitError) as e:
+        ctx.step(psi, -1, 1e-3, "strang")
+    assert e.value.code == P.LS_ERR_INVALID
+    with pytest.raises(P.LsplitError):
+        ctx.step(psi, 1, float("nan"), "strang")
+    with pytest.raises(P.LsplitError):
+        ctx.adjoint(psi, psi, 1, 1e-3, "strang_stoch")

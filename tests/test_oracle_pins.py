@@ -476,3 +476,20 @@ def test_2d_free_particle_and_mass():
     np.testing.assert_allclose(out, np.exp(-0.5j * 0.009 * (k ** 2).sum(-1)) * phi0, atol=1e-12)
     out = O.step(p, phi0, 0.003, "strang", 3)
     assert abs(np.linalg.norm(out) - 1) < 1e-13
+
+
+def test_fft_backend_equals_dense_definition():
+    """The NumPy-FFT backend (used for full-size parity) computes the same
+    transforms as the dense DFT matrices of the definition."""
+    for p in (W.bilayer_1d(16, 13, 1.1, 0.6, ecut=1e9), W.twisted_2d(q=4, hmax=1)):
+        x = W.random_state((p.M2, p.M1), 40)
+        ref = O.step(p, x, 0.01, "strang", 3)
+        ob = O.observables(p, x)
+        try:
+            O.use_fft(True)
+            got = O.step(p, x, 0.01, "strang", 3)
+            og = O.observables(p, x)
+        finally:
+            O.use_fft(False)
+        np.testing.assert_allclose(got, ref, atol=1e-13)
+        assert abs(og["energy"] - ob["energy"]) < 1e-12
