@@ -39,7 +39,7 @@ def _run(cmd):
 
 def sources():
     return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))
-            if f.endswith((".cu", ".cpp", ".h"))] + [os.path.join(ROOT, "include", "lsplit.h")]
+            if f.endswith((".cu", ".cuh", ".cpp", ".h"))] + [os.path.join(ROOT, "include", "lsplit.h")]
 
 
 def up_to_date() -> bool:
@@ -57,23 +57,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
-    ko = os.path.join(BUILD, "lsplit_kernels.o")
+    objs, jobs = [], []
+    for cu in ("lsplit_f32.cu", "lsplit_f64.cu", "lsplit_misc.cu"):
+        o = os.path.join(BUILD, cu.replace(".cu", ".o"))
+        objs.append(o)
+        jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                     "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", os.path.join(CSRC, cu), "-o", o])
     ho = os.path.join(BUILD, "lsplit_host.o")
-    jobs = [
-        [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-         "-Xptxas", "-v" if verbose else "-O3", *inc, "-c",
-         os.path.join(CSRC, "lsplit_kernels.cu"), "-o", ko],
-        ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
-         "-I", os.path.join(cuda, "include"), *inc, "-c",
-         os.path.join(CSRC, "lsplit_host.cpp"), "-o", ho],
-    ]
-    with ThreadPoolExecutor(2) as ex:
+    objs.append(ho)
+    jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+                 "-I", os.path.join(cuda, "include"), *inc, "-c",
+                 os.path.join(CSRC, "lsplit_host.cpp"), "-o", ho])
+    with ThreadPoolExecutor(len(jobs)) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:
         for o in outs:
             sys.stdout.write(o)
     tmp = LIB + ".tmp"
-    _run([nvcc, *ARCH, "-shared", "-cudart", "static", ko, ho, "-o", tmp])
+    _run([nvcc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp])
     os.replace(tmp, LIB)
     return LIB
 

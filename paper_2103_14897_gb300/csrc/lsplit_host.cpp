@@ -19,6 +19,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <map>
@@ -153,7 +154,8 @@ struct ls_ctx {
   int frac_den = 8;
   lsk::LayerGeom geom[2]{};
   int W[2] = {1, 1}, bpt[2] = {2, 2}, nt[2] = {64, 64};
-  DevBuf tw[2], twb[2], bm[2], bp[2], vgrid[2];
+  int fastW[2] = {0, 0};  // slices per CTA of the fast 1D pass (0: not applicable)
+  DevBuf tw[2], twb[2], bm[2], bp[2], chirp[2], vgrid[2];
   std::vector<double> vhost[2];
   std::map<std::pair<int, uint64_t>, std::shared_ptr<DevBuf>> ttab;  // (layer, bits(s)) -> table
   DevBuf partials, result, touch_row, touch_col, seedbuf, grad[2];
@@ -244,10 +246,11 @@ const void* phase_table(ls_ctx* c, int layer, double s) {
   if (it != c->ttab.end()) return it->second->p;
   const std::vector<double>& v = c->vhost[layer - 1];
   const double M = (double)v.size();
+  // (exp(-i s v) - 1) / M = -2 i sin(s v / 2) exp(-i s v / 2) / M (no cancellation)
   std::vector<cd> T(v.size());
   for (size_t p = 0; p < v.size(); ++p) {
-    const double ang = -s * v[p];
-    T[p] = cd(std::cos(ang), std::sin(ang)) / M;
+    const double h = -0.5 * s * v[p];
+    T[p] = cd(0.0, 2.0 * std::sin(h)) * cd(std::cos(h), std::sin(h)) / M;
   }
   auto buf = std::make_shared<DevBuf>();
   upload_c(c, *buf, T);
@@ -343,8 +346,6 @@ void build_geometry(ls_ctx* c) {
       g.np = g.bluestein ? (1 << log2i(2 * (int64_t)g.qa - 2)) : g.qa;
       g.npb = 1;
       g.buf = g.np;
-      g.two_q = 2 * g.qa;
-      g.chirp_unit = g.bluestein ? (uint64_t)(~0ull / (uint64_t)g.two_q) : 0;
     } else {
       g.bluestein = 0;
       g.np = g.qa;
@@ -390,6 +391,11 @@ void choose_launch(ls_ctx* c) {
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+bool getenv_flag(const char* name) {
+  const char* v = std::getenv(name);
+  return v && v[0] && v[0] != '0';
+}
+
 lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
   lsk::PassArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -401,7 +407,16 @@ lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
   return a;
 }
 
-cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a, int L, int64_t nitems, cudaStream_t st) {
+cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a0, int L, int64_t nitems, cudaStream_t st) {
+  if (c->fastW[L] > 0 && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
+    lsk::PassArgs a = a0;
+    a.W = c->fastW[L];
+    a.strided = (L == 1) ? 1 : 0;
+    const int64_t ntiles = (nitems + a.W - 1) / a.W;
+    if (c->dtype == LS_C64) return lsk::launch_fast<float>(a, ntiles, st);
+    return lsk::launch_fast<double>(a, ntiles, st);
+  }
+  const lsk::PassArgs& a = a0;
   const int64_t ntiles = (nitems + a.W - 1) / a.W;
   if (c->dtype == LS_C64) return lsk::launch_pass<float>(a, c->bpt[L], c->nt[L], ntiles, st);
   return lsk::launch_pass<double>(a, c->bpt[L], c->nt[L], ntiles, st);
@@ -616,6 +631,14 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
         upload_c(c.get(), c->bp[L], bluestein_kernel(g.qa, g.np, +1.0));
         g.bm = c->bm[L].p;
         g.bp = c->bp[L].p;
+        std::vector<cd> ch(g.qa);
+        for (int i = 0; i < g.qa; ++i) {
+          const int64_t r = ((int64_t)i * i) % (2 * (int64_t)g.qa);
+          const double ang = kPi * (double)r / (double)g.qa;
+          ch[i] = cd(std::cos(ang), std::sin(ang));
+        }
+        upload_c(c.get(), c->chirp[L], ch);
+        g.chirp = c->chirp[L].p;
       }
       c->vhost[L] = grid_potential(L == 0 ? c->h1 : c->h2, L == 0 ? c->c1 : c->c2, c->d,
                                    L == 0 ? prob->q1 : prob->q2);
@@ -632,6 +655,8 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     }
     int dev_max = 0;
     LS_CUDA(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const size_t static_reserve = 4096;  // the pass kernel's static shared memory
+    dev_max -= (int)static_reserve;
     if (maxsm > (size_t)dev_max) {
       // the adjoint needs two tiles; shrink W until it fits
       for (int L = 0; L < 2; ++L) {
@@ -641,10 +666,25 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
       }
       maxsm = (size_t)dev_max;
     }
-    if (c->dtype == LS_C64) LS_CUDA(lsk::pass_prepare<float>((size_t)dev_max));
-    else LS_CUDA(lsk::pass_prepare<double>((size_t)dev_max));
+    const size_t block_max = (size_t)dev_max + static_reserve;
+    if (c->dtype == LS_C64) LS_CUDA(lsk::pass_prepare<float>(block_max));
+    else LS_CUDA(lsk::pass_prepare<double>(block_max));
+    if (c->dtype == LS_C64) LS_CUDA(lsk::fast_prepare<float>(block_max));
+    else LS_CUDA(lsk::fast_prepare<double>(block_max));
+    for (int L = 0; L < 2; ++L) {
+      const lsk::LayerGeom& g = c->geom[L];
+      c->fastW[L] = 0;
+      if (g.d != 1 || g.np < 256 || g.np > 8192 || getenv_flag("LSPLIT_NO_FAST")) continue;
+      const int tps = g.np / 16;
+      const int maxnt = c->dtype == LS_C64 ? lsk::fast_max_threads<float>() : lsk::fast_max_threads<double>();
+      int W = std::min<int64_t>(std::min(lsk::kMaxTileSlices, maxnt / tps), g.nslices);
+      while (W > 0 && (c->dtype == LS_C64 ? lsk::fast_smem_bytes<float>(g, W) : lsk::fast_smem_bytes<double>(g, W)) >
+                          (size_t)dev_max)
+        --W;
+      c->fastW[L] = W;
+    }
     const size_t smax = (size_t)std::max(c->M1, c->M2) * 5;
-    if (smax > 48 * 1024) LS_CUDA(lsk::sampler_prepare(std::min(smax, (size_t)dev_max)));
+    if (smax > 48 * 1024) LS_CUDA(lsk::sampler_prepare(block_max));
     if (smax > (size_t)dev_max) throw CudaError{cudaErrorInvalidValue, "too many slices for the sampler"};
     elem_args(c.get());
     c->nblk_elem = lsk::kReduceBlocks;

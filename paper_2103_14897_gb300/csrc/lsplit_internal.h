@@ -28,12 +28,11 @@ struct LayerGeom {
   uint64_t A_aa, A_ab, A_bb;           // own quadratic form
   uint64_t X_aa, X_ab, X_ba, X_bb;     // cross: l_a = X_aa nu_a + X_ab nu_b, l_b = X_ba nu_a + X_bb nu_b
   uint64_t C_aa, C_ab, C_bb;           // other quadratic form
-  uint64_t chirp_unit;  // floor(2^64 / (2 q)) (Bluestein chirp in turns)
-  int two_q;
   const void* tw;     // np twiddles exp(-2 pi i x / np)
   const void* twb;    // npb twiddles (2D)
   const void* bm;     // Bluestein: FFT_np(b-) / np, b-_j = exp(-i pi j^2 / q)
   const void* bp;     // Bluestein: FFT_np(b+) / np
+  const void* chirp;  // Bluestein: exp(+i pi (i^2 mod 2q) / q), q entries
   const double* vgrid;  // v_j(x_p), FP64, M entries
 };
 
@@ -43,7 +42,7 @@ struct PassArgs {
   LayerGeom g;
   void* psi;
   void* lam;               // adjoint: lambda array (same layout)
-  const void* T;           // exp(-i s v_j(x_p)) / M, M entries (complex Real)
+  const void* T;           // (exp(-i s v_j(x_p)) - 1) / M, M entries (complex Real)
   int64_t units_pre;       // kinetic units before P (MODE_STEP / MODE_ADJOINT)
   int64_t units_post;      // kinetic units after P
   int W;                   // slices per CTA
@@ -100,6 +99,12 @@ cudaError_t launch_sampler(const SamplerArgs& sa, const uint64_t* seed_g0_dev, i
                            int32_t* out, cudaStream_t st);
 cudaError_t sampler_prepare(size_t smem);
 template <typename Real> int pass_max_threads(int bpt);
+// Fast 1D pass (MODE_STEP / MODE_LAZY, power-of-two transform length 256..8192):
+// W slices per CTA, W * np / 16 threads.
+template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntiles, cudaStream_t st);
+template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W);
+template <typename Real> cudaError_t fast_prepare(size_t max_smem);
+template <typename Real> int fast_max_threads();
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
 cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
 

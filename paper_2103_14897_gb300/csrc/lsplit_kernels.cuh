@@ -55,33 +55,68 @@ __device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
 
 // exp(2 pi i t / 2^64) for a fixed-point angle t.  The nearest quadrant is
 // removed exactly with integer arithmetic; the remainder (|angle| <= pi/4)
-// goes to sincospi.
-template <typename Real> __device__ __forceinline__ typename CT<Real>::C phase_of(uint64_t t);
-template <> __device__ __forceinline__ float2 phase_of<float>(uint64_t t) {
+// goes to sincospi.  In single precision two systematic errors are removed,
+// because the same angle recurs at every step for a given element:
+//  * the float argument is rounded; the exact integer residual of that
+//    rounding (< 2^-24 relative) rotates the result to first order;
+//  * |(c, s)| differs from 1 by O(eps); the deviation e = c^2 + s^2 - 1 is
+//    computed with error-free products and returned, and the caller scales the
+//    product x * (c, s) by (1 - e/2) with one fused rounding.
+template <typename Real> struct Phase {
+  typename CT<Real>::C v;
+  Real half_e;  // (c^2 + s^2 - 1) / 2
+};
+
+template <typename Real> __device__ __forceinline__ Phase<Real> phase_of(uint64_t t);
+template <> __device__ __forceinline__ Phase<float> phase_of<float>(uint64_t t) {
   const uint64_t q = (t + (1ull << 61)) >> 62;
-  const int64_t r = (int64_t)(t - (q << 62));
-  const float x = (float)(int)(r >> 32) * 0x1p-31f;  // units of pi
+  const int64_t r = (int64_t)(t - (q << 62));  // |r| <= 2^61, units of 2^-64 turns
+  const int rhi = (int)(r >> 32);
+  const float xf = (float)rhi;                  // may round (|rhi| <= 2^29)
+  const int64_t resid = r - ((int64_t)(int)xf << 32);
   float s, c;
-  sincospif(x, &s, &c);
+  sincospif(xf * 0x1p-31f, &s, &c);             // angle pi * xf / 2^31
+  const float d = (float)resid * 0x1.921fb6p-62f;  // residual angle in radians (2 pi / 2^64)
+  const float c1 = fmaf(-d, s, c), s1 = fmaf(d, c, s);
+  const float c2h = c1 * c1, c2l = fmaf(c1, c1, -c2h);
+  const float s2h = s1 * s1, s2l = fmaf(s1, s1, -s2h);
+  const float e = ((c2h - 1.0f) + s2h) + (c2l + s2l);
+  Phase<float> p;
   switch (q & 3) {
-    case 0: return make_float2(c, s);
-    case 1: return make_float2(-s, c);
-    case 2: return make_float2(-c, -s);
-    default: return make_float2(s, -c);
+    case 0: p.v = make_float2(c1, s1); break;
+    case 1: p.v = make_float2(-s1, c1); break;
+    case 2: p.v = make_float2(-c1, -s1); break;
+    default: p.v = make_float2(s1, -c1); break;
   }
+  p.half_e = 0.5f * e;
+  return p;
 }
-template <> __device__ __forceinline__ double2 phase_of<double>(uint64_t t) {
+template <> __device__ __forceinline__ Phase<double> phase_of<double>(uint64_t t) {
   const uint64_t q = (t + (1ull << 61)) >> 62;
   const int64_t r = (int64_t)(t - (q << 62));
   const double x = (double)r * 0x1p-63;
   double s, c;
   sincospi(x, &s, &c);
+  Phase<double> p;
   switch (q & 3) {
-    case 0: return make_double2(c, s);
-    case 1: return make_double2(-s, c);
-    case 2: return make_double2(-c, -s);
-    default: return make_double2(s, -c);
+    case 0: p.v = make_double2(c, s); break;
+    case 1: p.v = make_double2(-s, c); break;
+    case 2: p.v = make_double2(-c, -s); break;
+    default: p.v = make_double2(s, -c); break;
   }
+  p.half_e = 0.0;
+  return p;
+}
+
+// x * exp(i angle) with the modulus deviation of the phase removed.
+template <typename Real>
+__device__ __forceinline__ typename CT<Real>::C apply_phase(typename CT<Real>::C x, const Phase<Real>& p) {
+  typename CT<Real>::C y;
+  const Real ax = x.x * p.v.x - x.y * p.v.y;
+  const Real ay = x.x * p.v.y + x.y * p.v.x;
+  y.x = ax - p.half_e * ax;
+  y.y = ay - p.half_e * ay;
+  return y;
 }
 
 // ---------------------------------------------------------------- radix DFTs
@@ -280,15 +315,34 @@ __device__ __forceinline__ void bluestein_conv(typename CT<Real>::C* sm, const L
   fft_all<Real, true, true, BPT>(sm, f, (const C*)g.tw);
 }
 
-template <typename Real, int BPT>
+// One layer factor over a tile of W slices.  MODE selects the variant:
+//   MODE_STEP     K(post) P(s) K(pre) with fixed kinetic units;
+//   MODE_LAZY     stochastic: P on the listed slices only, the kinetic phase
+//                 pending since the element's last touch applied before P;
+//   MODE_KIN      settle: pending kinetic phase only, no transform;
+//   MODE_MEASURE  sum_p v(x_p)|psi(x_p)|^2 / M per CTA (potential energy);
+//   MODE_ADJOINT  inverse factor on psi and lambda together, accumulating
+//                 dL/dv(x_p).
+// P is applied as x + F diag(T - 1) F^{-1} x (T - 1 with the 1/M of the
+// forward transform in the table): the same operator, but the rounding of the
+// transforms only enters through the small correction term, so it does not
+// build up coherently over thousands of passes.
+template <typename Real, int BPT, int MODE>
 __global__ void __launch_bounds__(PassTraits<Real, BPT>::kMaxNT)
 pass_kernel(const PassArgs a) {
   using C = typename CT<Real>::C;
+  constexpr bool adj = (MODE == MODE_ADJOINT);
+  constexpr bool lazy = (MODE == MODE_LAZY);
+  constexpr bool kin_only = (MODE == MODE_KIN);
+  constexpr bool measure = (MODE == MODE_MEASURE);
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
   const LayerGeom& g = a.g;
   const int W = a.W;
-  C* sml = sm + (size_t)W * g.sb;  // adjoint: lambda tile
+  const int M = g.M;
+  C* sm = reinterpret_cast<C*>(smraw);
+  C* sml = sm + (size_t)W * g.sb;                         // adjoint: lambda tile
+  C* sx = sm + (size_t)W * g.sb * (adj ? 2 : 1);          // saved x (pre-phased)
+  C* sxl = sx + (size_t)W * M;                            // adjoint: saved lambda
   __shared__ int64_t s_slice[kMaxTileSlices];
   __shared__ uint64_t s_la[kMaxTileSlices], s_lb[kMaxTileSlices], s_c0[kMaxTileSlices];
   __shared__ int32_t s_touch[kMaxTileSlices];
@@ -296,10 +350,6 @@ pass_kernel(const PassArgs a) {
 
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
-  const bool adj = (a.mode == MODE_ADJOINT);
-  const bool lazy = (a.mode == MODE_LAZY);
-  const bool kin_only = (a.mode == MODE_KIN);
-  const bool measure = (a.mode == MODE_MEASURE);
 
   if (tid < W) {
     int64_t s = -1;
@@ -331,10 +381,9 @@ pass_kernel(const PassArgs a) {
 
   C* psi = reinterpret_cast<C*>(a.psi);
   C* lam = reinterpret_cast<C*>(a.lam);
-  const int M = g.M;
-  const int q = g.qa;  // 1D slice length (chirp index range)
+  const C* chirp = reinterpret_cast<const C*>(g.chirp);
 
-  // ---- load + kinetic pre-phase (+ Bluestein pre-chirp)
+  // ---- load + kinetic pre-phase (+ Bluestein pre-chirp on the transform input)
   for (int e = tid; e < W * M; e += NT) {
     int w, i;
     if (a.strided) { w = e % W; i = e / W; } else { w = e / M; i = e - w * M; }
@@ -346,34 +395,39 @@ pass_kernel(const PassArgs a) {
       x = psi[off];
       if (adj) xl = lam[off];
       if (!measure) {
-        const uint64_t qd = quad_turns(g, g.lo_a + ia, g.lo_b + ib, s_la[w], s_lb[w], s_c0[w]);
         int64_t units = a.units_pre;
         if (lazy || kin_only) {
           const int32_t t2 = a.touch_other[i];
           units = (int64_t)a.now - (int64_t)(s_touch[w] > t2 ? s_touch[w] : t2);
         }
-        uint64_t t = (uint64_t)0 - (uint64_t)units * qd;
-        if (g.bluestein && !kin_only) t += (uint64_t)(((int64_t)i * i) % g.two_q) * g.chirp_unit;
-        const C ph = phase_of<Real>(t);
-        x = cmul(x, ph);
-        if (adj) xl = cmul(xl, ph);
-      } else if (g.bluestein) {
-        const C ph = phase_of<Real>((uint64_t)(((int64_t)i * i) % g.two_q) * g.chirp_unit);
-        x = cmul(x, ph);
+        if (units != 0) {
+          const uint64_t qd = quad_turns(g, g.lo_a + ia, g.lo_b + ib, s_la[w], s_lb[w], s_c0[w]);
+          const Phase<Real> ph = phase_of<Real>((uint64_t)0 - (uint64_t)units * qd);
+          x = apply_phase<Real>(x, ph);
+          if (adj) xl = apply_phase<Real>(xl, ph);
+        }
+        if (kin_only) {
+          psi[off] = x;
+          continue;
+        }
       }
     }
-    if (kin_only) {
-      if (s >= 0) {
-        const int ia = i % g.qa, ib = i / g.qa;
-        psi[s * g.slice_stride + ia * g.ea + ib * g.eb] = x;
-      }
-      continue;
+    if (kin_only) continue;
+    if (!measure) {
+      sx[e] = x;
+      if (adj) sxl[e] = xl;
+    }
+    if (g.bluestein) {
+      const C ch = chirp[i];
+      x = cmul(x, ch);
+      if (adj) xl = cmul(xl, ch);
     }
     sm[w * g.sb + phys(i)] = x;
     if (adj) sml[w * g.sb + phys(i)] = xl;
   }
   if (kin_only) return;
   if (g.bluestein) {
+    const int q = g.qa;
     const int pad = g.np - q;
     for (int e = tid; e < W * pad; e += NT) {
       const int w = e / pad, i = q + (e - w * pad);
@@ -392,8 +446,8 @@ pass_kernel(const PassArgs a) {
     if (adj) transform<Real, true, BPT>(sml, g, W, false);
   }
 
-  // ---- pointwise potential factor (or measurement / gradient)
-  if (measure) {
+  // ---- pointwise: (T - 1)/M, or the measurement / gradient
+  if constexpr (measure) {
     double acc = 0.0;
     for (int e = tid; e < W * M; e += NT) {
       const int w = e / M, p = e - w * M;
@@ -410,8 +464,7 @@ pass_kernel(const PassArgs a) {
       if (tid == 0) a.partials[blockIdx.x] = v / (double)M;
     }
     return;
-  }
-  {
+  } else {
     const C* T = reinterpret_cast<const C*>(a.T);
     const int span = g.bluestein ? g.np : M;
     for (int e = tid; e < W * span; e += NT) {
@@ -435,44 +488,192 @@ pass_kernel(const PassArgs a) {
       sm[pi] = cmul(sm[pi], tp);
     }
     __syncthreads();
-  }
 
-  // ---- back to coefficients (forward transform; 1/M is folded into T)
-  if (g.bluestein) {
-    bluestein_conv<Real, BPT>(sm, g, W, (const C*)g.bp);
-    if (adj) bluestein_conv<Real, BPT>(sml, g, W, (const C*)g.bp);
-  } else {
-    transform<Real, false, BPT>(sm, g, W, false);
-    if (adj) transform<Real, false, BPT>(sml, g, W, false);
-  }
+    // ---- back to coefficients (forward transform; 1/M is in the table)
+    if (g.bluestein) {
+      bluestein_conv<Real, BPT>(sm, g, W, (const C*)g.bp);
+      if (adj) bluestein_conv<Real, BPT>(sml, g, W, (const C*)g.bp);
+    } else {
+      transform<Real, false, BPT>(sm, g, W, false);
+      if (adj) transform<Real, false, BPT>(sml, g, W, false);
+    }
 
-  // ---- store + kinetic post-phase (+ Bluestein post-chirp)
-  for (int e = tid; e < W * M; e += NT) {
-    int w, i;
-    if (a.strided) { w = e % W; i = e / W; } else { w = e / M; i = e - w * M; }
-    const int64_t s = s_slice[w];
-    if (s < 0) continue;
-    const int ia = i % g.qa, ib = i / g.qa;
-    const int64_t off = s * g.slice_stride + ia * g.ea + ib * g.eb;
-    uint64_t t = 0;
-    if (!lazy && a.units_post != 0) {
-      const uint64_t qd = quad_turns(g, g.lo_a + ia, g.lo_b + ib, s_la[w], s_lb[w], s_c0[w]);
-      t = (uint64_t)0 - (uint64_t)a.units_post * qd;
+    // ---- x + correction, kinetic post-phase, store
+    for (int e = tid; e < W * M; e += NT) {
+      int w, i;
+      if (a.strided) { w = e % W; i = e / W; } else { w = e / M; i = e - w * M; }
+      const int64_t s = s_slice[w];
+      if (s < 0) continue;
+      const int ia = i % g.qa, ib = i / g.qa;
+      const int64_t off = s * g.slice_stride + ia * g.ea + ib * g.eb;
+      C cx = sm[w * g.sb + phys(i)], cl;
+      if (adj) cl = sml[w * g.sb + phys(i)];
+      if (g.bluestein) {
+        const C ch = chirp[i];
+        cx = cmulconj(cx, ch);
+        if (adj) cl = cmulconj(cl, ch);
+      }
+      C x = cadd(sx[e], cx), xl;
+      if (adj) xl = cadd(sxl[e], cl);
+      if (!lazy && a.units_post != 0) {
+        const uint64_t qd = quad_turns(g, g.lo_a + ia, g.lo_b + ib, s_la[w], s_lb[w], s_c0[w]);
+        const Phase<Real> ph = phase_of<Real>((uint64_t)0 - (uint64_t)a.units_post * qd);
+        x = apply_phase<Real>(x, ph);
+        if (adj) xl = apply_phase<Real>(xl, ph);
+      }
+      psi[off] = x;
+      if (adj) lam[off] = xl;
     }
-    if (g.bluestein) t -= (uint64_t)(((int64_t)i * i) % g.two_q) * g.chirp_unit;
-    C x = sm[w * g.sb + phys(i)];
-    if (t != 0) {
-      const C ph = phase_of<Real>(t);
-      x = cmul(x, ph);
-      if (adj) lam[off] = cmul(sml[w * g.sb + phys(i)], ph);
-    } else if (adj) {
-      lam[off] = sml[w * g.sb + phys(i)];
-    }
-    psi[off] = x;
+    if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
   }
-  if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
 }
 
+// ---------------------------------------------------------------- fast 1D pass
+// Specialised pass for 1D slices whose transform length N = 2^LOGN is fixed at
+// compile time (8 <= LOGN <= 13): every thread owns 16 elements
+// x[j + r N/16] of its slice in registers; Stockham stages with radix 16
+// first and last (radix 2/4/8 in the middle), so the output of one FFT and the
+// input of the next have the same register layout and the pointwise products
+// between transforms (Bluestein kernels, the potential factor) happen in
+// registers.  Only the inner stages exchange through shared memory
+// (ping-pong buffers, one barrier per exchange).
+
+__host__ __device__ constexpr int fast_nstages(int logn) { return logn == 13 ? 4 : (logn == 8 ? 2 : 3); }
+__host__ __device__ constexpr int fast_radix(int logn, int s) {
+  // stage s of the plan for N = 2^logn
+  return (s == 0 || s == fast_nstages(logn) - 1) ? 16
+         : (logn == 9 ? 2 : logn == 10 ? 4 : logn == 11 ? 8 : logn == 12 ? 16 : (s == 1 ? 2 : 16));
+}
+__host__ __device__ constexpr int fast_ns(int logn, int s) {  // product of radices before stage s
+  return s == 0 ? 1 : fast_ns(logn, s - 1) * fast_radix(logn, s - 1);
+}
+
+// exp(-+2 pi i k / 16) for compile-time k: (cos, sin) of multiples of pi/8.
+template <typename C, bool INV, int K>
+__device__ __forceinline__ C rot16(C v) {
+  typedef decltype(v.x) R;
+  constexpr int k = K & 15;
+  if constexpr (k == 0) return v;
+  else if constexpr ((k & 1) == 0) return rot8<C, INV>(v, k / 2 < 4 ? k / 2 : 0) ;  // k = 2,4,6 (k <= 9 used)
+  else {
+    const R c8 = (R)0.92387953251128675613, s8 = (R)0.38268343236508977173;
+    R cr, ci;  // exp(-i 2 pi k / 16) = (cos, -sin)
+    if constexpr (k == 1) { cr = c8; ci = -s8; }
+    else if constexpr (k == 3) { cr = s8; ci = -c8; }
+    else if constexpr (k == 5) { cr = -s8; ci = -c8; }
+    else if constexpr (k == 7) { cr = -c8; ci = -s8; }
+    else { cr = -c8; ci = s8; }  // k == 9
+    if (INV) ci = -ci;
+    C r;
+    r.x = v.x * cr - v.y * ci;
+    r.y = v.x * ci + v.y * cr;
+    return r;
+  }
+}
+
+template <typename C, bool INV, int N2>
+__device__ __forceinline__ void dft16_col(C* v, C (&a)[4][4]) {
+  C t[4] = {v[N2], v[4 + N2], v[8 + N2], v[12 + N2]};
+  dft4<C, INV>(t);
+  a[N2][0] = t[0];
+  a[N2][1] = rot16<C, INV, N2 * 1>(t[1]);
+  a[N2][2] = rot16<C, INV, N2 * 2>(t[2]);
+  a[N2][3] = rot16<C, INV, N2 * 3>(t[3]);
+}
+
+// 16-point DFT in registers, natural order in and out (4 x 4 decomposition).
+template <typename C, bool INV>
+__device__ __forceinline__ void dft16(C* v) {
+  C a[4][4];
+  dft16_col<C, INV, 0>(v, a);
+  dft16_col<C, INV, 1>(v, a);
+  dft16_col<C, INV, 2>(v, a);
+  dft16_col<C, INV, 3>(v, a);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    dft4<C, INV>(t);
+    v[k1] = t[0];
+    v[k1 + 4] = t[1];
+    v[k1 + 8] = t[2];
+    v[k1 + 12] = t[3];
+  }
+}
+
+template <int R, typename C, bool INV> __device__ __forceinline__ void dftRR(C* v) {
+  if constexpr (R == 16) dft16<C, INV>(v);
+  else dftR<R, C, INV>(v);
+}
+
+// Multiply v[r] (r = 1..R-1) by w^r, w = exp(-+2 pi i k / (ns R)), powers by
+// binary splitting from one table entry.
+template <int R, typename Real, bool INV>
+__device__ __forceinline__ void twiddle_pow(typename CT<Real>::C* v, typename CT<Real>::C w) {
+  using C = typename CT<Real>::C;
+  if (INV) w.y = -w.y;
+  C p[R];
+  p[1] = w;
+#pragma unroll
+  for (int r = 2; r < R; ++r) p[r] = cmul(p[r / 2], p[r - r / 2]);
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = cmul(v[r], p[r]);
+}
+
+template <typename Real, int LOGN, int S, bool INV>
+__device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typename CT<Real>::C* buf,
+                                          const typename CT<Real>::C* __restrict__ tw, int j) {
+  using C = typename CT<Real>::C;
+  constexpr int N = 1 << LOGN, TPS = N / 16;
+  if constexpr (S < fast_nstages(LOGN)) {
+    // write the outputs of stage S-1, then read the inputs of stage S
+    constexpr int Rp = fast_radix(LOGN, S - 1), nsp = fast_ns(LOGN, S - 1);
+#pragma unroll
+    for (int u = 0; u < 16 / Rp; ++u) {
+      const int b = j + u * TPS;
+      const int k = b & (nsp - 1);
+      const int i0 = (b - k) * Rp + k;
+#pragma unroll
+      for (int r = 0; r < Rp; ++r) buf[phys(i0 + r * nsp)] = v[u * Rp + r];
+    }
+    __syncthreads();
+    constexpr int R = fast_radix(LOGN, S), ns = fast_ns(LOGN, S);
+#pragma unroll
+    for (int u = 0; u < 16 / R; ++u) {
+      const int b = j + u * TPS;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u * R + r] = buf[phys(b + r * (N / R))];
+      const int k = b & (ns - 1);
+      twiddle_pow<R, Real, INV>(v + u * R, tw[k * (N / (ns * R))]);
+      dftRR<R, C, INV>(v + u * R);
+    }
+  }
+}
+
+// Full FFT of length N on the register layout x[j + r N/16]; exchanges
+// alternate between the two buffers (one barrier each).
+template <typename Real, int LOGN, bool INV>
+__device__ __forceinline__ void fast_fft(typename CT<Real>::C (&v)[16], typename CT<Real>::C* bufA,
+                                         typename CT<Real>::C* bufB, int& flip,
+                                         const typename CT<Real>::C* __restrict__ tw, int j) {
+  using C = typename CT<Real>::C;
+  constexpr int N = 1 << LOGN, TPS = N / 16;
+  constexpr int NS = fast_nstages(LOGN);
+  dft16<C, INV>(v);
+#pragma unroll
+  for (int S = 1; S < NS; ++S) {
+    C* buf = (flip & 1) ? bufB : bufA;
+    ++flip;
+    // radix and stride of stages S-1 and S (S is a loop index; the switch
+    // below dispatches to compile-time stage bodies)
+    switch (S) {
+      case 1: fast_xchg<Real, LOGN, 1, INV>(v, buf, tw, j); break;
+      case 2: fast_xchg<Real, LOGN, 2, INV>(v, buf, tw, j); break;
+      case 3: fast_xchg<Real, LOGN, 3, INV>(v, buf, tw, j); break;
+    }
+  }
+  (void)TPS;
+}
+#ifdef LS_DEFINE_MISC
 int pass_threads(const LayerGeom& g, int W, int bpt) {
   // Largest butterfly count over all stages of all transforms of a pass.
   auto worst = [&](int n, int nbatch) {
@@ -495,24 +696,217 @@ int pass_threads(const LayerGeom& g, int W, int bpt) {
   return nt;
 }
 
+#endif  // LS_DEFINE_MISC
+
 template <typename Real> size_t pass_smem_bytes(const LayerGeom& g, int W, int mode) {
   using C = typename CT<Real>::C;
-  return (size_t)W * g.sb * sizeof(C) * (mode == MODE_ADJOINT ? 2 : 1);
+  const size_t k = (mode == MODE_ADJOINT) ? 2 : 1;
+  if (mode == MODE_KIN) return 0;
+  return ((size_t)W * g.sb + (mode == MODE_MEASURE ? 0 : (size_t)W * g.M)) * sizeof(C) * k;
 }
 
-template <typename Real> cudaError_t pass_prepare(size_t max_smem) {
-  cudaError_t e = cudaFuncSetAttribute(pass_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+// Opt-in dynamic shared memory: the per-block limit minus the kernel's static
+// shared memory.
+template <typename K> static cudaError_t allow_smem(K kernel, size_t max_block) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(pass_kernel<Real, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+  const size_t dyn = max_block > fa.sharedSizeBytes ? max_block - fa.sharedSizeBytes : 0;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
+
+template <typename Real> struct FastTraits {
+  static constexpr int kMaxNT = sizeof(Real) == 4 ? 512 : 256;
+};
+
+// Fast pass: MODE_STEP or MODE_LAZY, 1D slices, N = 2^LOGN.
+template <typename Real, int LOGN, int MODE>
+__global__ void __launch_bounds__(FastTraits<Real>::kMaxNT)
+pass_fast_kernel(const PassArgs a) {
+  using C = typename CT<Real>::C;
+  constexpr int N = 1 << LOGN, TPS = N / 16;
+  constexpr bool lazy = (MODE == MODE_LAZY);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const LayerGeom& g = a.g;
+  const int W = a.W;
+  const int Q = g.qa;
+  const int t = threadIdx.x;
+  const int w = a.strided ? t % W : t / TPS;
+  const int j = a.strided ? t / W : t % TPS;
+  C* bufA = reinterpret_cast<C*>(smraw) + (size_t)w * 2 * g.sb;
+  C* bufB = bufA + g.sb;
+  C* xs = reinterpret_cast<C*>(smraw) + (size_t)W * 2 * g.sb + (size_t)w * Q;
+  __shared__ int64_t s_slice[kMaxTileSlices];
+  __shared__ uint64_t s_la[kMaxTileSlices], s_c0[kMaxTileSlices];
+  __shared__ int32_t s_touch[kMaxTileSlices];
+  if (t < W) {
+    int64_t s = -1;
+    if (a.list) {
+      const int64_t li = (int64_t)blockIdx.x * W + t;
+      if (li < a.nlist) s = a.list[li];
+    } else {
+      s = (int64_t)blockIdx.x * W + t;
+      if (s >= g.nslices) s = -1;
+    }
+    s_slice[t] = s;
+    uint64_t la = 0, c0 = 0;
+    int32_t touch = 0;
+    if (s >= 0) {
+      const uint64_t ua = (uint64_t)(s + g.olo_a);
+      la = g.X_aa * ua;
+      c0 = g.C_aa * (ua * ua);
+      if (lazy) touch = a.touch_own[s];
+    }
+    s_la[t] = la;
+    s_c0[t] = c0;
+    s_touch[t] = touch;
+  }
+  __syncthreads();
+  const int64_t s = s_slice[w];
+  C* psi = reinterpret_cast<C*>(a.psi);
+  const C* chirp = reinterpret_cast<const C*>(g.chirp);
+  const C* tw = reinterpret_cast<const C*>(g.tw);
+  const int64_t base = s * g.slice_stride;
+  const uint64_t la = s_la[w], c0 = s_c0[w];
+
+  C v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = j + r * TPS;
+    C x = czero<C>();
+    if (s >= 0 && i < Q) {
+      x = psi[base + (int64_t)i * g.ea];
+      int64_t units = a.units_pre;
+      if (lazy) {
+        const int32_t t2 = a.touch_other[i];
+        units = (int64_t)a.now - (int64_t)(s_touch[w] > t2 ? s_touch[w] : t2);
+      }
+      if (units != 0) {
+        const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);
+        const uint64_t qd = g.A_aa * (m * m) + la * m + c0;
+        x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)units * qd));
+      }
+      xs[i] = x;
+      if (g.bluestein) x = cmul(x, chirp[i]);
+    }
+    v[r] = x;
+  }
+  int flip = 0;
+  const C* T = reinterpret_cast<const C*>(a.T);
+  if (g.bluestein) {
+    const C* bm = reinterpret_cast<const C*>(g.bm);
+    const C* bp = reinterpret_cast<const C*>(g.bp);
+    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], bm[j + r * TPS]);
+    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = j + r * TPS;
+      v[r] = i < Q ? cmul(v[r], T[i]) : czero<C>();
+    }
+    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], bp[j + r * TPS]);
+    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+  } else {
+    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], T[j + r * TPS]);
+    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+  }
+  if (s >= 0) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = j + r * TPS;
+      if (i < Q) {
+        C c = v[r];
+        if (g.bluestein) c = cmulconj(c, chirp[i]);
+        C x = cadd(xs[i], c);
+        if (!lazy && a.units_post != 0) {
+          const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);
+          const uint64_t qd = g.A_aa * (m * m) + la * m + c0;
+          x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)a.units_post * qd));
+        }
+        psi[base + (int64_t)i * g.ea] = x;
+      }
+    }
+  }
+  if (lazy && t < W && s_slice[t] >= 0) a.touch_own[s_slice[t]] = a.now;
+}
+
+template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W) {
+  using C = typename CT<Real>::C;
+  return ((size_t)W * 2 * g.sb + (size_t)W * g.qa) * sizeof(C);
+}
+
+template <typename Real, int LOGN>
+static cudaError_t launch_fast_n(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
+  const int nt = a.W * ((1 << LOGN) / 16);
+  const size_t smem = fast_smem_bytes<Real>(a.g, a.W);
+  if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  else pass_fast_kernel<Real, LOGN, MODE_STEP><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  switch (a.g.np) {
+    case 256: return launch_fast_n<Real, 8>(a, ntiles, st);
+    case 512: return launch_fast_n<Real, 9>(a, ntiles, st);
+    case 1024: return launch_fast_n<Real, 10>(a, ntiles, st);
+    case 2048: return launch_fast_n<Real, 11>(a, ntiles, st);
+    case 4096: return launch_fast_n<Real, 12>(a, ntiles, st);
+    case 8192: return launch_fast_n<Real, 13>(a, ntiles, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
+  cudaError_t e = cudaSuccess;
+#define LS_FPREP(L) \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP>, max_smem); \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY>, max_smem);
+  LS_FPREP(8) LS_FPREP(9) LS_FPREP(10) LS_FPREP(11) LS_FPREP(12) LS_FPREP(13)
+#undef LS_FPREP
+  return e;
+}
+template <typename Real> int fast_max_threads() { return FastTraits<Real>::kMaxNT; }
+
+#define LS_FOR_MODES(X, R, B) \
+  X(R, B, MODE_STEP) X(R, B, MODE_LAZY) X(R, B, MODE_MEASURE) X(R, B, MODE_ADJOINT) X(R, B, MODE_KIN)
+
+template <typename Real> cudaError_t pass_prepare(size_t max_smem) {
+  cudaError_t e = cudaSuccess;
+#define LS_PREP(R, B, MD) \
+  if (e == cudaSuccess) e = allow_smem(pass_kernel<R, B, MD>, max_smem);
+  LS_FOR_MODES(LS_PREP, Real, 2)
+  LS_FOR_MODES(LS_PREP, Real, 4)
+#undef LS_PREP
+  return e;
+}
+
+template <typename Real, int BPT>
+static cudaError_t launch_pass_b(const PassArgs& a, int nthreads, int64_t ntiles, size_t smem,
+                                 cudaStream_t st) {
+  switch (a.mode) {
+    case MODE_STEP: pass_kernel<Real, BPT, MODE_STEP><<<(unsigned)ntiles, nthreads, smem, st>>>(a); break;
+    case MODE_LAZY: pass_kernel<Real, BPT, MODE_LAZY><<<(unsigned)ntiles, nthreads, smem, st>>>(a); break;
+    case MODE_MEASURE: pass_kernel<Real, BPT, MODE_MEASURE><<<(unsigned)ntiles, nthreads, smem, st>>>(a); break;
+    case MODE_ADJOINT: pass_kernel<Real, BPT, MODE_ADJOINT><<<(unsigned)ntiles, nthreads, smem, st>>>(a); break;
+    case MODE_KIN: pass_kernel<Real, BPT, MODE_KIN><<<(unsigned)ntiles, nthreads, smem, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 template <typename Real> cudaError_t launch_pass(const PassArgs& a, int bpt, int nthreads, int64_t ntiles,
                                                  cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   const size_t smem = pass_smem_bytes<Real>(a.g, a.W, a.mode);
-  if (bpt == 4) pass_kernel<Real, 4><<<(unsigned)ntiles, nthreads, smem, st>>>(a);
-  else pass_kernel<Real, 2><<<(unsigned)ntiles, nthreads, smem, st>>>(a);
-  return cudaGetLastError();
+  if (bpt == 4) return launch_pass_b<Real, 4>(a, nthreads, ntiles, smem, st);
+  return launch_pass_b<Real, 2>(a, nthreads, ntiles, smem, st);
 }
 
 // ---------------------------------------------------------------- elementwise kernels
@@ -639,6 +1033,7 @@ __global__ void elem_obs_kernel(const ElemArgs e, const typename CT<Real>::C* ps
   }
 }
 
+#ifdef LS_DEFINE_MISC
 // Sum partials[nparts][nq] over parts in a fixed order (deterministic).
 __global__ void reduce_kernel(const double* partials, int nparts, int nq, double* out) {
   __shared__ double red[32];
@@ -710,6 +1105,8 @@ __global__ void zero_f64_kernel(double* p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0.0;
 }
 
+#endif  // LS_DEFINE_MISC
+
 template <typename Real>
 cudaError_t launch_gaussian(const ElemArgs& e, void* psi, const double* x0, double w, const double* k0,
                             double* partials, int nblocks, cudaStream_t st) {
@@ -731,6 +1128,7 @@ cudaError_t launch_elem_obs(const ElemArgs& e, const void* psi, const void* chi,
                                                  reinterpret_cast<const C*>(chi), partials);
   return cudaGetLastError();
 }
+#ifdef LS_DEFINE_MISC
 cudaError_t launch_reduce(const double* partials, int nparts, int nq, double* out, cudaStream_t st) {
   reduce_kernel<<<1, 1024, 0, st>>>(partials, nparts, nq, out);
   return cudaGetLastError();
@@ -742,9 +1140,7 @@ cudaError_t launch_sampler(const SamplerArgs& sa, const uint64_t* seed_g0_dev, i
   sampler_kernel<<<count, 256, smem, st>>>(sa, seed_g0_dev, out);
   return cudaGetLastError();
 }
-cudaError_t sampler_prepare(size_t smem) {
-  return cudaFuncSetAttribute(sampler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
+cudaError_t sampler_prepare(size_t smem) { return allow_smem(sampler_kernel, smem); }
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   zero_i32_kernel<<<256, 256, 0, st>>>(p, n);
@@ -756,6 +1152,8 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+#endif  // LS_DEFINE_MISC
+
 #define LS_INST(R)                                                                                        \
   template cudaError_t launch_pass<R>(const PassArgs&, int, int, int64_t, cudaStream_t);                 \
   template size_t pass_smem_bytes<R>(const LayerGeom&, int, int);                                        \
@@ -764,9 +1162,14 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
                                           double*, int, cudaStream_t);                                   \
   template cudaError_t launch_scale<R>(const ElemArgs&, void*, const double*, cudaStream_t);             \
   template cudaError_t launch_elem_obs<R>(const ElemArgs&, const void*, const void*, double*, int,      \
-                                          cudaStream_t);
-LS_INST(float)
-LS_INST(double)
+                                          cudaStream_t);                                                 \
+  template cudaError_t launch_fast<R>(const PassArgs&, int64_t, cudaStream_t);                           \
+  template size_t fast_smem_bytes<R>(const LayerGeom&, int);                                             \
+  template cudaError_t fast_prepare<R>(size_t);                                                          \
+  template int fast_max_threads<R>();
+#ifdef LS_INST_REAL
+LS_INST(LS_INST_REAL)
+#endif
 
 }  // namespace lsk
 
@@ -774,6 +1177,7 @@ namespace lsk {
 template <typename Real> int pass_max_threads(int bpt) {
   return bpt == 4 ? PassTraits<Real, 4>::kMaxNT : PassTraits<Real, 2>::kMaxNT;
 }
-template int pass_max_threads<float>(int);
-template int pass_max_threads<double>(int);
+#ifdef LS_INST_REAL
+template int pass_max_threads<LS_INST_REAL>(int);
+#endif
 }  // namespace lsk

@@ -216,8 +216,24 @@ def test_long_run_1000_steps(P):
     ctx.step(psi, 1000, 1e-3, "strang")
     ref = O.step(p, x, 1e-3, "strang", 1000)
     got = ctx.to_dense(psi)
+    print("1000-step rel-L2", rel(got, ref), "norm-1", np.linalg.norm(got) - 1)
     assert rel(got, ref) < 1e-4
     assert abs(np.linalg.norm(got) - 1) < 1e-5
+
+
+def test_fast_and_generic_paths_agree(P, monkeypatch):
+    """The register-resident fast pass and the generic pass compute the same
+    step (both are also checked against the oracle above)."""
+    for p in [W.config_scale_1d(), W.bilayer_1d(128, 200, 1.1, 0.6, ecut=1e9)]:
+        x = W.random_state((p.M2, p.M1), 9)
+        a = P.Context(p, "c64")
+        monkeypatch.setenv("LSPLIT_NO_FAST", "1")
+        b = P.Context(p, "c64")
+        monkeypatch.delenv("LSPLIT_NO_FAST")
+        pa, pb = a.from_dense(x), b.from_dense(x)
+        a.step(pa, 3, 5e-4, "strang")
+        b.step(pb, 3, 5e-4, "strang")
+        assert rel(a.to_dense(pa), b.to_dense(pb)) < 3e-6
 
 
 def test_fp64_config_small_100_steps(P):
