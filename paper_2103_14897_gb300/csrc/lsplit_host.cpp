@@ -674,10 +674,15 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     for (int L = 0; L < 2; ++L) {
       const lsk::LayerGeom& g = c->geom[L];
       c->fastW[L] = 0;
-      if (g.d != 1 || g.np < 256 || g.np > 8192 || getenv_flag("LSPLIT_NO_FAST")) continue;
+      if (g.d != 1 || g.np < 512 || g.np > 4096 || getenv_flag("LSPLIT_NO_FAST")) continue;
       const int tps = g.np / 16;
-      const int maxnt = c->dtype == LS_C64 ? lsk::fast_max_threads<float>() : lsk::fast_max_threads<double>();
-      int W = std::min<int64_t>(std::min(lsk::kMaxTileSlices, maxnt / tps), g.nslices);
+      // contiguous slices: 256-thread CTAs (several per SM); strided slices:
+      // up to the 512-thread variant so a CTA reads wider row segments
+      const int maxnt = (L == 0 || c->dtype != LS_C64) ? 256 : lsk::fast_max_threads<float>();
+      const char* ev = std::getenv(L == 0 ? "LSPLIT_FAST_NT1" : "LSPLIT_FAST_NT2");
+      const int cap = ev ? std::max(tps, std::min(std::atoi(ev), lsk::fast_max_threads<float>())) : maxnt;
+      const int ntcap = c->dtype == LS_C64 ? cap : std::min(cap, 256);
+      int W = std::min<int64_t>(std::min(lsk::kMaxTileSlices, std::max(1, ntcap / tps)), g.nslices);
       while (W > 0 && (c->dtype == LS_C64 ? lsk::fast_smem_bytes<float>(g, W) : lsk::fast_smem_bytes<double>(g, W)) >
                           (size_t)dev_max)
         --W;

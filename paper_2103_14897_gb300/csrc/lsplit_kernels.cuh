@@ -78,9 +78,10 @@ template <> __device__ __forceinline__ Phase<float> phase_of<float>(uint64_t t) 
   sincospif(xf * 0x1p-31f, &s, &c);             // angle pi * xf / 2^31
   const float d = (float)resid * 0x1.921fb6p-62f;  // residual angle in radians (2 pi / 2^64)
   const float c1 = fmaf(-d, s, c), s1 = fmaf(d, c, s);
-  const float c2h = c1 * c1, c2l = fmaf(c1, c1, -c2h);
-  const float s2h = s1 * s1, s2l = fmaf(s1, s1, -s2h);
-  const float e = ((c2h - 1.0f) + s2h) + (c2l + s2l);
+  // explicit round-to-nearest operations: no contraction may merge c2h - 1
+  const float c2h = __fmul_rn(c1, c1), c2l = fmaf(c1, c1, -c2h);
+  const float s2h = __fmul_rn(s1, s1), s2l = fmaf(s1, s1, -s2h);
+  const float e = __fadd_rn(__fadd_rn(__fadd_rn(c2h, -1.0f), s2h), __fadd_rn(c2l, s2l));
   Phase<float> p;
   switch (q & 3) {
     case 0: p.v = make_float2(c1, s1); break;
@@ -109,14 +110,35 @@ template <> __device__ __forceinline__ Phase<double> phase_of<double>(uint64_t t
 }
 
 // x * exp(i angle) with the modulus deviation of the phase removed.
+// In single precision the product is formed error-free (two-product and
+// two-sum transforms, explicit round-to-nearest intrinsics so nothing is
+// contracted), the factor (1 - e/2) is applied to the exact value and each
+// component is rounded once.  A correction of e/2 ~ eps applied after a
+// rounded product would itself round away, leaving the per-element bias of
+// |(c, s)| in place at every step.
+__device__ __forceinline__ float dot2_fix(float a, float c, float b, float s, float h) {
+  // a*c + b*s, times (1 - h), single final rounding
+  const float p = __fmul_rn(a, c), pe = fmaf(a, c, -p);
+  const float q = __fmul_rn(b, s), qe = fmaf(b, s, -q);
+  const float r = __fadd_rn(p, q);
+  const float bb = __fsub_rn(r, p);
+  const float re = __fadd_rn(__fsub_rn(p, __fsub_rn(r, bb)), __fsub_rn(q, bb));
+  const float lo = __fadd_rn(__fadd_rn(re, __fadd_rn(pe, qe)), -__fmul_rn(h, r));
+  return __fadd_rn(r, lo);
+}
+
 template <typename Real>
-__device__ __forceinline__ typename CT<Real>::C apply_phase(typename CT<Real>::C x, const Phase<Real>& p) {
-  typename CT<Real>::C y;
-  const Real ax = x.x * p.v.x - x.y * p.v.y;
-  const Real ay = x.x * p.v.y + x.y * p.v.x;
-  y.x = ax - p.half_e * ax;
-  y.y = ay - p.half_e * ay;
+__device__ __forceinline__ typename CT<Real>::C apply_phase(typename CT<Real>::C x, const Phase<Real>& p);
+template <>
+__device__ __forceinline__ float2 apply_phase<float>(float2 x, const Phase<float>& p) {
+  float2 y;
+  y.x = dot2_fix(x.x, p.v.x, -x.y, p.v.y, p.half_e);
+  y.y = dot2_fix(x.x, p.v.y, x.y, p.v.x, p.half_e);
   return y;
+}
+template <>
+__device__ __forceinline__ double2 apply_phase<double>(double2 x, const Phase<double>& p) {
+  return cmul(x, p.v);
 }
 
 // ---------------------------------------------------------------- radix DFTs
@@ -572,32 +594,44 @@ __device__ __forceinline__ C rot16(C v) {
 }
 
 template <typename C, bool INV, int N2>
-__device__ __forceinline__ void dft16_col(C* v, C (&a)[4][4]) {
+__device__ __forceinline__ void dft16_col(C* v) {
+  // 4-point DFT of v[N2 + 4 n1] over n1, in place, then the inner twiddles
+  // W16^(N2 k1): afterwards v[N2 + 4 k1] holds column N2, frequency k1.
   C t[4] = {v[N2], v[4 + N2], v[8 + N2], v[12 + N2]};
   dft4<C, INV>(t);
-  a[N2][0] = t[0];
-  a[N2][1] = rot16<C, INV, N2 * 1>(t[1]);
-  a[N2][2] = rot16<C, INV, N2 * 2>(t[2]);
-  a[N2][3] = rot16<C, INV, N2 * 3>(t[3]);
+  v[N2] = t[0];
+  v[4 + N2] = rot16<C, INV, N2 * 1>(t[1]);
+  v[8 + N2] = rot16<C, INV, N2 * 2>(t[2]);
+  v[12 + N2] = rot16<C, INV, N2 * 3>(t[3]);
 }
 
-// 16-point DFT in registers, natural order in and out (4 x 4 decomposition).
+// 16-point DFT in registers, natural order in and out (4 x 4 decomposition,
+// in place; the final 4 x 4 transpose is a register renaming).
 template <typename C, bool INV>
 __device__ __forceinline__ void dft16(C* v) {
-  C a[4][4];
-  dft16_col<C, INV, 0>(v, a);
-  dft16_col<C, INV, 1>(v, a);
-  dft16_col<C, INV, 2>(v, a);
-  dft16_col<C, INV, 3>(v, a);
+  dft16_col<C, INV, 0>(v);
+  dft16_col<C, INV, 1>(v);
+  dft16_col<C, INV, 2>(v);
+  dft16_col<C, INV, 3>(v);
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
-    C t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    // row k1: v[4 k1 + n2], n2 = 0..3 -> frequencies k2 (output k1 + 4 k2)
+    C t[4] = {v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]};
     dft4<C, INV>(t);
-    v[k1] = t[0];
-    v[k1 + 4] = t[1];
-    v[k1 + 8] = t[2];
-    v[k1 + 12] = t[3];
+    v[4 * k1] = t[0];
+    v[4 * k1 + 1] = t[1];
+    v[4 * k1 + 2] = t[2];
+    v[4 * k1 + 3] = t[3];
   }
+  // X[k1 + 4 k2] is at v[4 k1 + k2]: transpose the 4 x 4 block
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b) {
+      C t = v[4 * a + b];
+      v[4 * a + b] = v[4 * b + a];
+      v[4 * b + a] = t;
+    }
 }
 
 template <int R, typename C, bool INV> __device__ __forceinline__ void dftRR(C* v) {
@@ -605,18 +639,20 @@ template <int R, typename C, bool INV> __device__ __forceinline__ void dftRR(C* 
   else dftR<R, C, INV>(v);
 }
 
-// Multiply v[r] (r = 1..R-1) by w^r, w = exp(-+2 pi i k / (ns R)), powers by
-// binary splitting from one table entry.
+// Multiply v[r] (r = 1..R-1) by w^r, w = exp(-+2 pi i k / (ns R)), with the
+// powers formed by repeated multiplication from one table entry (two live
+// registers; relative error <= R eps, which enters the result only through
+// the small potential correction term).
 template <int R, typename Real, bool INV>
 __device__ __forceinline__ void twiddle_pow(typename CT<Real>::C* v, typename CT<Real>::C w) {
   using C = typename CT<Real>::C;
   if (INV) w.y = -w.y;
-  C p[R];
-  p[1] = w;
+  C p = w;
 #pragma unroll
-  for (int r = 2; r < R; ++r) p[r] = cmul(p[r / 2], p[r - r / 2]);
-#pragma unroll
-  for (int r = 1; r < R; ++r) v[r] = cmul(v[r], p[r]);
+  for (int r = 1; r < R; ++r) {
+    v[r] = cmul(v[r], p);
+    if (r + 1 < R) p = cmul(p, w);
+  }
 }
 
 template <typename Real, int LOGN, int S, bool INV>
@@ -716,13 +752,11 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t max_block) 
 }
 
 
-template <typename Real> struct FastTraits {
-  static constexpr int kMaxNT = sizeof(Real) == 4 ? 512 : 256;
-};
-
-// Fast pass: MODE_STEP or MODE_LAZY, 1D slices, N = 2^LOGN.
-template <typename Real, int LOGN, int MODE>
-__global__ void __launch_bounds__(FastTraits<Real>::kMaxNT)
+// Fast pass: MODE_STEP or MODE_LAZY, 1D slices, N = 2^LOGN, at most NTMAX
+// threads per CTA (256 threads: several CTAs per SM; 512: two slices per CTA
+// for wider row segments in the strided layer).
+template <typename Real, int LOGN, int MODE, int NTMAX>
+__global__ void __launch_bounds__(NTMAX, (NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1)
 pass_fast_kernel(const PassArgs a) {
   using C = typename CT<Real>::C;
   constexpr int N = 1 << LOGN, TPS = N / 16;
@@ -736,7 +770,6 @@ pass_fast_kernel(const PassArgs a) {
   const int j = a.strided ? t / W : t % TPS;
   C* bufA = reinterpret_cast<C*>(smraw) + (size_t)w * 2 * g.sb;
   C* bufB = bufA + g.sb;
-  C* xs = reinterpret_cast<C*>(smraw) + (size_t)W * 2 * g.sb + (size_t)w * Q;
   __shared__ int64_t s_slice[kMaxTileSlices];
   __shared__ uint64_t s_la[kMaxTileSlices], s_c0[kMaxTileSlices];
   __shared__ int32_t s_touch[kMaxTileSlices];
@@ -763,36 +796,44 @@ pass_fast_kernel(const PassArgs a) {
     s_touch[t] = touch;
   }
   __syncthreads();
-  const int64_t s = s_slice[w];
   C* psi = reinterpret_cast<C*>(a.psi);
   const C* chirp = reinterpret_cast<const C*>(g.chirp);
   const C* tw = reinterpret_cast<const C*>(g.tw);
-  const int64_t base = s * g.slice_stride;
-  const uint64_t la = s_la[w], c0 = s_c0[w];
 
-  C v[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int i = j + r * TPS;
+  // load + kinetic pre-phase into shared memory (element loop, low register
+  // pressure), then every thread picks up its 16 elements
+  const int NT = blockDim.x;
+  C* smc = reinterpret_cast<C*>(smraw);
+  C* xs0 = smc + (size_t)W * 2 * g.sb;
+  for (int e = t; e < W * N; e += NT) {
+    int ww, i;
+    if (a.strided) { ww = e % W; i = e / W; } else { ww = e / N; i = e - ww * N; }
+    const int64_t ss = s_slice[ww];
     C x = czero<C>();
-    if (s >= 0 && i < Q) {
-      x = psi[base + (int64_t)i * g.ea];
+    if (i < Q && ss >= 0) {
+      x = psi[ss * g.slice_stride + (int64_t)i * g.ea];
       int64_t units = a.units_pre;
       if (lazy) {
         const int32_t t2 = a.touch_other[i];
-        units = (int64_t)a.now - (int64_t)(s_touch[w] > t2 ? s_touch[w] : t2);
+        units = (int64_t)a.now - (int64_t)(s_touch[ww] > t2 ? s_touch[ww] : t2);
       }
       if (units != 0) {
         const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);
-        const uint64_t qd = g.A_aa * (m * m) + la * m + c0;
+        const uint64_t qd = g.A_aa * (m * m) + s_la[ww] * m + s_c0[ww];
         x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)units * qd));
       }
-      xs[i] = x;
+      xs0[(size_t)ww * Q + i] = x;
       if (g.bluestein) x = cmul(x, chirp[i]);
+    } else if (i < Q) {
+      xs0[(size_t)ww * Q + i] = x;
     }
-    v[r] = x;
+    smc[(size_t)ww * 2 * g.sb + phys(i)] = x;
   }
-  int flip = 0;
+  __syncthreads();
+  C v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = bufA[phys(j + r * TPS)];
+  int flip = 1;  // buffer A holds the input; the first exchange uses B
   const C* T = reinterpret_cast<const C*>(a.T);
   if (g.bluestein) {
     const C* bm = reinterpret_cast<const C*>(g.bm);
@@ -816,21 +857,27 @@ pass_fast_kernel(const PassArgs a) {
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], T[j + r * TPS]);
     fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
   }
-  if (s >= 0) {
+  // correction back to shared memory, then x + correction, post-phase, store
+  {
+    C* buf = (flip & 1) ? bufB : bufA;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int i = j + r * TPS;
-      if (i < Q) {
-        C c = v[r];
-        if (g.bluestein) c = cmulconj(c, chirp[i]);
-        C x = cadd(xs[i], c);
-        if (!lazy && a.units_post != 0) {
-          const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);
-          const uint64_t qd = g.A_aa * (m * m) + la * m + c0;
-          x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)a.units_post * qd));
-        }
-        psi[base + (int64_t)i * g.ea] = x;
+    for (int r = 0; r < 16; ++r) buf[phys(j + r * TPS)] = v[r];
+    const int ob = (flip & 1) ? 1 : 0;
+    __syncthreads();
+    for (int e = t; e < W * Q; e += NT) {
+      int ww, i;
+      if (a.strided) { ww = e % W; i = e / W; } else { ww = e / Q; i = e - ww * Q; }
+      const int64_t ss = s_slice[ww];
+      if (ss < 0) continue;
+      C c = smc[(size_t)ww * 2 * g.sb + (size_t)ob * g.sb + phys(i)];
+      if (g.bluestein) c = cmulconj(c, chirp[i]);
+      C x = cadd(xs0[(size_t)ww * Q + i], c);
+      if (!lazy && a.units_post != 0) {
+        const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);
+        const uint64_t qd = g.A_aa * (m * m) + s_la[ww] * m + s_c0[ww];
+        x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)a.units_post * qd));
       }
+      psi[ss * g.slice_stride + (int64_t)i * g.ea] = x;
     }
   }
   if (lazy && t < W && s_slice[t] >= 0) a.touch_own[s_slice[t]] = a.now;
@@ -845,34 +892,41 @@ template <typename Real, int LOGN>
 static cudaError_t launch_fast_n(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
   const int nt = a.W * ((1 << LOGN) / 16);
   const size_t smem = fast_smem_bytes<Real>(a.g, a.W);
-  if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY><<<(unsigned)ntiles, nt, smem, st>>>(a);
-  else pass_fast_kernel<Real, LOGN, MODE_STEP><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  if (nt <= 256) {
+    if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256><<<(unsigned)ntiles, nt, smem, st>>>(a);
+    else pass_fast_kernel<Real, LOGN, MODE_STEP, 256><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  } else if constexpr (sizeof(Real) == 4) {
+    if (nt > 512) return cudaErrorInvalidValue;
+    if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 512><<<(unsigned)ntiles, nt, smem, st>>>(a);
+    else pass_fast_kernel<Real, LOGN, MODE_STEP, 512><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   switch (a.g.np) {
-    case 256: return launch_fast_n<Real, 8>(a, ntiles, st);
     case 512: return launch_fast_n<Real, 9>(a, ntiles, st);
     case 1024: return launch_fast_n<Real, 10>(a, ntiles, st);
     case 2048: return launch_fast_n<Real, 11>(a, ntiles, st);
     case 4096: return launch_fast_n<Real, 12>(a, ntiles, st);
-    case 8192: return launch_fast_n<Real, 13>(a, ntiles, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
   cudaError_t e = cudaSuccess;
-#define LS_FPREP(L) \
-  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP>, max_smem); \
-  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY>, max_smem);
-  LS_FPREP(8) LS_FPREP(9) LS_FPREP(10) LS_FPREP(11) LS_FPREP(12) LS_FPREP(13)
+#define LS_FPREP(L, NTM) \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, NTM>, max_smem); \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, NTM>, max_smem);
+  LS_FPREP(9, 256) LS_FPREP(10, 256) LS_FPREP(11, 256) LS_FPREP(12, 256)
+  if constexpr (sizeof(Real) == 4) { LS_FPREP(9, 512) LS_FPREP(10, 512) LS_FPREP(11, 512) LS_FPREP(12, 512) }
 #undef LS_FPREP
   return e;
 }
-template <typename Real> int fast_max_threads() { return FastTraits<Real>::kMaxNT; }
+template <typename Real> int fast_max_threads() { return sizeof(Real) == 4 ? 512 : 256; }
 
 #define LS_FOR_MODES(X, R, B) \
   X(R, B, MODE_STEP) X(R, B, MODE_LAZY) X(R, B, MODE_MEASURE) X(R, B, MODE_ADJOINT) X(R, B, MODE_KIN)
