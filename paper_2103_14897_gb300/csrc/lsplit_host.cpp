@@ -128,6 +128,11 @@ struct PassSpec {
   int64_t step;   // step index within the call
 };
 
+struct ConvTab {
+  std::shared_ptr<DevBuf> khat;
+  double fix_re = 0, fix_im = 0;
+};
+
 struct GraphEntry {
   void* psi;
   int scheme;
@@ -158,6 +163,8 @@ struct ls_ctx {
   DevBuf tw[2], twb[2], bm[2], bp[2], chirp[2], vgrid[2];
   std::vector<double> vhost[2];
   std::map<std::pair<int, uint64_t>, std::shared_ptr<DevBuf>> ttab;  // (layer, bits(s)) -> table
+  std::map<std::pair<int, uint64_t>, ConvTab> ctab;                   // convolution-form tables
+  bool conv_form[2] = {false, false};
   DevBuf partials, result, touch_row, touch_col, seedbuf, grad[2];
   int nblk_elem = 0;
   size_t partial_count = 0;
@@ -256,6 +263,54 @@ const void* phase_table(ls_ctx* c, int layer, double s) {
   upload_c(c, *buf, T);
   c->ttab[key] = buf;
   return buf->p;
+}
+
+// Convolution-form table of P_j(s) - I for a 1D layer of length q with
+// transform length N: c'_j = (1/q) sum_p (exp(-i s v_p) - 1) exp(-2 pi i j p / q)
+// (FP64, exact integer-reduced angles), wrapped into N entries (d >= 0 at d,
+// d < 0 at N + d; with N = 2q - 2 index q - 1 keeps c'_{q-1}), then
+// Khat = FFT_N / N.
+const ConvTab& conv_table(ls_ctx* c, int layer, double s);
+
+const ConvTab& conv_table(ls_ctx* c, int layer, double s) {
+  uint64_t bits;
+  std::memcpy(&bits, &s, 8);
+  auto key = std::make_pair(layer, bits);
+  auto it = c->ctab.find(key);
+  if (it != c->ctab.end()) return it->second;
+  const std::vector<double>& v = c->vhost[layer - 1];
+  const int q = (int)v.size();
+  const int N = c->geom[layer - 1].np;
+  std::vector<cd> tm1(q), roots(q), cp(q);
+  for (int p2 = 0; p2 < q; ++p2) {
+    const double h = -0.5 * s * v[p2];
+    tm1[p2] = cd(0.0, 2.0 * std::sin(h)) * cd(std::cos(h), std::sin(h));
+    const double ang = -2.0 * kPi * (double)p2 / (double)q;
+    roots[p2] = cd(std::cos(ang), std::sin(ang));
+  }
+  for (int j = 0; j < q; ++j) {
+    cd acc(0, 0);
+    for (int p2 = 0; p2 < q; ++p2) acc += tm1[p2] * roots[(int)(((int64_t)j * p2) % q)];
+    cp[j] = acc / (double)q;
+  }
+  std::vector<cd> K(N, cd(0, 0));
+  for (int d = -(q - 1); d <= q - 1; ++d) {
+    const int idx = d >= 0 ? d : N + d;
+    const cd val = cp[((d % q) + q) % q];
+    if (d < 0 && idx == q - 1) continue;  // N = 2q - 2: index q-1 keeps c'_{q-1}
+    K[idx] = val;
+  }
+  ConvTab t;
+  if (N == 2 * q - 2 && q > 1) {
+    const cd f = cp[1 % q] - cp[q - 1];
+    t.fix_re = f.real();
+    t.fix_im = f.imag();
+  }
+  fft64(K, false);
+  for (auto& x : K) x /= (double)N;
+  t.khat = std::make_shared<DevBuf>();
+  upload_c(c, *t.khat, K);
+  return c->ctab[key] = t;
 }
 
 // Kinetic fixed-point coefficients for one unit of duration u: phase in turns
@@ -504,12 +559,24 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     if (!stoch) {
       a.mode = lsk::MODE_STEP;
       a.T = phase_table(c, q.layer, q.s);
+      if (c->conv_form[L]) {
+        const ConvTab& ct = conv_table(c, q.layer, q.s);
+        a.Khat = ct.khat->p;
+        a.fix0_re = ct.fix_re;
+        a.fix0_im = ct.fix_im;
+      }
       a.units_pre = q.pre;
       a.units_post = q.post;
       LS_CUDA(launch(c, a, L, S, st));
     } else {
       a.mode = lsk::MODE_LAZY;
       a.T = phase_table(c, q.layer, q.s * (double)S / (double)p);
+      if (c->conv_form[L]) {
+        const ConvTab& ct = conv_table(c, q.layer, q.s * (double)S / (double)p);
+        a.Khat = ct.khat->p;
+        a.fix0_re = ct.fix_re;
+        a.fix0_im = ct.fix_im;
+      }
       a.list = (const int32_t*)lists->p + (int64_t)i * sa.pmax;
       a.nlist = p;
       a.touch_own = (int32_t*)(L == 0 ? c->touch_row.p : c->touch_col.p);
@@ -539,7 +606,9 @@ void prepare_tables(ls_ctx* c, int64_t n, double tau, int scheme) {
   for (const PassSpec& q : ps) {
     const int64_t S = c->geom[q.layer - 1].nslices;
     const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
-    phase_table(c, q.layer, stoch ? q.s * (double)S / (double)p : q.s);
+    const double sd = stoch ? q.s * (double)S / (double)p : q.s;
+    phase_table(c, q.layer, sd);
+    if (c->conv_form[q.layer - 1]) conv_table(c, q.layer, sd);
   }
 }
 
@@ -687,6 +756,11 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
                           (size_t)dev_max)
         --W;
       c->fastW[L] = W;
+      // convolution form of the potential factor for Bluestein-length slices
+      // (two transforms instead of four); LSPLIT_TRANSFORM=bluestein keeps the
+      // chirp-z form
+      const char* tf = std::getenv("LSPLIT_TRANSFORM");
+      c->conv_form[L] = W > 0 && g.bluestein && !(tf && std::string(tf) == "bluestein");
     }
     const size_t smax = (size_t)std::max(c->M1, c->M2) * 5;
     if (smax > 48 * 1024) LS_CUDA(lsk::sampler_prepare(block_max));

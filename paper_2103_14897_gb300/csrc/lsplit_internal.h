@@ -59,6 +59,13 @@ struct PassArgs {
   double* partials;        // per-CTA partial sums (MODE_MEASURE)
   double* grad;            // M doubles (MODE_ADJOINT), accumulated atomically
   double sdur;             // duration s of the factor (MODE_ADJOINT)
+  // Convolution form of a potential factor (1D slices of length q < N):
+  // (P - I) x = c' (*) x, c' = DFT_q(T - 1) / q, as a length-N cyclic
+  // convolution through FFT_N; Khat = FFT_N(wrapped c') / N.  With N = 2q - 2
+  // the wrapped kernel cannot hold both c'_{q-1} and c'_1 at index q - 1: it
+  // keeps c'_{q-1} and output 0 is fixed by fix0 * x_{q-1}, fix0 = c'_1 - c'_{q-1}.
+  const void* Khat;        // N entries (complex Real); NULL: Bluestein form
+  double fix0_re, fix0_im;
 };
 
 struct ElemArgs {          // elementwise kernels over the whole lifted box

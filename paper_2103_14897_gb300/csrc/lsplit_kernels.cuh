@@ -823,7 +823,7 @@ pass_fast_kernel(const PassArgs a) {
         x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)units * qd));
       }
       xs0[(size_t)ww * Q + i] = x;
-      if (g.bluestein) x = cmul(x, chirp[i]);
+      if (g.bluestein && a.Khat == nullptr) x = cmul(x, chirp[i]);
     } else if (i < Q) {
       xs0[(size_t)ww * Q + i] = x;
     }
@@ -835,7 +835,15 @@ pass_fast_kernel(const PassArgs a) {
   for (int r = 0; r < 16; ++r) v[r] = bufA[phys(j + r * TPS)];
   int flip = 1;  // buffer A holds the input; the first exchange uses B
   const C* T = reinterpret_cast<const C*>(a.T);
-  if (g.bluestein) {
+  const bool conv = g.bluestein && a.Khat != nullptr;
+  if (conv) {
+    // cyclic convolution of the zero-padded slice with the wrapped kernel
+    const C* Kh = reinterpret_cast<const C*>(a.Khat);
+    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], Kh[j + r * TPS]);
+    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+  } else if (g.bluestein) {
     const C* bm = reinterpret_cast<const C*>(g.bm);
     const C* bp = reinterpret_cast<const C*>(g.bp);
     fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
@@ -870,7 +878,16 @@ pass_fast_kernel(const PassArgs a) {
       const int64_t ss = s_slice[ww];
       if (ss < 0) continue;
       C c = smc[(size_t)ww * 2 * g.sb + (size_t)ob * g.sb + phys(i)];
-      if (g.bluestein) c = cmulconj(c, chirp[i]);
+      if (conv) {
+        if (i == 0) {
+          C f;
+          f.x = (Real)a.fix0_re;
+          f.y = (Real)a.fix0_im;
+          c = cadd(c, cmul(f, xs0[(size_t)ww * Q + Q - 1]));
+        }
+      } else if (g.bluestein) {
+        c = cmulconj(c, chirp[i]);
+      }
       C x = cadd(xs0[(size_t)ww * Q + i], c);
       if (!lazy && a.units_post != 0) {
         const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);

@@ -76,10 +76,16 @@ def test_gaussian_initial_state(P, dtype):
         assert np.all(got[~O.index_mask(p)] == 0)
 
 
+@pytest.mark.parametrize("form", ["convolution", "bluestein"])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
-def test_step_parity_1d(P, dtype, scheme):
-    for p in problems_1d():
+def test_step_parity_1d(P, dtype, scheme, form, monkeypatch):
+    """Both forms of the potential factor for odd slice lengths: the cyclic
+    convolution through one power-of-two transform pair, and the chirp-z
+    (Bluestein) transform to the real-space grid and back."""
+    if form == "bluestein":
+        monkeypatch.setenv("LSPLIT_TRANSFORM", "bluestein")
+    for p in problems_1d() + [W.bilayer_1d(1024, 20, 1.1, 0.7, ecut=1e9)]:
         ctx = P.Context(p, dtype)
         x = W.random_state((p.M2, p.M1), 1)
         psi = ctx.from_dense(x)
