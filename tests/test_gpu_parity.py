@@ -94,7 +94,10 @@ def test_step_parity_1d(P, dtype, scheme, form, monkeypatch):
             ctx.step(psi, n, tau, scheme)
             got = ctx.to_dense(psi)
             ref = O.step(p, x, tau, scheme, n)
-            assert rel(got, ref) < TOL1[dtype] * (1 if n == 1 else 3), (p.name, n, rel(got, ref))
+            # the FP64 oracle's own phase error grows with tau |k|^2 / 2
+            th = tau * float(O.kinetic_energy_diag(p).max()) * n
+            tol = TOL1[dtype] * (1 if n == 1 else 3) + (4e-16 * th if dtype == "c128" else 0.0)
+            assert rel(got, ref) < tol, (p.name, n, rel(got, ref))
             assert np.all(psi[:, p.M1:].cpu().numpy() == 0)   # padding untouched
 
 
