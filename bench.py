@@ -165,6 +165,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_case(args):
+    """Smaller-than-bench ncu target whose array exceeds L2: a 2049 x 8192 lifted
+    box (134 MB complex64; layer-1 slices of length 2049 use the same
+    convolution-form pass as the bench workload).  Runs --steps Strang steps."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    import paper_2103_14897_gb300 as P
+    p = W.Problem(1, np.array([[2 * math.pi]]), np.array([[2 * math.pi / W.GOLDEN]]), (-1024,), (2049,),
+                  (-4096,), (8192,), 1e12, np.array([[1], [-1]]), np.array([0.6, 0.6], dtype=complex),
+                  np.array([[1], [-1]]), np.array([0.45, 0.45], dtype=complex), "bilayer1d-2049x8192")
+    ctx = P.Context(p, "c64")
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
+    ctx.step(psi, args.steps, TAU, args.scheme)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": p.name, "steps": args.steps, "norm": ctx.observables(psi)["norm"]}))
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -325,10 +344,14 @@ def main():
     ap.add_argument("--scheme", default="strang")
     ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the 2049x8192 ncu target instead of the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -53,24 +53,18 @@ template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y =
 // power-of-two strides of the first Stockham stages across banks.
 __device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
 
-// Multiplication by exp(2 pi i t / 2^64) for a fixed-point angle t.  The
-// nearest quadrant is removed exactly with integer arithmetic (a multiple of
-// i); the remainder phi (|phi| <= pi/4) is applied
-//  * in single precision as three shears (x -= tan(phi/2) y; y += sin(phi) x;
-//    x -= tan(phi/2) y).  Each shear has determinant one whatever the rounded
-//    coefficients, so the rotation cannot scale |x| systematically: the same
-//    angle recurs at every step for a given element, and a factor (c, s) with
-//    c^2 + s^2 = 1 + O(eps) would grow the norm linearly in the step count.
-//    The float argument of sincospi is rounded; the exact integer residual of
-//    that rounding is added to first order;
-//  * in double precision as a product with (cos phi, sin phi).
-template <typename Real> struct Phase;
-template <> struct Phase<float> {
-  float a, b;  // tan(phi/2), sin(phi)
-  int q;       // quadrant
-};
-template <> struct Phase<double> {
-  double2 v;
+// exp(2 pi i t / 2^64) for a fixed-point angle t.  The nearest quadrant is
+// removed exactly with integer arithmetic; the remainder (|angle| <= pi/4)
+// goes to sincospi.  In single precision two systematic errors are removed,
+// because the same angle recurs at every step for a given element:
+//  * the float argument is rounded; the exact integer residual of that
+//    rounding (< 2^-24 relative) rotates the result to first order;
+//  * |(c, s)| differs from 1 by O(eps); the deviation e = c^2 + s^2 - 1 is
+//    computed with error-free products and returned, and the caller scales the
+//    product x * (c, s) by (1 - e/2) with one fused rounding.
+template <typename Real> struct Phase {
+  typename CT<Real>::C v;
+  Real half_e;  // (c^2 + s^2 - 1) / 2
 };
 
 template <typename Real> __device__ __forceinline__ Phase<Real> phase_of(uint64_t t);
@@ -80,17 +74,22 @@ template <> __device__ __forceinline__ Phase<float> phase_of<float>(uint64_t t) 
   const int rhi = (int)(r >> 32);
   const float xf = (float)rhi;                  // may round (|rhi| <= 2^29)
   const int64_t resid = r - ((int64_t)(int)xf << 32);
-  float sh, ch;
-  sincospif(xf * 0x1p-32f, &sh, &ch);           // half angle: pi * xf / 2^32
-  const float d = (float)resid * 0x1.921fb6p-62f;  // residual angle (radians)
-  float ta = __fdividef(sh, ch);
-  float sb = 2.0f * sh * ch;
-  ta = fmaf(0.5f * d, fmaf(ta, ta, 1.0f), ta);  // tan((phi + d)/2), first order
-  sb = fmaf(d, (ch - sh) * (ch + sh), sb);      // sin(phi + d), first order
+  float s, c;
+  sincospif(xf * 0x1p-31f, &s, &c);             // angle pi * xf / 2^31
+  const float d = (float)resid * 0x1.921fb6p-62f;  // residual angle in radians (2 pi / 2^64)
+  const float c1 = fmaf(-d, s, c), s1 = fmaf(d, c, s);
+  // explicit round-to-nearest operations: no contraction may merge c2h - 1
+  const float c2h = __fmul_rn(c1, c1), c2l = fmaf(c1, c1, -c2h);
+  const float s2h = __fmul_rn(s1, s1), s2l = fmaf(s1, s1, -s2h);
+  const float e = __fadd_rn(__fadd_rn(__fadd_rn(c2h, -1.0f), s2h), __fadd_rn(c2l, s2l));
   Phase<float> p;
-  p.a = ta;
-  p.b = sb;
-  p.q = (int)(q & 3);
+  switch (q & 3) {
+    case 0: p.v = make_float2(c1, s1); break;
+    case 1: p.v = make_float2(-s1, c1); break;
+    case 2: p.v = make_float2(-c1, -s1); break;
+    default: p.v = make_float2(s1, -c1); break;
+  }
+  p.half_e = 0.5f * e;
   return p;
 }
 template <> __device__ __forceinline__ Phase<double> phase_of<double>(uint64_t t) {
@@ -106,22 +105,36 @@ template <> __device__ __forceinline__ Phase<double> phase_of<double>(uint64_t t
     case 2: p.v = make_double2(-c, -s); break;
     default: p.v = make_double2(s, -c); break;
   }
+  p.half_e = 0.0;
   return p;
+}
+
+// x * exp(i angle) with the modulus deviation of the phase removed.
+// In single precision the product is formed error-free (two-product and
+// two-sum transforms, explicit round-to-nearest intrinsics so nothing is
+// contracted), the factor (1 - e/2) is applied to the exact value and each
+// component is rounded once.  A correction of e/2 ~ eps applied after a
+// rounded product would itself round away, leaving the per-element bias of
+// |(c, s)| in place at every step.
+__device__ __forceinline__ float dot2_fix(float a, float c, float b, float s, float h) {
+  // a*c + b*s, times (1 - h), single final rounding
+  const float p = __fmul_rn(a, c), pe = fmaf(a, c, -p);
+  const float q = __fmul_rn(b, s), qe = fmaf(b, s, -q);
+  const float r = __fadd_rn(p, q);
+  const float bb = __fsub_rn(r, p);
+  const float re = __fadd_rn(__fsub_rn(p, __fsub_rn(r, bb)), __fsub_rn(q, bb));
+  const float lo = __fadd_rn(__fadd_rn(re, __fadd_rn(pe, qe)), -__fmul_rn(h, r));
+  return __fadd_rn(r, lo);
 }
 
 template <typename Real>
 __device__ __forceinline__ typename CT<Real>::C apply_phase(typename CT<Real>::C x, const Phase<Real>& p);
 template <>
 __device__ __forceinline__ float2 apply_phase<float>(float2 x, const Phase<float>& p) {
-  float u = fmaf(-p.a, x.y, x.x);
-  const float w = fmaf(p.b, u, x.y);
-  u = fmaf(-p.a, w, u);
-  switch (p.q) {
-    case 0: return make_float2(u, w);
-    case 1: return make_float2(-w, u);
-    case 2: return make_float2(-u, -w);
-    default: return make_float2(w, -u);
-  }
+  float2 y;
+  y.x = dot2_fix(x.x, p.v.x, -x.y, p.v.y, p.half_e);
+  y.y = dot2_fix(x.x, p.v.y, x.y, p.v.x, p.half_e);
+  return y;
 }
 template <>
 __device__ __forceinline__ double2 apply_phase<double>(double2 x, const Phase<double>& p) {
@@ -648,6 +661,12 @@ __device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typenam
   using C = typename CT<Real>::C;
   constexpr int N = 1 << LOGN, TPS = N / 16;
   if constexpr (S < fast_nstages(LOGN)) {
+    // twiddle bases of stage S are fetched before the exchange so that their
+    // latency overlaps the shared-memory round trip and the barrier
+    constexpr int R0 = fast_radix(LOGN, S), ns0 = fast_ns(LOGN, S);
+    C wb[16 / R0];
+#pragma unroll
+    for (int u = 0; u < 16 / R0; ++u) wb[u] = tw[((j + u * TPS) & (ns0 - 1)) * (N / (ns0 * R0))];
     // write the outputs of stage S-1, then read the inputs of stage S
     constexpr int Rp = fast_radix(LOGN, S - 1), nsp = fast_ns(LOGN, S - 1);
 #pragma unroll
@@ -665,8 +684,7 @@ __device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typenam
       const int b = j + u * TPS;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[u * R + r] = buf[phys(b + r * (N / R))];
-      const int k = b & (ns - 1);
-      twiddle_pow<R, Real, INV>(v + u * R, tw[k * (N / (ns * R))]);
+      twiddle_pow<R, Real, INV>(v + u * R, wb[u]);
       dftRR<R, C, INV>(v + u * R);
     }
   }
@@ -677,7 +695,16 @@ __device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typenam
 template <typename Real, int LOGN, bool INV>
 __device__ __forceinline__ void fast_fft(typename CT<Real>::C (&v)[16], typename CT<Real>::C* bufA,
                                          typename CT<Real>::C* bufB, int& flip,
-                                         const typename CT<Real>::C* __restrict__ tw, int j) {
+                                         const typename CT<Real>::C* __restrict__ tw, int j,
+                                         const typename CT<Real>::C* __restrict__ pre = nullptr) {
+  // pre: a table read right after this transform at j + r N/16; its lines are
+  // prefetched into L1 here so the loads after the last stage hit
+  if (pre) {
+#pragma unroll
+    for (int r = 0; r < 16; r += 4) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(pre + j + r * ((1 << LOGN) / 16)));
+    }
+  }
   using C = typename CT<Real>::C;
   constexpr int N = 1 << LOGN, TPS = N / 16;
   constexpr int NS = fast_nstages(LOGN);
@@ -792,6 +819,7 @@ pass_fast_kernel(const PassArgs a) {
   const int NT = blockDim.x;
   C* smc = reinterpret_cast<C*>(smraw);
   C* xs0 = smc + (size_t)W * 2 * g.sb;
+#pragma unroll 4
   for (int e = t; e < W * N; e += NT) {
     int ww, i;
     if (a.strided) { ww = e % W; i = e / W; } else { ww = e / N; i = e - ww * N; }
@@ -826,7 +854,7 @@ pass_fast_kernel(const PassArgs a) {
   if (conv) {
     // cyclic convolution of the zero-padded slice with the wrapped kernel
     const C* Kh = reinterpret_cast<const C*>(a.Khat);
-    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j, Kh);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], Kh[j + r * TPS]);
     fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
@@ -859,6 +887,7 @@ pass_fast_kernel(const PassArgs a) {
     for (int r = 0; r < 16; ++r) buf[phys(j + r * TPS)] = v[r];
     const int ob = (flip & 1) ? 1 : 0;
     __syncthreads();
+#pragma unroll 4
     for (int e = t; e < W * Q; e += NT) {
       int ww, i;
       if (a.strided) { ww = e % W; i = e / W; } else { ww = e / Q; i = e - ww * Q; }
