@@ -747,7 +747,7 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
       const int tps = g.np / 16;
       // contiguous slices: 256-thread CTAs (several per SM); strided slices:
       // up to the 512-thread variant so a CTA reads wider row segments
-      const int maxnt = (L == 0 || c->dtype != LS_C64) ? 256 : lsk::fast_max_threads<float>();
+      const int maxnt = 256;  // one slice per 256-thread CTA measured fastest for both layers
       const char* ev = std::getenv(L == 0 ? "LSPLIT_FAST_NT1" : "LSPLIT_FAST_NT2");
       const int cap = ev ? std::max(tps, std::min(std::atoi(ev), lsk::fast_max_threads<float>())) : maxnt;
       const int ntcap = c->dtype == LS_C64 ? cap : std::min(cap, 256);
