@@ -174,6 +174,24 @@ int ls_adjoint(ls_ctx* ctx, void* psi_dev, void* lam_dev, int64_t nsteps, double
                int32_t scheme, double* grad_v1_host, double* grad_v2_host,
                double* grad_c1_host, double* grad_c2_host, void* stream);
 
+/* Mass N = sum |phi|^2 (FP64) of a wave-function array, computed WITHOUT
+ * allocating memory: for callers that cannot call cudaMalloc (work issued while
+ * a stream is captured into a CUDA graph, hosts that own all device memory
+ * through their own pool, loops that must not touch the allocator).  The paper
+ * has no counterpart; the same quantity is ls_observables()->norm.
+ *   psi_dev   device array, rows x cols used elements, row pitch `pitch`
+ *             elements (the ls_layout() layout: rows = M2, cols = M1)
+ *   dtype     LS_C64 or LS_C128
+ *   out_dev   device double (caller-owned) that receives the mass
+ * Scratch is a fixed file-scope device array of 65536 FP64 row sums (512 KB,
+ * held by every GPU that loads the library until the process exits); rows >
+ * 65536 return LS_ERR_INVALID.  The first call on a device looks up that
+ * array's device address (make it before any stream capture).  All calls share
+ * the array: calls that overlap on the GPU race and must be ordered by the
+ * caller.  Needs no context; enqueued on stream, no synchronisation. */
+int ls_mass_noalloc(const void* psi_dev, int32_t dtype, int64_t rows, int64_t cols, int64_t pitch,
+                    double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

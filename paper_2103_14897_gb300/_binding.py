@@ -23,7 +23,8 @@ SCHEMES = {"lie": 0, "strang": 1, "strang_kp": 2, "lie_stoch": 3, "strang_stoch"
 
 # Every entry point declared in include/lsplit.h.
 EXPORTS = ["ls_last_error", "ls_create", "ls_destroy", "ls_layout", "ls_index_set",
-           "ls_init_gaussian", "ls_step", "ls_observables", "ls_samples", "ls_adjoint"]
+           "ls_init_gaussian", "ls_step", "ls_observables", "ls_samples", "ls_adjoint",
+           "ls_mass_noalloc"]
 
 
 class LsProblem(C.Structure):
@@ -78,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     lib.ls_samples.argtypes = [vp, i32, u64, u64, i32, C.POINTER(i32), C.POINTER(i32), vp]
     lib.ls_adjoint.argtypes = [vp, vp, vp, i64, dbl, i32, C.POINTER(dbl), C.POINTER(dbl),
                                C.POINTER(dbl), C.POINTER(dbl), vp]
+    lib.ls_mass_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp]
     for name in EXPORTS[1:]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -234,3 +236,11 @@ class Context:
                                c1.ctypes.data_as(P) if len(c1) else None,
                                c2.ctypes.data_as(P) if len(c2) else None, _stream_handle(stream)))
         return g1, g2, c1.reshape(-1, 2), c2.reshape(-1, 2)
+
+
+def mass_noalloc(psi, dtype: str, rows: int, cols: int, pitch: int, out, stream=None) -> None:
+    """ls_mass_noalloc: sum |psi|^2 into the device double ``out`` without any
+    allocation inside the library (fixed device scratch, rows <= 65536)."""
+    lib = load_library()
+    _check(lib.ls_mass_noalloc(_ptr(psi), LS_C64 if dtype == "c64" else LS_C128, int(rows), int(cols),
+                               int(pitch), _ptr(out), _stream_handle(stream)))

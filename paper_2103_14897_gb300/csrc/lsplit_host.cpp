@@ -147,6 +147,10 @@ struct GraphEntry {
 
 }  // namespace
 
+namespace lsk {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace lsk
+
 struct ls_ctx {
   ls_problem p{};
   std::vector<int32_t> h1, h2;

@@ -4,6 +4,8 @@
 #include <stdint.h>
 #include <cuda_runtime.h>
 
+#include <string>
+
 namespace lsk {
 
 constexpr int kMaxTileSlices = 64;   // W: slices per CTA (upper bound)
@@ -114,6 +116,9 @@ template <typename Real> cudaError_t fast_prepare(size_t max_smem);
 template <typename Real> int fast_max_threads();
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
 cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
+
+// Message returned by ls_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 constexpr int kObsQ = 8;   // norm, ekin, k0, k1, ovl_re, ovl_im, spare, spare
 constexpr int kReduceBlocks = 1024;
