@@ -174,6 +174,37 @@ int ls_adjoint(ls_ctx* ctx, void* psi_dev, void* lam_dev, int64_t nsteps, double
                int32_t scheme, double* grad_v1_host, double* grad_v2_host,
                double* grad_c1_host, double* grad_c2_host, void* stream);
 
+/* ---- batched uneven instances (one persistent launch per call) ----
+ * A batch is a set of independent problems (same dtype, any boxes) whose wave
+ * functions live in one caller-owned device buffer: instance i starts at
+ * element offsets[i] (ls_batch_layout; offsets has count+1 entries, the last
+ * being the total element count) with row pitch pitches[i]. */
+typedef struct ls_batch ls_batch;
+
+/* Create count instances (an ls_create per problem, same dtype required). */
+int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out);
+int ls_batch_destroy(ls_batch* batch);
+/* offsets: count+1 int64 (host), pitches: count int64 (host); either may be NULL. */
+int ls_batch_layout(const ls_batch* batch, int64_t* offsets, int64_t* pitches);
+/* ls_init_gaussian for every instance (same x0, w, k0). */
+int ls_batch_init_gaussian(ls_batch* batch, void* psi_dev, const double* x0_host, double w,
+                           const double* k0_host, void* stream);
+/* nsteps steps of tau of a deterministic scheme (LS_LIE, LS_STRANG,
+ * LS_STRANG_KP) for every instance in ONE persistent kernel launch (replayed
+ * from a cached CUDA graph): CTAs claim (step, pass, instance, slice-tile)
+ * items in order and wait, with a bounded spin, until their instance has
+ * finished the previous pass.  Synchronises the stream to read the status:
+ * LS_ERR_TIMEOUT if a wait expired (psi is then incomplete; the batch stays
+ * usable). */
+int ls_batch_step(ls_batch* batch, void* psi_dev, int64_t nsteps, double tau, int32_t scheme,
+                  void* stream);
+/* ls_observables for every instance; out: count ls_obs (host).  Synchronises. */
+int ls_batch_observables(ls_batch* batch, const void* psi_dev, ls_obs* out_host, void* stream);
+/* Wait budget of one dependency wait (seconds, default 1) and a test hook that
+ * makes one wait unsatisfiable (unmet_dependency != 0) to exercise the
+ * timeout path. */
+int ls_batch_debug(ls_batch* batch, int32_t unmet_dependency, double timeout_seconds);
+
 /* Mass N = sum |phi|^2 (FP64) of a wave-function array, computed WITHOUT
  * allocating memory: for callers that cannot call cudaMalloc (work issued while
  * a stream is captured into a CUDA graph, hosts that own all device memory

@@ -24,7 +24,8 @@ SCHEMES = {"lie": 0, "strang": 1, "strang_kp": 2, "lie_stoch": 3, "strang_stoch"
 # Every entry point declared in include/lsplit.h.
 EXPORTS = ["ls_last_error", "ls_create", "ls_destroy", "ls_layout", "ls_index_set",
            "ls_init_gaussian", "ls_step", "ls_observables", "ls_samples", "ls_adjoint",
-           "ls_mass_noalloc"]
+           "ls_mass_noalloc", "ls_batch_create", "ls_batch_destroy", "ls_batch_layout",
+           "ls_batch_init_gaussian", "ls_batch_step", "ls_batch_observables", "ls_batch_debug"]
 
 
 class LsProblem(C.Structure):
@@ -80,6 +81,13 @@ def load_library(path: str = LIB_PATH):
     lib.ls_adjoint.argtypes = [vp, vp, vp, i64, dbl, i32, C.POINTER(dbl), C.POINTER(dbl),
                                C.POINTER(dbl), C.POINTER(dbl), vp]
     lib.ls_mass_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp]
+    lib.ls_batch_create.argtypes = [C.POINTER(LsProblem), i32, C.POINTER(vp)]
+    lib.ls_batch_destroy.argtypes = [vp]
+    lib.ls_batch_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    lib.ls_batch_init_gaussian.argtypes = [vp, vp, C.POINTER(dbl), dbl, C.POINTER(dbl), vp]
+    lib.ls_batch_step.argtypes = [vp, vp, i64, dbl, i32, vp]
+    lib.ls_batch_observables.argtypes = [vp, vp, C.POINTER(LsObs), vp]
+    lib.ls_batch_debug.argtypes = [vp, i32, dbl]
     for name in EXPORTS[1:]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -244,3 +252,75 @@ def mass_noalloc(psi, dtype: str, rows: int, cols: int, pitch: int, out, stream=
     lib = load_library()
     _check(lib.ls_mass_noalloc(_ptr(psi), LS_C64 if dtype == "c64" else LS_C128, int(rows), int(cols),
                                int(pitch), _ptr(out), _stream_handle(stream)))
+
+
+class Batch:
+    """Independent uneven instances in one device buffer (ls_batch_*)."""
+
+    def __init__(self, probs, dtype: str = "c64"):
+        lib = load_library()
+        self.probs = list(probs)
+        self.dtype = dtype
+        arr = (LsProblem * len(self.probs))()
+        keep = []
+        for i, p in enumerate(self.probs):
+            st, k = make_problem_struct(p, dtype)
+            arr[i] = st
+            keep.append(k)
+        h = C.c_void_p()
+        _check(lib.ls_batch_create(arr, len(self.probs), C.byref(h)))
+        self._h = h
+        n = len(self.probs)
+        off = (C.c_int64 * (n + 1))()
+        pit = (C.c_int64 * n)()
+        _check(lib.ls_batch_layout(self._h, off, pit))
+        self.offsets = [off[i] for i in range(n + 1)]
+        self.pitches = [pit[i] for i in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.ls_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, device="cuda"):
+        import torch
+        dt = torch.complex64 if self.dtype == "c64" else torch.complex128
+        return torch.zeros(self.offsets[-1], dtype=dt, device=device)
+
+    def view(self, psi, i):
+        p = self.probs[i]
+        seg = psi[self.offsets[i]:self.offsets[i] + self.pitches[i] * p.M2]
+        return seg.view(p.M2, self.pitches[i])[:, :p.M1]
+
+    def set_dense(self, psi, i, phi):
+        import torch
+        dt = torch.complex64 if self.dtype == "c64" else torch.complex128
+        self.view(psi, i).copy_(torch.from_numpy(np.asarray(phi)).to(dt))
+
+    def get_dense(self, psi, i):
+        return self.view(psi, i).cpu().numpy().astype(np.complex128)
+
+    def init_gaussian(self, psi, x0, w, k0, stream=None):
+        x0 = np.ascontiguousarray(np.asarray(x0, dtype=np.float64).reshape(-1))
+        k0 = np.ascontiguousarray(np.asarray(k0, dtype=np.float64).reshape(-1))
+        _check(_lib.ls_batch_init_gaussian(self._h, _ptr(psi), x0.ctypes.data_as(C.POINTER(C.c_double)),
+                                           float(w), k0.ctypes.data_as(C.POINTER(C.c_double)),
+                                           _stream_handle(stream)))
+
+    def step(self, psi, nsteps, tau, scheme="strang", stream=None):
+        _check(_lib.ls_batch_step(self._h, _ptr(psi), int(nsteps), float(tau), SCHEMES[scheme],
+                                  _stream_handle(stream)))
+
+    def observables(self, psi, stream=None):
+        out = (LsObs * len(self.probs))()
+        _check(_lib.ls_batch_observables(self._h, _ptr(psi), out, _stream_handle(stream)))
+        return [{"norm": o.norm, "energy": o.energy} for o in out]
+
+    def debug(self, unmet: bool, timeout_s: float = 1.0):
+        _check(_lib.ls_batch_debug(self._h, 1 if unmet else 0, float(timeout_s)))

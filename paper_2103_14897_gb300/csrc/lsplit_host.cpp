@@ -1040,3 +1040,277 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
 }
 
 }  // extern "C"
+
+// ====================================================================== batched runner
+struct ls_batch {
+  std::vector<ls_ctx*> inst;
+  std::vector<int64_t> off;   // element offset of each instance's array
+  int dtype = LS_C64;
+  int nthreads = 256;
+  int W[2][1] = {{0}, {0}};
+  std::vector<int> Wi[2];     // per instance and layer: slices per tile
+  DevBuf args, cum, tsteps, counters, status;
+  double timeout_s = 1.0;
+  int unmet = 0;
+  size_t smem = 0;
+  int blocks = 0;
+  int device = 0;
+  struct Cached {
+    void* psi;
+    int scheme;
+    double tau;
+    int64_t n;
+    cudaGraphExec_t exec = nullptr;
+    std::shared_ptr<DevBuf> args;
+    ~Cached() {
+      if (exec) cudaGraphExecDestroy(exec);
+    }
+  };
+  std::list<std::unique_ptr<Cached>> graphs;
+  cudaStream_t cap = nullptr;
+  ~ls_batch() {
+    graphs.clear();
+    for (ls_ctx* c : inst) ls_destroy(c);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+namespace {
+
+// Units of the kinetic factors before/after each pass for the first, middle,
+// last and only step of a call (the merging of build_passes).
+void batch_units(int scheme, int32_t u[4][3][2], int& npass, double& unit, double tau) {
+  std::memset(u, 0, sizeof(int32_t) * 24);
+  std::vector<PassSpec> ps;
+  int32_t end_time = 0;
+  for (int var = 0; var < 4; ++var) {
+    const int64_t n = var == 3 ? 1 : 3;
+    const int64_t k = var == 0 ? 0 : (var == 1 ? 1 : (var == 2 ? 2 : 0));
+    unit = build_passes(scheme, tau, n, ps, end_time);
+    npass = factors_per_step(scheme);
+    for (int q = 0; q < npass; ++q) {
+      const PassSpec& sp = ps[(size_t)(k * npass + q)];
+      u[var][q][0] = (int32_t)sp.pre;
+      u[var][q][1] = (int32_t)sp.post;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
+  g_last_error.clear();
+  if (!out || !probs || count < 1) return fail(LS_ERR_INVALID, "need probs, count >= 1 and out");
+  *out = nullptr;
+  for (int32_t i = 0; i < count; ++i) {
+    int v = validate(&probs[i]);
+    if (v != LS_OK) return v;
+    if (probs[i].dtype != probs[0].dtype) return fail(LS_ERR_INVALID, "all instances need the same dtype");
+  }
+  return guarded([&]() -> int {
+    std::unique_ptr<ls_batch> b(new ls_batch());
+    b->dtype = probs[0].dtype;
+    LS_CUDA(cudaGetDevice(&b->device));
+    int64_t total = 0;
+    for (int32_t i = 0; i < count; ++i) {
+      ls_ctx* c = nullptr;
+      int rc = ls_create(&probs[i], &c);
+      if (rc != LS_OK) return rc;
+      b->inst.push_back(c);
+      b->off.push_back(total);
+      total += c->pitch * c->M2;
+      total = (total + 31) / 32 * 32;  // 256-byte alignment for complex64
+    }
+    b->off.push_back(total);
+    // slices per tile so that every tile of every instance fits the common block size
+    size_t smem = 0;
+    for (int L = 0; L < 2; ++L) {
+      b->Wi[L].resize(count);
+      for (int32_t i = 0; i < count; ++i) {
+        const lsk::LayerGeom& g = b->inst[i]->geom[L];
+        int W = 1;
+        while (W * 2 <= lsk::kMaxTileSlices && W * 2 <= g.nslices && lsk::pass_threads(g, W * 2, 2) <= b->nthreads)
+          W *= 2;
+        if (lsk::pass_threads(g, W, 2) > b->nthreads) throw CudaError{cudaErrorInvalidValue, "slice too long for the batched runner"};
+        b->Wi[L][i] = W;
+        const size_t sm = b->dtype == LS_C64 ? lsk::pass_smem_bytes<float>(g, W, lsk::MODE_STEP)
+                                             : lsk::pass_smem_bytes<double>(g, W, lsk::MODE_STEP);
+        smem = std::max(smem, sm);
+      }
+    }
+    int dev_max = 0;
+    LS_CUDA(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    if (smem + 4096 > (size_t)dev_max) throw CudaError{cudaErrorInvalidValue, "batched tile exceeds shared memory"};
+    b->smem = smem;
+    int per_sm = 0;
+    if (b->dtype == LS_C64) LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, &per_sm));
+    else LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, &per_sm));
+    int sms = 0;
+    LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->blocks = std::max(1, per_sm) * sms;
+    b->counters.alloc((size_t)(count + 1) * sizeof(unsigned long long));
+    b->status.alloc(sizeof(int32_t));
+    LS_CUDA(cudaMemset(b->status.p, 0, sizeof(int32_t)));
+    LS_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    *out = b.release();
+    return LS_OK;
+  });
+}
+
+int ls_batch_destroy(ls_batch* b) {
+  if (!b) return LS_OK;
+  return guarded([&]() -> int {
+    cudaDeviceSynchronize();
+    delete b;
+    return LS_OK;
+  });
+}
+
+int ls_batch_layout(const ls_batch* b, int64_t* offsets, int64_t* pitches) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    if (offsets) offsets[i] = b->off[i];
+    if (pitches) pitches[i] = b->inst[i]->pitch;
+  }
+  if (offsets) offsets[b->inst.size()] = b->off.back();
+  return LS_OK;
+}
+
+int ls_batch_init_gaussian(ls_batch* b, void* psi, const double* x0, double w, const double* k0, void* stream) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
+  const size_t es = b->dtype == LS_C64 ? 8 : 16;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    int rc = ls_init_gaussian(b->inst[i], static_cast<char*>(psi) + b->off[i] * es, x0, w, k0, stream);
+    if (rc != LS_OK) return rc;
+  }
+  return LS_OK;
+}
+
+int ls_batch_observables(ls_batch* b, const void* psi, ls_obs* out, void* stream) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (!psi || !out) return fail(LS_ERR_INVALID, "NULL argument");
+  const size_t es = b->dtype == LS_C64 ? 8 : 16;
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    int rc = ls_observables(b->inst[i], static_cast<const char*>(psi) + b->off[i] * es, nullptr, &out[i], stream);
+    if (rc != LS_OK) return rc;
+  }
+  return LS_OK;
+}
+
+int ls_batch_debug(ls_batch* b, int32_t unmet_dependency, double timeout_seconds) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (!(timeout_seconds > 0) || timeout_seconds > 60) return fail(LS_ERR_INVALID, "timeout must be in (0, 60] s");
+  b->unmet = unmet_dependency ? 1 : 0;
+  b->timeout_s = timeout_seconds;
+  for (auto& g : b->graphs) (void)g;
+  b->graphs.clear();  // the hook and timeout are baked into captured graphs
+  return LS_OK;
+}
+
+int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, void* stream) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
+  if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
+  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP)
+    return fail(LS_ERR_INVALID, "the batched runner takes the deterministic schemes");
+  if (n == 0) return LS_OK;
+  if (n > (int64_t)1 << 30) return fail(LS_ERR_INVALID, "nsteps too large");
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    ls_batch::Cached* ge = nullptr;
+    for (auto& e : b->graphs)
+      if (e->psi == psi && e->scheme == scheme && e->tau == tau && e->n == n) ge = e.get();
+    const int ninst = (int)b->inst.size();
+    if (!ge) {
+      std::unique_ptr<ls_batch::Cached> e(new ls_batch::Cached());
+      e->psi = psi;
+      e->scheme = scheme;
+      e->tau = tau;
+      e->n = n;
+      lsk::BatchArgs ba;
+      std::memset(&ba, 0, sizeof(ba));
+      int npass = 0;
+      double u = 0;
+      batch_units(scheme, ba.units, npass, u, tau);
+      ba.npass = npass;
+      ba.ninst = ninst;
+      ba.nsteps = (int32_t)std::min<int64_t>(n, INT32_MAX);
+      std::vector<PassSpec> ps;
+      int32_t et = 0;
+      build_passes(scheme, tau, 1, ps, et);
+      std::vector<lsk::PassArgs> args((size_t)npass * ninst);
+      std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0);
+      const size_t es = b->dtype == LS_C64 ? 8 : 16;
+      for (int q = 0; q < npass; ++q) {
+        const int layer = ps[q].layer, L = layer - 1;
+        int64_t acc = 0;
+        for (int i = 0; i < ninst; ++i) {
+          ls_ctx* c = b->inst[i];
+          set_kinetic(c, u);
+          lsk::PassArgs a = base_args(c, L, static_cast<char*>(psi) + b->off[i] * es);
+          a.mode = lsk::MODE_STEP;
+          a.W = b->Wi[L][i];
+          a.T = phase_table(c, layer, ps[q].s);
+          args[(size_t)q * ninst + i] = a;
+          const int64_t tiles = (c->geom[L].nslices + a.W - 1) / a.W;
+          cum[(size_t)q * (ninst + 1) + i] = acc;
+          acc += tiles;
+          tsteps[i] += tiles;
+        }
+        cum[(size_t)q * (ninst + 1) + ninst] = acc;
+        ba.pass_items[q] = acc;
+        ba.step_items += acc;
+      }
+      e->args = std::make_shared<DevBuf>();
+      const size_t bytes_args = args.size() * sizeof(lsk::PassArgs);
+      const size_t bytes_cum = cum.size() * sizeof(int64_t);
+      const size_t bytes_ts = tsteps.size() * sizeof(int64_t);
+      e->args->alloc(bytes_args + bytes_cum + bytes_ts);
+      char* base = static_cast<char*>(e->args->p);
+      LS_CUDA(cudaMemcpy(base, args.data(), bytes_args, cudaMemcpyHostToDevice));
+      LS_CUDA(cudaMemcpy(base + bytes_args, cum.data(), bytes_cum, cudaMemcpyHostToDevice));
+      LS_CUDA(cudaMemcpy(base + bytes_args + bytes_cum, tsteps.data(), bytes_ts, cudaMemcpyHostToDevice));
+      ba.args = reinterpret_cast<const lsk::PassArgs*>(base);
+      ba.cum = reinterpret_cast<const int64_t*>(base + bytes_args);
+      ba.tiles_step = reinterpret_cast<const int64_t*>(base + bytes_args + bytes_cum);
+      ba.counters = static_cast<unsigned long long*>(b->counters.p);
+      ba.status = static_cast<int32_t*>(b->status.p);
+      int clk_khz = 0;
+      LS_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device));
+      ba.timeout_cycles = (long long)(b->timeout_s * (double)std::max(clk_khz, 1000000) * 1e3);
+      ba.unmet = b->unmet;
+      cudaGraph_t graph = nullptr;
+      LS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cudaMemsetAsync(b->counters.p, 0, (size_t)(ninst + 1) * sizeof(unsigned long long), b->cap);
+      if (ce == cudaSuccess)
+        ce = b->dtype == LS_C64 ? lsk::launch_batch<float>(ba, b->nthreads, b->blocks, b->smem, b->cap)
+                                : lsk::launch_batch<double>(ba, b->nthreads, b->blocks, b->smem, b->cap);
+      cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
+      if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        throw CudaError{ce != cudaSuccess ? ce : ee, "batched graph capture"};
+      }
+      cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) throw CudaError{ie, "cudaGraphInstantiate"};
+      b->graphs.push_front(std::move(e));
+      while (b->graphs.size() > 4) b->graphs.pop_back();
+      ge = b->graphs.front().get();
+    }
+    LS_CUDA(cudaGraphLaunch(ge->exec, st));
+    int32_t status = 0;
+    LS_CUDA(cudaMemcpyAsync(&status, b->status.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaStreamSynchronize(st));
+    if (status != 0) {
+      LS_CUDA(cudaMemsetAsync(b->status.p, 0, sizeof(int32_t), st));
+      LS_CUDA(cudaStreamSynchronize(st));
+      return fail(LS_ERR_TIMEOUT, "a dependency wait of the batched runner timed out; psi is incomplete");
+    }
+    return LS_OK;
+  });
+}
+
+}  // extern "C"

@@ -117,6 +117,27 @@ template <typename Real> int fast_max_threads();
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
 cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
 
+// Persistent batched runner: one launch walks the work list of
+// (step, pass, instance, slice-tile) items in order, claimed through
+// counters[0]; an item waits (bounded) until its instance has completed every
+// tile of the previous pass, counted in counters[1 + instance].
+struct BatchArgs {
+  const PassArgs* args;        // [npass][ninst], units set per step variant below
+  const int64_t* cum;          // [npass][ninst + 1] cumulative tile counts per pass
+  const int64_t* tiles_step;   // [ninst] tiles of one step of instance i
+  int64_t pass_items[4];       // tiles per pass summed over instances
+  int64_t step_items;          // tiles per step summed over passes and instances
+  int32_t ninst, npass, nsteps;
+  int32_t units[4][3][2];      // [variant: first, middle, last, only][pass][pre, post]
+  unsigned long long* counters;
+  int32_t* status;             // 0 ok, 1 a wait timed out
+  long long timeout_cycles;    // clock64() budget of one wait
+  int32_t unmet;               // test hook: one wait that nothing can satisfy
+};
+template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
+                                                  cudaStream_t st);
+template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm);
+
 // Message returned by ls_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -349,15 +349,21 @@ __device__ __forceinline__ void bluestein_conv(typename CT<Real>::C* sm, const L
 // forward transform in the table): the same operator, but the rounding of the
 // transforms only enters through the small correction term, so it does not
 // build up coherently over thousands of passes.
-template <typename Real, int BPT, int MODE>
-__global__ void __launch_bounds__(PassTraits<Real, BPT>::kMaxNT)
-pass_kernel(const PassArgs a) {
+// Global loads of the wave function: plain in the one-pass-per-launch
+// kernels; through L2 only (no L1 allocation) in the persistent batched runner,
+// where another CTA of the same launch may have written the data.
+template <bool CG, typename C> __device__ __forceinline__ C ldpsi(const C* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
+template <typename Real, int BPT, int MODE, bool CG>
+__device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   using C = typename CT<Real>::C;
   constexpr bool adj = (MODE == MODE_ADJOINT);
   constexpr bool lazy = (MODE == MODE_LAZY);
   constexpr bool kin_only = (MODE == MODE_KIN);
   constexpr bool measure = (MODE == MODE_MEASURE);
-  extern __shared__ __align__(16) unsigned char smraw[];
   const LayerGeom& g = a.g;
   const int W = a.W;
   const int M = g.M;
@@ -376,10 +382,10 @@ pass_kernel(const PassArgs a) {
   if (tid < W) {
     int64_t s = -1;
     if (a.list) {
-      const int64_t li = (int64_t)blockIdx.x * W + tid;
+      const int64_t li = tile * W + tid;
       if (li < a.nlist) s = a.list[li];
     } else {
-      s = (int64_t)blockIdx.x * W + tid;
+      s = tile * W + tid;
       if (s >= g.nslices) s = -1;
     }
     s_slice[tid] = s;
@@ -414,7 +420,7 @@ pass_kernel(const PassArgs a) {
     if (s >= 0) {
       const int ia = i % g.qa, ib = i / g.qa;
       const int64_t off = s * g.slice_stride + ia * g.ea + ib * g.eb;
-      x = psi[off];
+      x = ldpsi<CG>(psi + off);
       if (adj) xl = lam[off];
       if (!measure) {
         int64_t units = a.units_pre;
@@ -483,7 +489,7 @@ pass_kernel(const PassArgs a) {
     if (tid < 32) {
       double v = tid < (NT + 31) / 32 ? s_red[tid] : 0.0;
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (tid == 0) a.partials[blockIdx.x] = v / (double)M;
+      if (tid == 0) a.partials[tile] = v / (double)M;
     }
     return;
   } else {
@@ -548,6 +554,13 @@ pass_kernel(const PassArgs a) {
     }
     if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
   }
+}
+
+template <typename Real, int BPT, int MODE>
+__global__ void __launch_bounds__(PassTraits<Real, BPT>::kMaxNT)
+pass_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  pass_tile<Real, BPT, MODE, false>(a, (int64_t)blockIdx.x, smraw);
 }
 
 // ---------------------------------------------------------------- fast 1D pass
@@ -961,6 +974,100 @@ template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
 }
 template <typename Real> int fast_max_threads() { return sizeof(Real) == 4 ? 512 : 256; }
 
+// ---------------------------------------------------------------- batched runner
+template <typename Real, int BPT>
+__global__ void __launch_bounds__(PassTraits<Real, BPT>::kMaxNT)
+batch_kernel(const BatchArgs b) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ PassArgs s_args;
+  __shared__ long long s_item;
+  __shared__ int s_stop, s_inst, s_pass;
+  __shared__ long long s_tile;
+  const long long total = b.step_items * (long long)b.nsteps;
+  volatile int32_t* status = b.status;
+  volatile unsigned long long* done = b.counters + 1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      long long it = -1;
+      s_stop = 0;
+      if (*status == 0) it = (long long)atomicAdd(&b.counters[0], 1ull);
+      s_item = (it >= 0 && it < total) ? it : -1;
+      if (s_item >= 0) {
+        const long long k = s_item / b.step_items;
+        long long r = s_item - k * b.step_items;
+        int p = 0;
+        while (p + 1 < b.npass && r >= b.pass_items[p]) {
+          r -= b.pass_items[p];
+          ++p;
+        }
+        // instance: largest i with cum[p][i] <= r
+        const int64_t* cum = b.cum + (size_t)p * (b.ninst + 1);
+        int lo = 0, hi = b.ninst - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (cum[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        const int i = lo;
+        s_inst = i;
+        s_pass = p;
+        s_tile = r - cum[i];
+        // completed tiles of instance i needed before this pass may start
+        unsigned long long need = (unsigned long long)(k * b.tiles_step[i]);
+        for (int pp = 0; pp < p; ++pp) {
+          const int64_t* c2 = b.cum + (size_t)pp * (b.ninst + 1);
+          need += (unsigned long long)(c2[i + 1] - c2[i]);
+        }
+        if (b.unmet && i == 0 && p == 1 && k == 0) need += 1;  // test hook
+        const long long t0 = clock64();
+        unsigned int spins = 0;
+        while (done[i] < need) {
+          if (*status != 0) { s_stop = 1; break; }
+          if (clock64() - t0 > b.timeout_cycles || ++spins > (1u << 26)) {
+            atomicExch(b.status, 1);
+            s_stop = 1;
+            break;
+          }
+          __nanosleep(200);
+        }
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_item < 0 || s_stop) return;
+    // per-item arguments: the instance's pass arguments with this step's kinetic units
+    {
+      const int i = s_inst, p = s_pass;
+      const long long k = s_item / b.step_items;
+      const int var = b.nsteps == 1 ? 3 : (k == 0 ? 0 : (k == b.nsteps - 1 ? 2 : 1));
+      const int* src = reinterpret_cast<const int*>(b.args + (size_t)p * b.ninst + i);
+      int* dst = reinterpret_cast<int*>(&s_args);
+      for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / 4); w += blockDim.x) dst[w] = src[w];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_args.units_pre = b.units[var][p][0];
+        s_args.units_post = b.units[var][p][1];
+      }
+      __syncthreads();
+    }
+    pass_tile<Real, BPT, MODE_STEP, true>(s_args, s_tile, smraw);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&done[s_inst], 1ull);
+  }
+}
+
+template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
+                                                  cudaStream_t st) {
+  batch_kernel<Real, 2><<<nblocks, nthreads, smem, st>>>(b);
+  return cudaGetLastError();
+}
+
+template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm) {
+  cudaError_t e = allow_smem(batch_kernel<Real, 2>, max_smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<Real, 2>, nthreads, smem);
+}
+
 #define LS_FOR_MODES(X, R, B) \
   X(R, B, MODE_STEP) X(R, B, MODE_LAZY) X(R, B, MODE_MEASURE) X(R, B, MODE_ADJOINT) X(R, B, MODE_KIN)
 
@@ -1253,7 +1360,9 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
   template cudaError_t launch_fast<R>(const PassArgs&, int64_t, cudaStream_t);                           \
   template size_t fast_smem_bytes<R>(const LayerGeom&, int);                                             \
   template cudaError_t fast_prepare<R>(size_t);                                                          \
-  template int fast_max_threads<R>();
+  template int fast_max_threads<R>();                                                                    \
+  template cudaError_t launch_batch<R>(const BatchArgs&, int, int, size_t, cudaStream_t);               \
+  template cudaError_t batch_prepare<R>(size_t, int, size_t, int*);
 #ifdef LS_INST_REAL
 LS_INST(LS_INST_REAL)
 #endif

@@ -1,0 +1,151 @@
+"""Batched persistent runner and the autograd wrapper of the reverse sweep,
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_14897_gb300 import build as B
+    B.build()
+    import paper_2103_14897_gb300 as P
+    P.load_library()
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def uneven_batch():
+    # uneven boxes of the batched workload's kind (odd lengths, L2/L1 drawn,
+    # cos potentials), small enough for the oracle
+    return W.batch_1d(count=7, seed=4, nmin=3, nmax=40) + [W.bilayer_1d(64, 3, 1.0, 0.7, ecut=1e9)]
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
+@pytest.mark.parametrize("scheme", ["strang", "lie", "strang_kp"])
+def test_batched_runner_parity(P, dtype, tol, scheme):
+    probs = uneven_batch()
+    b = P.Batch(probs, dtype)
+    psi = b.empty()
+    xs = [W.random_state((p.M2, p.M1), 40 + i) for i, p in enumerate(probs)]
+    for i, x in enumerate(xs):
+        b.set_dense(psi, i, x)
+    b.step(psi, 3, 1e-2, scheme)
+    for i, p in enumerate(probs):
+        ref = O.step(p, xs[i], 1e-2, scheme, 3)
+        assert rel(b.get_dense(psi, i), ref) < tol * 3, (i, p.name, rel(b.get_dense(psi, i), ref))
+    # single step (the "only step" units) and a second call continuing
+    b.step(psi, 1, 1e-2, scheme)
+    for i, p in enumerate(probs):
+        ref = O.step(p, O.step(p, xs[i], 1e-2, scheme, 3), 1e-2, scheme, 1)
+        assert rel(b.get_dense(psi, i), ref) < tol * 4
+
+
+def test_batched_matches_single_contexts(P):
+    """The same instances stepped one context at a time agree with the batch."""
+    probs = W.batch_1d(count=5, seed=11, nmin=8, nmax=300)
+    b = P.Batch(probs, "c64")
+    psi = b.empty()
+    b.init_gaussian(psi, [0.0], 2.0, [1.0])
+    b.step(psi, 10, 1e-3, "strang")
+    obs = b.observables(psi)
+    for i, p in enumerate(probs):
+        c = P.Context(p, "c64")
+        x = c.empty()
+        c.init_gaussian(x, [0.0], 2.0, [1.0])
+        c.step(x, 10, 1e-3, "strang")
+        assert rel(b.get_dense(psi, i), c.to_dense(x)) < 2e-6
+        assert abs(obs[i]["norm"] - 1) < 1e-5
+
+
+def test_batched_wait_timeout_is_reported_and_recoverable(P):
+    """A dependency that nothing satisfies makes the bounded wait expire: the
+    call returns LS_ERR_TIMEOUT and the batch works again afterwards."""
+    probs = W.batch_1d(count=3, seed=2, nmin=4, nmax=20)
+    b = P.Batch(probs, "c64")
+    psi = b.empty()
+    b.debug(True, 0.2)
+    with pytest.raises(P.LsplitError) as e:
+        b.step(psi, 2, 1e-2, "strang")
+    assert e.value.code == P.LS_ERR_TIMEOUT
+    b.debug(False, 1.0)
+    xs = [W.random_state((p.M2, p.M1), 50 + i) for i, p in enumerate(probs)]
+    for i, x in enumerate(xs):
+        b.set_dense(psi, i, x)
+    b.step(psi, 2, 1e-2, "strang")
+    for i, p in enumerate(probs):
+        assert rel(b.get_dense(psi, i), O.step(p, xs[i], 1e-2, "strang", 2)) < 3e-5
+
+
+def test_autograd_overlap_gradient_matches_oracle(P):
+    import torch
+    from paper_2103_14897_gb300.autograd import overlap_loss
+    base = W.bilayer_1d(20, 16, 0.0, 0.0, ecut=1e9)
+    th1 = np.array([0.6, -0.3, 0.2, 0.1])
+    th2 = np.array([0.4, 0.25, -0.1])
+    phi0 = O.gaussian_packet(base, [0.0], 0.8, [1.0])
+    chi = O.gaussian_packet(base, [0.3], 0.8, [1.2])
+    h1, c1 = W.cos_series_coeffs(th1)
+    h2, c2 = W.cos_series_coeffs(th2)
+    prob = base.with_potentials(c1, c2, h1, h2)
+    Lref, _, g1, g2 = O.adjoint(prob, phi0, 0.02, "strang", 8, lambda f: O.overlap_loss(chi, f))
+    cg1 = O.coefficient_gradient(g1, h1, prob.q1)
+    cg2 = O.coefficient_gradient(g2, h2, prob.q2)
+    ref1 = 0.5 * (cg1[0::2, 0] + cg1[1::2, 0])
+    ref2 = 0.5 * (cg2[0::2, 0] + cg2[1::2, 0])
+    for dtype, tol in (("c64", 1e-5), ("c128", 1e-10)):
+        for ck in (0, 3):
+            t1 = torch.tensor(th1, requires_grad=True)
+            t2 = torch.tensor(th2, requires_grad=True)
+            L = overlap_loss(t1, t2, base, phi0, chi, 0.02, 8, "strang", dtype, checkpoint_every=ck)
+            L.backward()
+            assert abs(float(L) - Lref) < tol * 10
+            sc = max(np.abs(ref1).max(), np.abs(ref2).max())
+            assert np.abs(t1.grad.numpy() - ref1).max() < tol * sc * 20, (dtype, ck)
+            assert np.abs(t2.grad.numpy() - ref2).max() < tol * sc * 20, (dtype, ck)
+
+
+def test_autograd_adjoint_workload_central_differences(P):
+    """513 x 513 box, 8 cosine coefficients per layer (N(0, 0.5), seed 5),
+    overlap loss after 500 steps of tau = 1e-3: the FP32 reverse-sweep gradient
+    against central differences (h = 1e-4) of the FP64 GPU forward."""
+    import torch
+    from paper_2103_14897_gb300.autograd import overlap_loss
+    prob, th1, th2 = W.config_adjoint_1d()
+    base = prob
+    phi0 = O.gaussian_packet(base, [0.0], 2.0, [1.0])
+    chi = O.gaussian_packet(base, [0.5], 2.0, [1.2])
+    t1 = torch.tensor(th1, requires_grad=True)
+    t2 = torch.tensor(th2, requires_grad=True)
+    L = overlap_loss(t1, t2, base, phi0, chi, 1e-3, 500, "strang", "c64", checkpoint_every=100)
+    L.backward()
+    h = 1e-4
+
+    def f(a, b):
+        return float(overlap_loss(torch.tensor(a), torch.tensor(b), base, phi0, chi, 1e-3, 500, "strang", "c128"))
+    fd1, fd2 = [], []
+    for i in (0, 3, 7):
+        a, b = th1.copy(), th1.copy()
+        a[i] += h
+        b[i] -= h
+        fd1.append((f(a, th2) - f(b, th2)) / (2 * h))
+    for i in (1, 6):
+        a, b = th2.copy(), th2.copy()
+        a[i] += h
+        b[i] -= h
+        fd2.append((f(th1, a) - f(th1, b)) / (2 * h))
+    got1 = t1.grad.numpy()[[0, 3, 7]]
+    got2 = t2.grad.numpy()[[1, 6]]
+    scale = max(np.abs(fd1).max(), np.abs(fd2).max(), 1e-6)
+    assert np.abs(got1 - fd1).max() < 1e-3 * scale + 1e-7, (got1, fd1)
+    assert np.abs(got2 - fd2).max() < 1e-3 * scale + 1e-7, (got2, fd2)
