@@ -192,6 +192,97 @@ def profile_case(args):
     print(json.dumps({"workload": p.name, "steps": args.steps, "norm": ctx.observables(psi)["norm"]}))
 
 
+def _timed(fn, reps=3):
+    """Median seconds of fn() bracketed by CUDA events on the current stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return float(np.median(ts))
+
+
+def run_suite(args):
+    """Secondary workloads (parity is in tests/; these are throughput lines).
+    One JSON line each: the 65^2 FP64 case, the stochastic and other schemes on
+    the 2049^2 box, the 64^4 twisted bilayer, the 256-instance batched runner and
+    the 513^2 adjoint."""
+    import torch
+    import __graft_entry__ as G
+    G.build()
+    import paper_2103_14897_gb300 as P
+    from paper_2103_14897_gb300.autograd import overlap_loss
+    import oracle as O
+    hbm, _ = peaks()
+    out = []
+
+    def line(name, dof, steps, sec, extra):
+        d = {"workload": name, "dof": dof, "steps": steps, "seconds": sec, "dof_steps_per_s": dof * steps / sec}
+        d.update(extra)
+        out.append(d)
+        print(json.dumps(d), flush=True)
+
+    p = W.config_small_1d()
+    c = P.Context(p, "c128")
+    psi = c.empty()
+    c.init_gaussian(psi, [0.0], 2.0, [1.0])
+    t = _timed(lambda: c.step(psi, 100, 1e-3, "strang"))
+    line("bilayer1d-65x65 strang c128 tau=1e-3", p.dof, 100, t, {"norm_minus_1": c.observables(psi)["norm"] - 1})
+
+    p = W.config_scale_1d()
+    for scheme, n in (("strang_stoch", 20), ("lie_stoch", 20), ("strang_kp", 20), ("lie", 20), ("strang", 20)):
+        c = P.Context(p, "c64")
+        psi = c.empty()
+        c.init_gaussian(psi, [0.0], 2.0, [1.0])
+        t = _timed(lambda: c.step(psi, n, TAU, scheme, seed=7))
+        npass = 3 if scheme.startswith("strang") and scheme != "strang_kp" else 2
+        line(f"bilayer1d-2049x2049 {scheme} c64 tau=5e-4", p.dof, n, t,
+             {"norm_minus_1": c.observables(psi)["norm"] - 1,
+              "hbm_frac_algorithmic": (16 * p.dof * npass * n / t / 1e9) / hbm if not scheme.endswith("stoch") else None})
+
+    p = W.twisted_2d(q=64)
+    c = P.Context(p, "c64")
+    psi = c.empty()
+    c.init_gaussian(psi, [0.0, 0.0], 2.0, [1.0, 0.0])
+    t = _timed(lambda: c.step(psi, 5, 1e-3, "strang"))
+    line("twisted2d-64^4 strang c64 tau=1e-3", p.dof, 5, t,
+         {"norm_minus_1": c.observables(psi)["norm"] - 1,
+          "hbm_frac_algorithmic": (48 * p.dof * 5 / t / 1e9) / hbm})
+
+    probs = W.batch_1d()
+    b = P.Batch(probs, "c64")
+    psi = b.empty()
+    b.init_gaussian(psi, [0.0], 2.0, [1.0])
+    dof = sum(q.dof for q in probs)
+    t = _timed(lambda: b.step(psi, 10, 1e-3, "strang"), reps=2)
+    obs = b.observables(psi)
+    line("batch1d-256 uneven strang c64 tau=1e-3 (one persistent launch per call)", dof, 10, t,
+         {"max_norm_minus_1": max(abs(o["norm"] - 1) for o in obs), "instances": len(probs),
+          "hbm_frac_algorithmic": (48 * dof * 10 / t / 1e9) / hbm})
+
+    prob, th1, th2 = W.config_adjoint_1d()
+    phi0 = O.gaussian_packet(prob, [0.0], 2.0, [1.0])
+    chi = O.gaussian_packet(prob, [0.5], 2.0, [1.2])
+
+    def fb():
+        t1 = torch.tensor(th1, requires_grad=True)
+        t2 = torch.tensor(th2, requires_grad=True)
+        L = overlap_loss(t1, t2, prob, phi0, chi, 1e-3, 500, "strang", "c64", checkpoint_every=100)
+        L.backward()
+    t0 = time.perf_counter()
+    fb()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    line("adjoint bilayer1d-513x513 500 steps forward+backward c64 (host wall clock)", prob.dof, 500, t, {})
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -363,12 +454,15 @@ def main():
     ap.add_argument("--scheme", default="strang")
     ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--suite", action="store_true", help="throughput lines of the secondary workloads")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the 2049x8192 ncu target instead of the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.profile_case:
+    if args.suite:
+        run_suite(args)
+    elif args.profile_case:
         profile_case(args)
     elif args.impl == "reference":
         run_reference(args)
