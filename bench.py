@@ -260,11 +260,12 @@ def run_suite(args):
     psi = b.empty()
     b.init_gaussian(psi, [0.0], 2.0, [1.0])
     dof = sum(q.dof for q in probs)
-    t = _timed(lambda: b.step(psi, 10, 1e-3, "strang"), reps=2)
-    obs = b.observables(psi)
-    line("batch1d-256 uneven strang c64 tau=1e-3 (one persistent launch per call)", dof, 10, t,
-         {"max_norm_minus_1": max(abs(o["norm"] - 1) for o in obs), "instances": len(probs),
-          "hbm_frac_algorithmic": (48 * dof * 10 / t / 1e9) / hbm})
+    for scheme in ("strang", "strang_stoch"):
+        t = _timed(lambda: b.step(psi, 10, 1e-3, scheme, seed=3), reps=2)
+        obs = b.observables(psi)
+        line(f"batch1d-256 uneven {scheme} c64 tau=1e-3 (one persistent launch per call)", dof, 10, t,
+             {"max_norm_minus_1": max(abs(o["norm"] - 1) for o in obs), "instances": len(probs),
+              "hbm_frac_algorithmic": (48 * dof * 10 / t / 1e9) / hbm if scheme == "strang" else None})
 
     prob, th1, th2 = W.config_adjoint_1d()
     phi0 = O.gaussian_packet(prob, [0.0], 2.0, [1.0])

@@ -189,15 +189,17 @@ int ls_batch_layout(const ls_batch* batch, int64_t* offsets, int64_t* pitches);
 /* ls_init_gaussian for every instance (same x0, w, k0). */
 int ls_batch_init_gaussian(ls_batch* batch, void* psi_dev, const double* x0_host, double w,
                            const double* k0_host, void* stream);
-/* nsteps steps of tau of a deterministic scheme (LS_LIE, LS_STRANG,
- * LS_STRANG_KP) for every instance in ONE persistent kernel launch (replayed
- * from a cached CUDA graph): CTAs claim (step, pass, instance, slice-tile)
- * items in order and wait, with a bounded spin, until their instance has
- * finished the previous pass.  Synchronises the stream to read the status:
- * LS_ERR_TIMEOUT if a wait expired (psi is then incomplete; the batch stays
- * usable). */
+/* nsteps steps of tau of any scheme for every instance in ONE persistent
+ * kernel launch (replayed from a cached CUDA graph): CTAs claim
+ * (step, pass, instance, slice-tile) items in order and wait, with a bounded
+ * spin, until their instance has finished the previous pass.  Stochastic
+ * schemes: instance i draws its samples with seed + i (sub-step g as in
+ * ls_step), the sampled-slice lists are drawn on the device in the same graph,
+ * kinetic phases are applied lazily and a settle phase ends the call.
+ * Synchronises the stream to read the status: LS_ERR_TIMEOUT if a wait
+ * expired (psi is then incomplete; the batch stays usable). */
 int ls_batch_step(ls_batch* batch, void* psi_dev, int64_t nsteps, double tau, int32_t scheme,
-                  void* stream);
+                  uint64_t seed, uint64_t step0, void* stream);
 /* ls_observables for every instance; out: count ls_obs (host).  Synchronises. */
 int ls_batch_observables(ls_batch* batch, const void* psi_dev, ls_obs* out_host, void* stream);
 /* Wait budget of one dependency wait (seconds, default 1) and a test hook that

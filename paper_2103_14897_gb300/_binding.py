@@ -85,7 +85,7 @@ def load_library(path: str = LIB_PATH):
     lib.ls_batch_destroy.argtypes = [vp]
     lib.ls_batch_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     lib.ls_batch_init_gaussian.argtypes = [vp, vp, C.POINTER(dbl), dbl, C.POINTER(dbl), vp]
-    lib.ls_batch_step.argtypes = [vp, vp, i64, dbl, i32, vp]
+    lib.ls_batch_step.argtypes = [vp, vp, i64, dbl, i32, u64, u64, vp]
     lib.ls_batch_observables.argtypes = [vp, vp, C.POINTER(LsObs), vp]
     lib.ls_batch_debug.argtypes = [vp, i32, dbl]
     for name in EXPORTS[1:]:
@@ -313,9 +313,9 @@ class Batch:
                                            float(w), k0.ctypes.data_as(C.POINTER(C.c_double)),
                                            _stream_handle(stream)))
 
-    def step(self, psi, nsteps, tau, scheme="strang", stream=None):
+    def step(self, psi, nsteps, tau, scheme="strang", seed=0, step0=0, stream=None):
         _check(_lib.ls_batch_step(self._h, _ptr(psi), int(nsteps), float(tau), SCHEMES[scheme],
-                                  _stream_handle(stream)))
+                                  int(seed) & (2 ** 64 - 1), int(step0), _stream_handle(stream)))
 
     def observables(self, psi, stream=None):
         out = (LsObs * len(self.probs))()

@@ -1049,7 +1049,8 @@ struct ls_batch {
   int nthreads = 256;
   int W[2][1] = {{0}, {0}};
   std::vector<int> Wi[2];     // per instance and layer: slices per tile
-  DevBuf args, cum, tsteps, counters, status;
+  DevBuf args, cum, tsteps, counters, status, touch, seedbuf;
+  std::vector<int64_t> touch_off;  // per instance: rows at touch_off[i], columns after them
   double timeout_s = 1.0;
   int unmet = 0;
   size_t smem = 0;
@@ -1061,7 +1062,7 @@ struct ls_batch {
     double tau;
     int64_t n;
     cudaGraphExec_t exec = nullptr;
-    std::shared_ptr<DevBuf> args;
+    std::shared_ptr<DevBuf> args, lists;
     ~Cached() {
       if (exec) cudaGraphExecDestroy(exec);
     }
@@ -1150,6 +1151,17 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     int sms = 0;
     LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     b->blocks = std::max(1, per_sm) * sms;
+    int64_t tt = 0;
+    int32_t smax = 1;
+    for (int32_t i = 0; i < count; ++i) {
+      b->touch_off.push_back(tt);
+      tt += b->inst[i]->M2 + b->inst[i]->M1;
+      smax = std::max<int32_t>(smax, (int32_t)std::max(b->inst[i]->M1, b->inst[i]->M2));
+    }
+    b->touch.alloc((size_t)tt * sizeof(int32_t));
+    b->seedbuf.alloc(2 * sizeof(uint64_t));
+    if ((size_t)smax * 5 > 48 * 1024) LS_CUDA(lsk::batch_sampler_prepare((size_t)dev_max));
+    if ((size_t)smax * 5 > (size_t)dev_max - 1024) throw CudaError{cudaErrorInvalidValue, "too many slices for the sampler"};
     b->counters.alloc((size_t)(count + 1) * sizeof(unsigned long long));
     b->status.alloc(sizeof(int32_t));
     LS_CUDA(cudaMemset(b->status.p, 0, sizeof(int32_t)));
@@ -1210,16 +1222,21 @@ int ls_batch_debug(ls_batch* b, int32_t unmet_dependency, double timeout_seconds
   return LS_OK;
 }
 
-int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, void* stream) {
+int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, uint64_t seed, uint64_t step0,
+                  void* stream) {
   if (!b) return fail(LS_ERR_STATE, "batch is NULL");
   if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
   if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
-  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP)
-    return fail(LS_ERR_INVALID, "the batched runner takes the deterministic schemes");
+  if (scheme < LS_LIE || scheme > LS_STRANG_STOCH) return fail(LS_ERR_INVALID, "unknown scheme");
   if (n == 0) return LS_OK;
-  if (n > (int64_t)1 << 30) return fail(LS_ERR_INVALID, "nsteps too large");
+  if (n > (int64_t)1 << 24) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
+  const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
+    if (stoch) {
+      const uint64_t hp[2] = {seed, step0 * (uint64_t)factors_per_step(scheme)};
+      LS_CUDA(cudaMemcpyAsync(b->seedbuf.p, hp, sizeof(hp), cudaMemcpyHostToDevice, st));
+    }
     ls_batch::Cached* ge = nullptr;
     for (auto& e : b->graphs)
       if (e->psi == psi && e->scheme == scheme && e->tau == tau && e->n == n) ge = e.get();
@@ -1237,13 +1254,40 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       batch_units(scheme, ba.units, npass, u, tau);
       ba.npass = npass;
       ba.ninst = ninst;
-      ba.nsteps = (int32_t)std::min<int64_t>(n, INT32_MAX);
+      ba.nsteps = (int32_t)n;
+      ba.stoch = stoch ? 1 : 0;
       std::vector<PassSpec> ps;
       int32_t et = 0;
       build_passes(scheme, tau, 1, ps, et);
-      std::vector<lsk::PassArgs> args((size_t)npass * ninst);
-      std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0);
+      ba.now_mul = et;
+      for (int q = 0; q < npass; ++q) ba.now_off[q] = ps[q].now;
+      // sampled-slice lists: [instance][step][pass][p entries]
+      std::vector<int32_t> sS((size_t)ninst * npass), sP((size_t)ninst * npass);
+      std::vector<int64_t> sBase(ninst), sStep(ninst), sOff((size_t)ninst * npass);
+      int64_t ltot = 0;
+      int32_t smax = 1;
+      for (int i = 0; i < ninst; ++i) {
+        ls_ctx* c = b->inst[i];
+        int64_t step_len = 0;
+        for (int q = 0; q < npass; ++q) {
+          const int64_t Sv = c->geom[ps[q].layer - 1].nslices;
+          const int32_t pv = std::max<int32_t>(1, (int32_t)(Sv / c->frac_den));
+          sS[(size_t)i * npass + q] = (int32_t)Sv;
+          sP[(size_t)i * npass + q] = pv;
+          sOff[(size_t)i * npass + q] = step_len;
+          step_len += pv;
+          smax = std::max<int32_t>(smax, (int32_t)Sv);
+        }
+        sBase[i] = ltot;
+        sStep[i] = step_len;
+        ltot += step_len * n;
+      }
+      e->lists = std::make_shared<DevBuf>();
+      if (stoch) e->lists->alloc((size_t)ltot * sizeof(int32_t));
+      std::vector<lsk::PassArgs> args((size_t)npass * ninst), sargs(ninst);
+      std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0), scum(ninst + 1, 0);
       const size_t es = b->dtype == LS_C64 ? 8 : 16;
+      int32_t* touch = static_cast<int32_t*>(b->touch.p);
       for (int q = 0; q < npass; ++q) {
         const int layer = ps[q].layer, L = layer - 1;
         int64_t acc = 0;
@@ -1251,11 +1295,27 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
           ls_ctx* c = b->inst[i];
           set_kinetic(c, u);
           lsk::PassArgs a = base_args(c, L, static_cast<char*>(psi) + b->off[i] * es);
-          a.mode = lsk::MODE_STEP;
           a.W = b->Wi[L][i];
-          a.T = phase_table(c, layer, ps[q].s);
+          int64_t tiles;
+          if (!stoch) {
+            a.mode = lsk::MODE_STEP;
+            a.T = phase_table(c, layer, ps[q].s);
+            tiles = (c->geom[L].nslices + a.W - 1) / a.W;
+          } else {
+            const int64_t Sv = c->geom[L].nslices;
+            const int32_t pv = sP[(size_t)i * npass + q];
+            a.mode = lsk::MODE_LAZY;
+            a.T = phase_table(c, layer, ps[q].s * (double)Sv / (double)pv);
+            a.list = static_cast<const int32_t*>(e->lists->p) + sBase[i] + sOff[(size_t)i * npass + q];
+            a.nlist = pv;
+            a.list_step = sStep[i];
+            int32_t* rows = touch + b->touch_off[i];
+            int32_t* cols = rows + c->M2;
+            a.touch_own = L == 0 ? rows : cols;
+            a.touch_other = L == 0 ? cols : rows;
+            tiles = (pv + a.W - 1) / a.W;
+          }
           args[(size_t)q * ninst + i] = a;
-          const int64_t tiles = (c->geom[L].nslices + a.W - 1) / a.W;
           cum[(size_t)q * (ninst + 1) + i] = acc;
           acc += tiles;
           tsteps[i] += tiles;
@@ -1264,18 +1324,54 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
         ba.pass_items[q] = acc;
         ba.step_items += acc;
       }
+      if (stoch) {
+        int64_t acc = 0;
+        for (int i = 0; i < ninst; ++i) {
+          ls_ctx* c = b->inst[i];
+          lsk::PassArgs a = base_args(c, 0, static_cast<char*>(psi) + b->off[i] * es);
+          a.mode = lsk::MODE_KIN;
+          a.W = b->Wi[0][i];
+          int32_t* rows = touch + b->touch_off[i];
+          a.touch_own = rows;
+          a.touch_other = rows + c->M2;
+          a.now = (int32_t)(et * n);
+          sargs[i] = a;
+          scum[i] = acc;
+          acc += (c->M2 + a.W - 1) / a.W;
+        }
+        scum[ninst] = acc;
+        ba.settle_items = acc;
+      }
       e->args = std::make_shared<DevBuf>();
-      const size_t bytes_args = args.size() * sizeof(lsk::PassArgs);
-      const size_t bytes_cum = cum.size() * sizeof(int64_t);
-      const size_t bytes_ts = tsteps.size() * sizeof(int64_t);
-      e->args->alloc(bytes_args + bytes_cum + bytes_ts);
+      const size_t b_args = args.size() * sizeof(lsk::PassArgs), b_cum = cum.size() * sizeof(int64_t);
+      const size_t b_ts = tsteps.size() * sizeof(int64_t), b_sargs = sargs.size() * sizeof(lsk::PassArgs);
+      const size_t b_scum = scum.size() * sizeof(int64_t);
+      const size_t b_si = sS.size() * sizeof(int32_t), b_sl = sBase.size() * sizeof(int64_t);
+      const size_t b_so = sOff.size() * sizeof(int64_t);
+      const size_t total_b = b_args + b_cum + b_ts + b_sargs + b_scum + 2 * b_si + 2 * b_sl + b_so;
+      e->args->alloc(total_b);
       char* base = static_cast<char*>(e->args->p);
-      LS_CUDA(cudaMemcpy(base, args.data(), bytes_args, cudaMemcpyHostToDevice));
-      LS_CUDA(cudaMemcpy(base + bytes_args, cum.data(), bytes_cum, cudaMemcpyHostToDevice));
-      LS_CUDA(cudaMemcpy(base + bytes_args + bytes_cum, tsteps.data(), bytes_ts, cudaMemcpyHostToDevice));
-      ba.args = reinterpret_cast<const lsk::PassArgs*>(base);
-      ba.cum = reinterpret_cast<const int64_t*>(base + bytes_args);
-      ba.tiles_step = reinterpret_cast<const int64_t*>(base + bytes_args + bytes_cum);
+      size_t o = 0;
+      auto put = [&](const void* src, size_t bytes) -> void* {
+        void* d = base + o;
+        LS_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+        o += bytes;
+        return d;
+      };
+      ba.args = static_cast<const lsk::PassArgs*>(put(args.data(), b_args));
+      ba.settle_args = static_cast<const lsk::PassArgs*>(put(sargs.data(), b_sargs));
+      ba.cum = static_cast<const int64_t*>(put(cum.data(), b_cum));
+      ba.tiles_step = static_cast<const int64_t*>(put(tsteps.data(), b_ts));
+      ba.settle_cum = static_cast<const int64_t*>(put(scum.data(), b_scum));
+      lsk::BatchSamplerArgs sa;
+      sa.base = static_cast<const int64_t*>(put(sBase.data(), b_sl));
+      sa.step_len = static_cast<const int64_t*>(put(sStep.data(), b_sl));
+      sa.pass_off = static_cast<const int64_t*>(put(sOff.data(), b_so));
+      sa.S = static_cast<const int32_t*>(put(sS.data(), b_si));
+      sa.p = static_cast<const int32_t*>(put(sP.data(), b_si));
+      sa.npf = npass;
+      sa.nsteps = (int32_t)n;
+      sa.Smax = smax;
       ba.counters = static_cast<unsigned long long*>(b->counters.p);
       ba.status = static_cast<int32_t*>(b->status.p);
       int clk_khz = 0;
@@ -1285,6 +1381,10 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       cudaGraph_t graph = nullptr;
       LS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
       cudaError_t ce = cudaMemsetAsync(b->counters.p, 0, (size_t)(ninst + 1) * sizeof(unsigned long long), b->cap);
+      if (ce == cudaSuccess && stoch) ce = cudaMemsetAsync(b->touch.p, 0, b->touch.bytes, b->cap);
+      if (ce == cudaSuccess && stoch)
+        ce = lsk::launch_batch_sampler(sa, static_cast<const uint64_t*>(b->seedbuf.p), (int64_t)ninst * n * npass,
+                                       static_cast<int32_t*>(e->lists->p), b->cap);
       if (ce == cudaSuccess)
         ce = b->dtype == LS_C64 ? lsk::launch_batch<float>(ba, b->nthreads, b->blocks, b->smem, b->cap)
                                 : lsk::launch_batch<double>(ba, b->nthreads, b->blocks, b->smem, b->cap);

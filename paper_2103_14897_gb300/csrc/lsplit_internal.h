@@ -68,6 +68,7 @@ struct PassArgs {
   // keeps c'_{q-1} and output 0 is fixed by fix0 * x_{q-1}, fix0 = c'_1 - c'_{q-1}.
   const void* Khat;        // N entries (complex Real); NULL: Bluestein form
   double fix0_re, fix0_im;
+  int64_t list_step;       // batched stochastic runner: list advance per step
 };
 
 struct ElemArgs {          // elementwise kernels over the whole lifted box
@@ -133,7 +134,31 @@ struct BatchArgs {
   int32_t* status;             // 0 ok, 1 a wait timed out
   long long timeout_cycles;    // clock64() budget of one wait
   int32_t unmet;               // test hook: one wait that nothing can satisfy
+  // stochastic schemes: sub-step items walk sampled-slice lists (MODE_LAZY;
+  // list of step k = args.list + k * args.list_step, kinetic clock
+  // now = k * now_mul + now_off[pass]); a settle phase (MODE_KIN) follows the
+  // last step
+  int32_t stoch;
+  int32_t now_mul, now_off[3];
+  const PassArgs* settle_args;  // [ninst]
+  const int64_t* settle_cum;    // [ninst + 1]
+  int64_t settle_items;
 };
+
+// Slice samples of a batch: block b draws instance i = b / (nsteps * npf),
+// sub-step rel = b % (nsteps * npf) with seed + i and g = g0 + rel; writes p
+// sorted indices at base[i] + (rel / npf) * step_len[i] + pass_off[i * npf + rel % npf].
+struct BatchSamplerArgs {
+  const int32_t* S;         // [ninst * npf] slice count of each pass's layer
+  const int32_t* p;         // [ninst * npf] samples per sub-step
+  const int64_t* base;      // [ninst]
+  const int64_t* step_len;  // [ninst]
+  const int64_t* pass_off;  // [ninst * npf]
+  int32_t npf, nsteps, Smax;
+};
+cudaError_t launch_batch_sampler(const BatchSamplerArgs& sa, const uint64_t* seed_g0_dev, int64_t blocks,
+                                 int32_t* out, cudaStream_t st);
+cudaError_t batch_sampler_prepare(size_t max_block);
 template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
                                                   cudaStream_t st);
 template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm);

@@ -398,7 +398,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
       la = g.X_aa * ua + g.X_ab * ub;
       lb = g.X_ba * ua + g.X_bb * ub;
       c0 = g.C_aa * (ua * ua) + g.C_ab * (ua * ub) + g.C_bb * (ub * ub);
-      if (lazy || kin_only) touch = a.touch_own[s];
+      if (lazy || kin_only) touch = CG ? __ldcg(a.touch_own + s) : a.touch_own[s];
     }
     s_la[tid] = la;
     s_lb[tid] = lb;
@@ -425,7 +425,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
       if (!measure) {
         int64_t units = a.units_pre;
         if (lazy || kin_only) {
-          const int32_t t2 = a.touch_other[i];
+          const int32_t t2 = CG ? __ldcg(a.touch_other + i) : a.touch_other[i];
           units = (int64_t)a.now - (int64_t)(s_touch[w] > t2 ? s_touch[w] : t2);
         }
         if (units != 0) {
@@ -983,41 +983,62 @@ batch_kernel(const BatchArgs b) {
   __shared__ long long s_item;
   __shared__ int s_stop, s_inst, s_pass;
   __shared__ long long s_tile;
-  const long long total = b.step_items * (long long)b.nsteps;
+  const long long steps_total = b.step_items * (long long)b.nsteps;
+  const long long total = steps_total + (b.stoch ? b.settle_items : 0);
   volatile int32_t* status = b.status;
   volatile unsigned long long* done = b.counters + 1;
+  __shared__ int s_settle;
   for (;;) {
     if (threadIdx.x == 0) {
       long long it = -1;
       s_stop = 0;
+      s_settle = 0;
       if (*status == 0) it = (long long)atomicAdd(&b.counters[0], 1ull);
       s_item = (it >= 0 && it < total) ? it : -1;
       if (s_item >= 0) {
-        const long long k = s_item / b.step_items;
-        long long r = s_item - k * b.step_items;
-        int p = 0;
-        while (p + 1 < b.npass && r >= b.pass_items[p]) {
-          r -= b.pass_items[p];
-          ++p;
+        unsigned long long need;
+        int i;
+        if (s_item >= steps_total) {
+          // settle phase: after every sub-step of instance i
+          const long long r = s_item - steps_total;
+          int lo = 0, hi = b.ninst - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.settle_cum[mid] <= r) lo = mid; else hi = mid - 1;
+          }
+          i = lo;
+          s_settle = 1;
+          s_inst = i;
+          s_pass = 0;
+          s_tile = r - b.settle_cum[i];
+          need = (unsigned long long)((long long)b.nsteps * b.tiles_step[i]);
+        } else {
+          const long long k = s_item / b.step_items;
+          long long r = s_item - k * b.step_items;
+          int p = 0;
+          while (p + 1 < b.npass && r >= b.pass_items[p]) {
+            r -= b.pass_items[p];
+            ++p;
+          }
+          // instance: largest i with cum[p][i] <= r
+          const int64_t* cum = b.cum + (size_t)p * (b.ninst + 1);
+          int lo = 0, hi = b.ninst - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cum[mid] <= r) lo = mid; else hi = mid - 1;
+          }
+          i = lo;
+          s_inst = i;
+          s_pass = p;
+          s_tile = r - cum[i];
+          // completed tiles of instance i needed before this pass may start
+          need = (unsigned long long)(k * b.tiles_step[i]);
+          for (int pp = 0; pp < p; ++pp) {
+            const int64_t* c2 = b.cum + (size_t)pp * (b.ninst + 1);
+            need += (unsigned long long)(c2[i + 1] - c2[i]);
+          }
+          if (b.unmet && i == 0 && p == 1 && k == 0) need += 1;  // test hook
         }
-        // instance: largest i with cum[p][i] <= r
-        const int64_t* cum = b.cum + (size_t)p * (b.ninst + 1);
-        int lo = 0, hi = b.ninst - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (cum[mid] <= r) lo = mid; else hi = mid - 1;
-        }
-        const int i = lo;
-        s_inst = i;
-        s_pass = p;
-        s_tile = r - cum[i];
-        // completed tiles of instance i needed before this pass may start
-        unsigned long long need = (unsigned long long)(k * b.tiles_step[i]);
-        for (int pp = 0; pp < p; ++pp) {
-          const int64_t* c2 = b.cum + (size_t)pp * (b.ninst + 1);
-          need += (unsigned long long)(c2[i + 1] - c2[i]);
-        }
-        if (b.unmet && i == 0 && p == 1 && k == 0) need += 1;  // test hook
         const long long t0 = clock64();
         unsigned int spins = 0;
         while (done[i] < need) {
@@ -1034,22 +1055,30 @@ batch_kernel(const BatchArgs b) {
     }
     __syncthreads();
     if (s_item < 0 || s_stop) return;
-    // per-item arguments: the instance's pass arguments with this step's kinetic units
+    // per-item arguments: the instance's pass arguments with this step's
+    // kinetic units (deterministic) or list and clock (stochastic)
     {
       const int i = s_inst, p = s_pass;
-      const long long k = s_item / b.step_items;
-      const int var = b.nsteps == 1 ? 3 : (k == 0 ? 0 : (k == b.nsteps - 1 ? 2 : 1));
-      const int* src = reinterpret_cast<const int*>(b.args + (size_t)p * b.ninst + i);
+      const int* src = reinterpret_cast<const int*>(s_settle ? b.settle_args + i : b.args + (size_t)p * b.ninst + i);
       int* dst = reinterpret_cast<int*>(&s_args);
       for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / 4); w += blockDim.x) dst[w] = src[w];
       __syncthreads();
-      if (threadIdx.x == 0) {
-        s_args.units_pre = b.units[var][p][0];
-        s_args.units_post = b.units[var][p][1];
+      if (threadIdx.x == 0 && !s_settle) {
+        const long long k = s_item / b.step_items;
+        if (b.stoch) {
+          s_args.list += k * s_args.list_step;
+          s_args.now = (int32_t)(k * b.now_mul + b.now_off[p]);
+        } else {
+          const int var = b.nsteps == 1 ? 3 : (k == 0 ? 0 : (k == b.nsteps - 1 ? 2 : 1));
+          s_args.units_pre = b.units[var][p][0];
+          s_args.units_post = b.units[var][p][1];
+        }
       }
       __syncthreads();
     }
-    pass_tile<Real, BPT, MODE_STEP, true>(s_args, s_tile, smraw);
+    if (s_settle) pass_tile<Real, BPT, MODE_KIN, true>(s_args, s_tile, smraw);
+    else if (b.stoch) pass_tile<Real, BPT, MODE_LAZY, true>(s_args, s_tile, smraw);
+    else pass_tile<Real, BPT, MODE_STEP, true>(s_args, s_tile, smraw);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd((unsigned long long*)&done[s_inst], 1ull);
@@ -1292,6 +1321,43 @@ __global__ void sampler_kernel(SamplerArgs sa, const uint64_t* seed_g0, int32_t*
   }
 }
 
+__global__ void batch_sampler_kernel(BatchSamplerArgs sa, const uint64_t* seed_g0, int32_t* out) {
+  extern __shared__ int32_t perm[];  // Smax ints, then Smax flag bytes
+  const int64_t per = (int64_t)sa.nsteps * sa.npf;
+  const int64_t i = blockIdx.x / per;
+  const int64_t rel = blockIdx.x - i * per;
+  const int pass = (int)(rel % sa.npf);
+  const int S = sa.S[i * sa.npf + pass];
+  const int p = sa.p[i * sa.npf + pass];
+  unsigned char* flag = reinterpret_cast<unsigned char*>(perm + sa.Smax);
+  const uint64_t seed = seed_g0[0] + (uint64_t)i;
+  const uint64_t g = seed_g0[1] + (uint64_t)rel;
+  for (int q = threadIdx.x; q < S; q += blockDim.x) {
+    perm[q] = q;
+    flag[q] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t state = seed ^ (g * 0xD1B54A32D192ED03ull);
+    for (int q = 0; q < p; ++q) {
+      const uint64_t r = splitmix64_next(state);
+      const int j = q + (int)(r % (uint64_t)(S - q));
+      const int t = perm[q];
+      perm[q] = perm[j];
+      perm[j] = t;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < p; q += blockDim.x) flag[perm[q]] = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t* o = out + sa.base[i] + (rel / sa.npf) * sa.step_len[i] + sa.pass_off[i * sa.npf + pass];
+    int c = 0;
+    for (int q = 0; q < S; ++q)
+      if (flag[q]) o[c++] = q;
+  }
+}
+
 __global__ void zero_i32_kernel(int32_t* p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0;
 }
@@ -1335,6 +1401,14 @@ cudaError_t launch_sampler(const SamplerArgs& sa, const uint64_t* seed_g0_dev, i
   return cudaGetLastError();
 }
 cudaError_t sampler_prepare(size_t smem) { return allow_smem(sampler_kernel, smem); }
+cudaError_t launch_batch_sampler(const BatchSamplerArgs& sa, const uint64_t* seed_g0_dev, int64_t blocks,
+                                 int32_t* out, cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  const size_t smem = (size_t)sa.Smax * 5;
+  batch_sampler_kernel<<<(unsigned)blocks, 256, smem, st>>>(sa, seed_g0_dev, out);
+  return cudaGetLastError();
+}
+cudaError_t batch_sampler_prepare(size_t max_block) { return allow_smem(batch_sampler_kernel, max_block); }
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   zero_i32_kernel<<<256, 256, 0, st>>>(p, n);

@@ -51,6 +51,27 @@ def test_batched_runner_parity(P, dtype, tol, scheme):
         assert rel(b.get_dense(psi, i), ref) < tol * 4
 
 
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
+@pytest.mark.parametrize("scheme", ["strang_stoch", "lie_stoch"])
+def test_batched_runner_stochastic_parity(P, dtype, tol, scheme):
+    """Stochastic schemes inside the persistent launch: instance i samples with
+    seed + i; lists drawn on the device; lazy kinetic phases and a settle phase."""
+    probs = uneven_batch()
+    b = P.Batch(probs, dtype)
+    psi = b.empty()
+    xs = [W.random_state((p.M2, p.M1), 60 + i) for i, p in enumerate(probs)]
+    for i, x in enumerate(xs):
+        b.set_dense(psi, i, x)
+    b.step(psi, 3, 1e-2, scheme, seed=9, step0=4)
+    refs = [O.step(p, xs[i], 1e-2, scheme, 3, seed=9 + i, step0=4) for i, p in enumerate(probs)]
+    for i, p in enumerate(probs):
+        assert rel(b.get_dense(psi, i), refs[i]) < tol * 3, (i, p.name, rel(b.get_dense(psi, i), refs[i]))
+    b.step(psi, 2, 1e-2, scheme, seed=9, step0=7)
+    for i, p in enumerate(probs):
+        ref = O.step(p, refs[i], 1e-2, scheme, 2, seed=9 + i, step0=7)
+        assert rel(b.get_dense(psi, i), ref) < tol * 5
+
+
 def test_batched_matches_single_contexts(P):
     """The same instances stepped one context at a time agree with the batch."""
     probs = W.batch_1d(count=5, seed=11, nmin=8, nmax=300)
