@@ -164,6 +164,7 @@ struct ls_ctx {
   lsk::LayerGeom geom[2]{};
   int W[2] = {1, 1}, bpt[2] = {2, 2}, nt[2] = {64, 64};
   int fastW[2] = {0, 0};  // slices per CTA of the fast 1D pass (0: not applicable)
+  int fast_variant = 0;   // shared-buffer / register-budget variant of the fast pass
   DevBuf tw[2], twb[2], bm[2], bp[2], chirp[2], vgrid[2];
   std::vector<double> vhost[2];
   std::map<std::pair<int, uint64_t>, std::shared_ptr<DevBuf>> ttab;  // (layer, bits(s)) -> table
@@ -470,6 +471,7 @@ cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a0, int L, int64_t nitems, cu
   if (c->fastW[L] > 0 && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
     lsk::PassArgs a = a0;
     a.W = c->fastW[L];
+    a.variant = (c->dtype == LS_C64 && a.W * (c->geom[L].np / 16) <= 256) ? c->fast_variant : 0;
     a.strided = (L == 1) ? 1 : 0;
     const int64_t ntiles = (nitems + a.W - 1) / a.W;
     if (c->dtype == LS_C64) return lsk::launch_fast<float>(a, ntiles, st);
@@ -756,7 +758,13 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
       const int cap = ev ? std::max(tps, std::min(std::atoi(ev), lsk::fast_max_threads<float>())) : maxnt;
       const int ntcap = c->dtype == LS_C64 ? cap : std::min(cap, 256);
       int W = std::min<int64_t>(std::min(lsk::kMaxTileSlices, std::max(1, ntcap / tps)), g.nslices);
-      while (W > 0 && (c->dtype == LS_C64 ? lsk::fast_smem_bytes<float>(g, W) : lsk::fast_smem_bytes<double>(g, W)) >
+      {
+        // one shared buffer and three resident CTAs per SM measured 13% faster
+        // than two buffers at two CTAs per SM (2049^2, Strang); FP64 keeps two
+        const char* fv = std::getenv("LSPLIT_FAST_VARIANT");
+        c->fast_variant = fv ? std::max(0, std::min(1, std::atoi(fv))) : (c->dtype == LS_C64 ? 1 : 0);
+      }
+      while (W > 0 && (c->dtype == LS_C64 ? lsk::fast_smem_bytes<float>(g, W, 0) : lsk::fast_smem_bytes<double>(g, W, 0)) >
                           (size_t)dev_max)
         --W;
       c->fastW[L] = W;

@@ -69,6 +69,7 @@ struct PassArgs {
   const void* Khat;        // N entries (complex Real); NULL: Bluestein form
   double fix0_re, fix0_im;
   int64_t list_step;       // batched stochastic runner: list advance per step
+  int32_t variant;         // fast pass: 0 two shared buffers (2 CTAs/SM), 1 one buffer (3 CTAs/SM)
 };
 
 struct ElemArgs {          // elementwise kernels over the whole lifted box
@@ -112,7 +113,7 @@ template <typename Real> int pass_max_threads(int bpt);
 // Fast 1D pass (MODE_STEP / MODE_LAZY, power-of-two transform length 256..8192):
 // W slices per CTA, W * np / 16 threads.
 template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntiles, cudaStream_t st);
-template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W);
+template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W, int variant);
 template <typename Real> cudaError_t fast_prepare(size_t max_smem);
 template <typename Real> int fast_max_threads();
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);

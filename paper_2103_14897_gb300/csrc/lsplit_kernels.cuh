@@ -668,7 +668,7 @@ __device__ __forceinline__ void twiddle_pow(typename CT<Real>::C* v, typename CT
   }
 }
 
-template <typename Real, int LOGN, int S, bool INV>
+template <typename Real, int LOGN, int S, bool INV, bool SINGLE = false>
 __device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typename CT<Real>::C* buf,
                                           const typename CT<Real>::C* __restrict__ tw, int j) {
   using C = typename CT<Real>::C;
@@ -697,6 +697,11 @@ __device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typenam
       const int b = j + u * TPS;
 #pragma unroll
       for (int r = 0; r < R; ++r) v[u * R + r] = buf[phys(b + r * (N / R))];
+    }
+    // one shared buffer: every read must finish before the next exchange writes
+    if constexpr (SINGLE) __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16 / R; ++u) {
       twiddle_pow<R, Real, INV>(v + u * R, wb[u]);
       dftRR<R, C, INV>(v + u * R);
     }
@@ -705,7 +710,7 @@ __device__ __forceinline__ void fast_xchg(typename CT<Real>::C (&v)[16], typenam
 
 // Full FFT of length N on the register layout x[j + r N/16]; exchanges
 // alternate between the two buffers (one barrier each).
-template <typename Real, int LOGN, bool INV>
+template <typename Real, int LOGN, bool INV, bool SINGLE = false>
 __device__ __forceinline__ void fast_fft(typename CT<Real>::C (&v)[16], typename CT<Real>::C* bufA,
                                          typename CT<Real>::C* bufB, int& flip,
                                          const typename CT<Real>::C* __restrict__ tw, int j,
@@ -729,9 +734,9 @@ __device__ __forceinline__ void fast_fft(typename CT<Real>::C (&v)[16], typename
     // radix and stride of stages S-1 and S (S is a loop index; the switch
     // below dispatches to compile-time stage bodies)
     switch (S) {
-      case 1: fast_xchg<Real, LOGN, 1, INV>(v, buf, tw, j); break;
-      case 2: fast_xchg<Real, LOGN, 2, INV>(v, buf, tw, j); break;
-      case 3: fast_xchg<Real, LOGN, 3, INV>(v, buf, tw, j); break;
+      case 1: fast_xchg<Real, LOGN, 1, INV, SINGLE>(v, buf, tw, j); break;
+      case 2: fast_xchg<Real, LOGN, 2, INV, SINGLE>(v, buf, tw, j); break;
+      case 3: fast_xchg<Real, LOGN, 3, INV, SINGLE>(v, buf, tw, j); break;
     }
   }
   (void)TPS;
@@ -782,9 +787,11 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t max_block) 
 // Fast pass: MODE_STEP or MODE_LAZY, 1D slices, N = 2^LOGN, at most NTMAX
 // threads per CTA (256 threads: several CTAs per SM; 512: two slices per CTA
 // for wider row segments in the strided layer).
-template <typename Real, int LOGN, int MODE, int NTMAX>
-__global__ void __launch_bounds__(NTMAX, (NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1)
+template <typename Real, int LOGN, int MODE, int NTMAX, int NBUF = 2,
+          int MINB = ((NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1)>
+__global__ void __launch_bounds__(NTMAX, MINB)
 pass_fast_kernel(const PassArgs a) {
+  constexpr bool SINGLE = (NBUF == 1);
   using C = typename CT<Real>::C;
   constexpr int N = 1 << LOGN, TPS = N / 16;
   constexpr bool lazy = (MODE == MODE_LAZY);
@@ -795,8 +802,8 @@ pass_fast_kernel(const PassArgs a) {
   const int t = threadIdx.x;
   const int w = a.strided ? t % W : t / TPS;
   const int j = a.strided ? t / W : t % TPS;
-  C* bufA = reinterpret_cast<C*>(smraw) + (size_t)w * 2 * g.sb;
-  C* bufB = bufA + g.sb;
+  C* bufA = reinterpret_cast<C*>(smraw) + (size_t)w * NBUF * g.sb;
+  C* bufB = SINGLE ? bufA : bufA + g.sb;
   __shared__ int64_t s_slice[kMaxTileSlices];
   __shared__ uint64_t s_la[kMaxTileSlices], s_c0[kMaxTileSlices];
   __shared__ int32_t s_touch[kMaxTileSlices];
@@ -831,7 +838,7 @@ pass_fast_kernel(const PassArgs a) {
   // pressure), then every thread picks up its 16 elements
   const int NT = blockDim.x;
   C* smc = reinterpret_cast<C*>(smraw);
-  C* xs0 = smc + (size_t)W * 2 * g.sb;
+  C* xs0 = smc + (size_t)W * NBUF * g.sb;
 #pragma unroll 4
   for (int e = t; e < W * N; e += NT) {
     int ww, i;
@@ -855,43 +862,44 @@ pass_fast_kernel(const PassArgs a) {
     } else if (i < Q) {
       xs0[(size_t)ww * Q + i] = x;
     }
-    smc[(size_t)ww * 2 * g.sb + phys(i)] = x;
+    smc[(size_t)ww * NBUF * g.sb + phys(i)] = x;
   }
   __syncthreads();
   C v[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = bufA[phys(j + r * TPS)];
+  if constexpr (SINGLE) __syncthreads();
   int flip = 1;  // buffer A holds the input; the first exchange uses B
   const C* T = reinterpret_cast<const C*>(a.T);
   const bool conv = g.bluestein && a.Khat != nullptr;
   if (conv) {
     // cyclic convolution of the zero-padded slice with the wrapped kernel
     const C* Kh = reinterpret_cast<const C*>(a.Khat);
-    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j, Kh);
+    fast_fft<Real, LOGN, false, SINGLE>(v, bufA, bufB, flip, tw, j, Kh);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], Kh[j + r * TPS]);
-    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
   } else if (g.bluestein) {
     const C* bm = reinterpret_cast<const C*>(g.bm);
     const C* bp = reinterpret_cast<const C*>(g.bp);
-    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, false, SINGLE>(v, bufA, bufB, flip, tw, j);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], bm[j + r * TPS]);
-    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int i = j + r * TPS;
       v[r] = i < Q ? cmul(v[r], T[i]) : czero<C>();
     }
-    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, false, SINGLE>(v, bufA, bufB, flip, tw, j);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], bp[j + r * TPS]);
-    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
   } else {
-    fast_fft<Real, LOGN, true>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], T[j + r * TPS]);
-    fast_fft<Real, LOGN, false>(v, bufA, bufB, flip, tw, j);
+    fast_fft<Real, LOGN, false, SINGLE>(v, bufA, bufB, flip, tw, j);
   }
   // correction back to shared memory, then x + correction, post-phase, store
   {
@@ -906,7 +914,7 @@ pass_fast_kernel(const PassArgs a) {
       if (a.strided) { ww = e % W; i = e / W; } else { ww = e / Q; i = e - ww * Q; }
       const int64_t ss = s_slice[ww];
       if (ss < 0) continue;
-      C c = smc[(size_t)ww * 2 * g.sb + (size_t)ob * g.sb + phys(i)];
+      C c = smc[(size_t)ww * NBUF * g.sb + (size_t)(SINGLE ? 0 : ob) * g.sb + phys(i)];
       if (conv) {
         if (i == 0) {
           C f;
@@ -929,16 +937,24 @@ pass_fast_kernel(const PassArgs a) {
   if (lazy && t < W && s_slice[t] >= 0) a.touch_own[s_slice[t]] = a.now;
 }
 
-template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W) {
+template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W, int variant) {
   using C = typename CT<Real>::C;
-  return ((size_t)W * 2 * g.sb + (size_t)W * g.qa) * sizeof(C);
+  const size_t nbuf = (variant == 0) ? 2 : 1;
+  return ((size_t)W * nbuf * g.sb + (size_t)W * g.qa) * sizeof(C);
 }
 
 template <typename Real, int LOGN>
 static cudaError_t launch_fast_n(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
   const int nt = a.W * ((1 << LOGN) / 16);
-  const size_t smem = fast_smem_bytes<Real>(a.g, a.W);
+  const size_t smem = fast_smem_bytes<Real>(a.g, a.W, a.variant);
   if (nt <= 256) {
+    if constexpr (sizeof(Real) == 4) {
+      if (a.variant == 1) {
+        if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256, 1, 3><<<(unsigned)ntiles, nt, smem, st>>>(a);
+        else pass_fast_kernel<Real, LOGN, MODE_STEP, 256, 1, 3><<<(unsigned)ntiles, nt, smem, st>>>(a);
+        return cudaGetLastError();
+      }
+    }
     if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256><<<(unsigned)ntiles, nt, smem, st>>>(a);
     else pass_fast_kernel<Real, LOGN, MODE_STEP, 256><<<(unsigned)ntiles, nt, smem, st>>>(a);
   } else if constexpr (sizeof(Real) == 4) {
@@ -964,11 +980,16 @@ template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntil
 
 template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
   cudaError_t e = cudaSuccess;
-#define LS_FPREP(L, NTM) \
-  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, NTM>, max_smem); \
-  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, NTM>, max_smem);
-  LS_FPREP(9, 256) LS_FPREP(10, 256) LS_FPREP(11, 256) LS_FPREP(12, 256)
-  if constexpr (sizeof(Real) == 4) { LS_FPREP(9, 512) LS_FPREP(10, 512) LS_FPREP(11, 512) LS_FPREP(12, 512) }
+#define LS_FPREP(L, NTM, NB, MB) \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, NTM, NB, MB>, max_smem); \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, NTM, NB, MB>, max_smem);
+  if constexpr (sizeof(Real) == 4) {
+    LS_FPREP(9, 256, 2, 2) LS_FPREP(10, 256, 2, 2) LS_FPREP(11, 256, 2, 2) LS_FPREP(12, 256, 2, 2)
+    LS_FPREP(9, 256, 1, 3) LS_FPREP(10, 256, 1, 3) LS_FPREP(11, 256, 1, 3) LS_FPREP(12, 256, 1, 3)
+    LS_FPREP(9, 512, 2, 1) LS_FPREP(10, 512, 2, 1) LS_FPREP(11, 512, 2, 1) LS_FPREP(12, 512, 2, 1)
+  } else {
+    LS_FPREP(9, 256, 2, 1) LS_FPREP(10, 256, 2, 1) LS_FPREP(11, 256, 2, 1) LS_FPREP(12, 256, 2, 1)
+  }
 #undef LS_FPREP
   return e;
 }
@@ -1432,7 +1453,7 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
   template cudaError_t launch_elem_obs<R>(const ElemArgs&, const void*, const void*, double*, int,      \
                                           cudaStream_t);                                                 \
   template cudaError_t launch_fast<R>(const PassArgs&, int64_t, cudaStream_t);                           \
-  template size_t fast_smem_bytes<R>(const LayerGeom&, int);                                             \
+  template size_t fast_smem_bytes<R>(const LayerGeom&, int, int);                                        \
   template cudaError_t fast_prepare<R>(size_t);                                                          \
   template int fast_max_threads<R>();                                                                    \
   template cudaError_t launch_batch<R>(const BatchArgs&, int, int, size_t, cudaStream_t);               \
