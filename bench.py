@@ -174,20 +174,38 @@ def run_reference(args):
 
 
 def profile_case(args):
-    """Smaller-than-bench ncu target whose array exceeds L2: a 2049 x 8192 lifted
-    box (134 MB complex64; layer-1 slices of length 2049 use the same
-    convolution-form pass as the bench workload).  Runs --steps Strang steps."""
+    """ncu targets whose arrays exceed L2 (few GB at most), --steps steps each:
+    1d    : 2049 x 8192 lifted box (134 MB complex64); layer-1 slices of length
+            2049 use the same convolution-form pass as the bench workload;
+    2d    : the 64^4 twisted bilayer (134 MB), general pass with 64 x 64 slices;
+    batch : 64 uneven instances of the batched workload, one persistent launch."""
     import torch
     import __graft_entry__ as G
     G.build()
     import paper_2103_14897_gb300 as P
-    p = W.Problem(1, np.array([[2 * math.pi]]), np.array([[2 * math.pi / W.GOLDEN]]), (-1024,), (2049,),
-                  (-4096,), (8192,), 1e12, np.array([[1], [-1]]), np.array([0.6, 0.6], dtype=complex),
-                  np.array([[1], [-1]]), np.array([0.45, 0.45], dtype=complex), "bilayer1d-2049x8192")
+    kind = args.profile_case
+    if kind == "batch":
+        probs = W.batch_1d(count=64, seed=4)
+        b = P.Batch(probs, "c64")
+        psi = b.empty()
+        b.init_gaussian(psi, [0.0], 2.0, [1.0])
+        b.step(psi, args.steps, 1e-3, args.scheme)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "batch1d-64", "steps": args.steps,
+                          "norm": b.observables(psi)[0]["norm"]}))
+        return
+    if kind == "2d":
+        p = W.twisted_2d(q=64)
+        x0, k0, tau = [0.0, 0.0], [1.0, 0.0], 1e-3
+    else:
+        p = W.Problem(1, np.array([[2 * math.pi]]), np.array([[2 * math.pi / W.GOLDEN]]), (-1024,), (2049,),
+                      (-4096,), (8192,), 1e12, np.array([[1], [-1]]), np.array([0.6, 0.6], dtype=complex),
+                      np.array([[1], [-1]]), np.array([0.45, 0.45], dtype=complex), "bilayer1d-2049x8192")
+        x0, k0, tau = [0.0], [1.0], TAU
     ctx = P.Context(p, "c64")
     psi = ctx.empty()
-    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
-    ctx.step(psi, args.steps, TAU, args.scheme)
+    ctx.init_gaussian(psi, x0, 2.0, k0)
+    ctx.step(psi, args.steps, tau, args.scheme)
     torch.cuda.synchronize()
     print(json.dumps({"workload": p.name, "steps": args.steps, "norm": ctx.observables(psi)["norm"]}))
 
@@ -449,15 +467,15 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scheme", default="strang")
     ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--suite", action="store_true", help="throughput lines of the secondary workloads")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run the 2049x8192 ncu target instead of the bench workload")
+    ap.add_argument("--profile-case", choices=["1d", "2d", "batch"], default=None,
+                    help="run an ncu target (array larger than L2) instead of the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
