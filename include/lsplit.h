@@ -181,7 +181,8 @@ int ls_adjoint(ls_ctx* ctx, void* psi_dev, void* lam_dev, int64_t nsteps, double
  * being the total element count) with row pitch pitches[i]. */
 typedef struct ls_batch ls_batch;
 
-/* Create count instances (an ls_create per problem, same dtype required). */
+/* Create count instances (an ls_create per problem; 1D problems with the same
+ * dtype). */
 int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out);
 int ls_batch_destroy(ls_batch* batch);
 /* offsets: count+1 int64 (host), pitches: count int64 (host); either may be NULL. */

@@ -471,7 +471,7 @@ cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a0, int L, int64_t nitems, cu
   if (c->fastW[L] > 0 && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
     lsk::PassArgs a = a0;
     a.W = c->fastW[L];
-    a.variant = (c->dtype == LS_C64 && a.W * (c->geom[L].np / 16) <= 256) ? c->fast_variant : 0;
+    a.variant = c->fast_variant;
     a.strided = (L == 1) ? 1 : 0;
     const int64_t ntiles = (nitems + a.W - 1) / a.W;
     if (c->dtype == LS_C64) return lsk::launch_fast<float>(a, ntiles, st);
@@ -761,10 +761,9 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
       {
         // one shared buffer and three resident CTAs per SM measured 13% faster
         // than two buffers at two CTAs per SM (2049^2, Strang); FP64 keeps two
-        const char* fv = std::getenv("LSPLIT_FAST_VARIANT");
-        c->fast_variant = fv ? std::max(0, std::min(1, std::atoi(fv))) : (c->dtype == LS_C64 ? 1 : 0);
+        c->fast_variant = c->dtype == LS_C64 ? 1 : 0;
       }
-      while (W > 0 && (c->dtype == LS_C64 ? lsk::fast_smem_bytes<float>(g, W, 0) : lsk::fast_smem_bytes<double>(g, W, 0)) >
+      while (W > 0 && (c->dtype == LS_C64 ? lsk::fast_smem_bytes<float>(g, W, 1) : lsk::fast_smem_bytes<double>(g, W, 0)) >
                           (size_t)dev_max)
         --W;
       c->fastW[L] = W;
@@ -1117,6 +1116,7 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     int v = validate(&probs[i]);
     if (v != LS_OK) return v;
     if (probs[i].dtype != probs[0].dtype) return fail(LS_ERR_INVALID, "all instances need the same dtype");
+    if (probs[i].d != 1) return fail(LS_ERR_INVALID, "the batched runner takes 1D instances");
   }
   return guarded([&]() -> int {
     std::unique_ptr<ls_batch> b(new ls_batch());

@@ -305,12 +305,12 @@ __device__ __forceinline__ uint64_t quad_turns(const LayerGeom& g, int64_t mua, 
   return g.A_aa * (a * a) + g.A_ab * (a * b) + g.A_bb * (b * b) + la * a + lb * b + c0;
 }
 
-template <typename Real, bool INV, int BPT>
+template <typename Real, bool INV, int BPT, bool D1 = false>
 __device__ __forceinline__ void transform(typename CT<Real>::C* sm, const LayerGeom& g, int W,
                                           bool bluestein_half_fwd) {
   using C = typename CT<Real>::C;
   (void)bluestein_half_fwd;
-  if (g.d == 1) {
+  if (D1 || g.d == 1) {
     FftGeo f{W, g.sb, g.np, 1, 1, 0};
     fft_all<Real, INV, true, BPT>(sm, f, (const C*)g.tw);
   } else {
@@ -357,7 +357,7 @@ template <bool CG, typename C> __device__ __forceinline__ C ldpsi(const C* p) {
   else return *p;
 }
 
-template <typename Real, int BPT, int MODE, bool CG>
+template <typename Real, int BPT, int MODE, bool CG, bool D1 = false>
 __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   using C = typename CT<Real>::C;
   constexpr bool adj = (MODE == MODE_ADJOINT);
@@ -470,8 +470,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
     bluestein_conv<Real, BPT>(sm, g, W, (const C*)g.bm);
     if (adj) bluestein_conv<Real, BPT>(sml, g, W, (const C*)g.bm);
   } else {
-    transform<Real, true, BPT>(sm, g, W, false);
-    if (adj) transform<Real, true, BPT>(sml, g, W, false);
+    transform<Real, true, BPT, D1>(sm, g, W, false);
+    if (adj) transform<Real, true, BPT, D1>(sml, g, W, false);
   }
 
   // ---- pointwise: (T - 1)/M, or the measurement / gradient
@@ -522,8 +522,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
       bluestein_conv<Real, BPT>(sm, g, W, (const C*)g.bp);
       if (adj) bluestein_conv<Real, BPT>(sml, g, W, (const C*)g.bp);
     } else {
-      transform<Real, false, BPT>(sm, g, W, false);
-      if (adj) transform<Real, false, BPT>(sml, g, W, false);
+      transform<Real, false, BPT, D1>(sm, g, W, false);
+      if (adj) transform<Real, false, BPT, D1>(sml, g, W, false);
     }
 
     // ---- x + correction, kinetic post-phase, store
@@ -946,24 +946,14 @@ template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W, int v
 template <typename Real, int LOGN>
 static cudaError_t launch_fast_n(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
   const int nt = a.W * ((1 << LOGN) / 16);
-  const size_t smem = fast_smem_bytes<Real>(a.g, a.W, a.variant);
-  if (nt <= 256) {
-    if constexpr (sizeof(Real) == 4) {
-      if (a.variant == 1) {
-        if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256, 1, 3><<<(unsigned)ntiles, nt, smem, st>>>(a);
-        else pass_fast_kernel<Real, LOGN, MODE_STEP, 256, 1, 3><<<(unsigned)ntiles, nt, smem, st>>>(a);
-        return cudaGetLastError();
-      }
-    }
-    if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256><<<(unsigned)ntiles, nt, smem, st>>>(a);
-    else pass_fast_kernel<Real, LOGN, MODE_STEP, 256><<<(unsigned)ntiles, nt, smem, st>>>(a);
-  } else if constexpr (sizeof(Real) == 4) {
-    if (nt > 512) return cudaErrorInvalidValue;
-    if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 512><<<(unsigned)ntiles, nt, smem, st>>>(a);
-    else pass_fast_kernel<Real, LOGN, MODE_STEP, 512><<<(unsigned)ntiles, nt, smem, st>>>(a);
-  } else {
-    return cudaErrorInvalidValue;
-  }
+  if (nt > 256) return cudaErrorInvalidValue;
+  // single precision: one shared buffer, three resident CTAs per SM; double:
+  // two buffers (ping-pong), registers for one CTA
+  constexpr int NBUF = sizeof(Real) == 4 ? 1 : 2;
+  constexpr int MINB = sizeof(Real) == 4 ? 3 : 1;
+  const size_t smem = fast_smem_bytes<Real>(a.g, a.W, NBUF == 1 ? 1 : 0);
+  if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256, NBUF, MINB><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  else pass_fast_kernel<Real, LOGN, MODE_STEP, 256, NBUF, MINB><<<(unsigned)ntiles, nt, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -980,24 +970,22 @@ template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntil
 
 template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
   cudaError_t e = cudaSuccess;
-#define LS_FPREP(L, NTM, NB, MB) \
-  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, NTM, NB, MB>, max_smem); \
-  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, NTM, NB, MB>, max_smem);
-  if constexpr (sizeof(Real) == 4) {
-    LS_FPREP(9, 256, 2, 2) LS_FPREP(10, 256, 2, 2) LS_FPREP(11, 256, 2, 2) LS_FPREP(12, 256, 2, 2)
-    LS_FPREP(9, 256, 1, 3) LS_FPREP(10, 256, 1, 3) LS_FPREP(11, 256, 1, 3) LS_FPREP(12, 256, 1, 3)
-    LS_FPREP(9, 512, 2, 1) LS_FPREP(10, 512, 2, 1) LS_FPREP(11, 512, 2, 1) LS_FPREP(12, 512, 2, 1)
-  } else {
-    LS_FPREP(9, 256, 2, 1) LS_FPREP(10, 256, 2, 1) LS_FPREP(11, 256, 2, 1) LS_FPREP(12, 256, 2, 1)
-  }
+  constexpr int NBUF = sizeof(Real) == 4 ? 1 : 2;
+  constexpr int MINB = sizeof(Real) == 4 ? 3 : 1;
+#define LS_FPREP(L) \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, 256, NBUF, MINB>, max_smem); \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, 256, NBUF, MINB>, max_smem);
+  LS_FPREP(9) LS_FPREP(10) LS_FPREP(11) LS_FPREP(12)
 #undef LS_FPREP
   return e;
 }
-template <typename Real> int fast_max_threads() { return sizeof(Real) == 4 ? 512 : 256; }
+template <typename Real> int fast_max_threads() { return 256; }
 
 // ---------------------------------------------------------------- batched runner
-template <typename Real, int BPT>
-__global__ void __launch_bounds__(PassTraits<Real, BPT>::kMaxNT)
+// 256-thread CTAs (the block size the host uses for every tile shape); 1D
+// slices only; STOCH selects the stochastic (lazy + settle) or deterministic body.
+template <typename Real, int BPT, bool STOCH>
+__global__ void __launch_bounds__(256, 2)
 batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ PassArgs s_args;
@@ -1097,9 +1085,12 @@ batch_kernel(const BatchArgs b) {
       }
       __syncthreads();
     }
-    if (s_settle) pass_tile<Real, BPT, MODE_KIN, true>(s_args, s_tile, smraw);
-    else if (b.stoch) pass_tile<Real, BPT, MODE_LAZY, true>(s_args, s_tile, smraw);
-    else pass_tile<Real, BPT, MODE_STEP, true>(s_args, s_tile, smraw);
+    if constexpr (STOCH) {
+      if (s_settle) pass_tile<Real, BPT, MODE_KIN, true, true>(s_args, s_tile, smraw);
+      else pass_tile<Real, BPT, MODE_LAZY, true, true>(s_args, s_tile, smraw);
+    } else {
+      pass_tile<Real, BPT, MODE_STEP, true, true>(s_args, s_tile, smraw);
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) atomicAdd((unsigned long long*)&done[s_inst], 1ull);
@@ -1108,14 +1099,20 @@ batch_kernel(const BatchArgs b) {
 
 template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
                                                   cudaStream_t st) {
-  batch_kernel<Real, 2><<<nblocks, nthreads, smem, st>>>(b);
+  if (b.stoch) batch_kernel<Real, 2, true><<<nblocks, nthreads, smem, st>>>(b);
+  else batch_kernel<Real, 2, false><<<nblocks, nthreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 
 template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm) {
-  cudaError_t e = allow_smem(batch_kernel<Real, 2>, max_smem);
+  cudaError_t e = allow_smem(batch_kernel<Real, 2, false>, max_smem);
+  if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true>, max_smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel<Real, 2>, nthreads, smem);
+  int a = 0, c = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false>, nthreads, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true>, nthreads, smem);
+  *blocks_per_sm = a < c ? a : c;
+  return e;
 }
 
 #define LS_FOR_MODES(X, R, B) \
@@ -1455,11 +1452,15 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
   template cudaError_t launch_fast<R>(const PassArgs&, int64_t, cudaStream_t);                           \
   template size_t fast_smem_bytes<R>(const LayerGeom&, int, int);                                        \
   template cudaError_t fast_prepare<R>(size_t);                                                          \
-  template int fast_max_threads<R>();                                                                    \
-  template cudaError_t launch_batch<R>(const BatchArgs&, int, int, size_t, cudaStream_t);               \
-  template cudaError_t batch_prepare<R>(size_t, int, size_t, int*);
+  template int fast_max_threads<R>();
 #ifdef LS_INST_REAL
 LS_INST(LS_INST_REAL)
+#endif
+#ifdef LS_INST_BATCH
+template cudaError_t launch_batch<float>(const BatchArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t batch_prepare<float>(size_t, int, size_t, int*);
+template cudaError_t launch_batch<double>(const BatchArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t batch_prepare<double>(size_t, int, size_t, int*);
 #endif
 
 }  // namespace lsk
