@@ -337,8 +337,9 @@ def run_ours(args):
     relerr = float(np.linalg.norm(got1 - ref1) / np.linalg.norm(ref1))
     del chk
 
+    NI = args.inner
     for k in range(args.warmup):
-        ctx.step(psi, 1, TAU, scheme, seed=7, step0=k)
+        ctx.step(psi, NI, TAU, scheme, seed=7, step0=k * NI)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -349,7 +350,7 @@ def run_ours(args):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(st)
-            ctx.step(psi, 1, TAU, scheme, seed=7, step0=args.warmup + k)
+            ctx.step(psi, NI, TAU, scheme, seed=7, step0=(args.warmup + k) * NI)
             ev[k][1].record(st)
         torch.cuda.synchronize()
     if world > 1:
@@ -360,8 +361,19 @@ def run_ours(args):
         t = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_ms = float(t.item())
+    # one-time-step calls (no cross-step fusion), for reference
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t1 = 0.0
+    for k in range(20):
+        flush.fill_(float(k))
+        e0.record(st)
+        ctx.step(psi, 1, TAU, scheme, seed=7, step0=k)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t1 += e0.elapsed_time(e1)
+    single_call = p.dof * 20 / (t1 / 1e3)
     obs = ctx.observables(psi)
-    value = world * p.dof * args.steps / (t_ms / 1e3)
+    value = world * p.dof * args.steps * NI / (t_ms / 1e3)
 
     # plain FP64 GPU form (same kernels in complex128)
     ctx64 = P.Context(p, "c128")
@@ -388,15 +400,16 @@ def run_ours(args):
     nbytes = host.numel() * host.element_size()
     dev = ctx.empty()
     ne = max(3, args.steps // 2)
+    ctx.step(dev, NI, TAU, scheme, seed=7, step0=0)  # graph for this buffer
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(ne):
         dev.copy_(host, non_blocking=True)
-        ctx.step(dev, 1, TAU, scheme, seed=7, step0=k)
+        ctx.step(dev, NI, TAU, scheme, seed=7, step0=k * NI)
         host.copy_(dev, non_blocking=True)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    e2e = world * p.dof * ne / te
+    e2e = world * p.dof * NI * ne / te
 
     # roofline of the pass kernel: every launch in a step is a pass (3 for
     # Strang, 2 for Lie / kinetic-potential Strang).  The pass is FFT work on
@@ -405,17 +418,20 @@ def run_ours(args):
     # convolution form (two complex FFTs of N at 5 N log2 N each, the kernel
     # product, and the kinetic phase / correction arithmetic of q elements),
     # against the FP32 FMA peak 152 SMs x 128 lanes x 2 flop x SM clock.
-    npass = 3 if scheme in ("strang", "strang_stoch") else 2
+    # every launch is a pass kernel; a fused launch applies two layer factors.
+    # Layer factors per call: 3 n (Strang) or 2 n (Lie, kinetic/potential Strang).
+    nfac = (3 if scheme in ("strang", "strang_stoch") else 2) * NI
+    nlaunch = (2 * NI + 1) if scheme == "strang" else nfac
     hbm, src = peaks()
-    ms_launch = t_ms / args.steps / npass
+    ms_factor = t_ms / args.steps / nfac
     q = p.q1[0]
     nfft = 1 << (2 * q - 3).bit_length() if q & (q - 1) else q
     flops = p.M2 * (10 * nfft * math.log2(nfft) + 6 * nfft + 12 * q)
     clk_peak = sm_max_mhz()
     alu_peak = 152 * 128 * 2 * clk_peak * 1e6 / 1e12
-    achieved = flops / (ms_launch / 1e3) / 1e12
+    achieved = flops / (ms_factor / 1e3) / 1e12
     algo_bytes = BYTES_PER_DOF_PASS * p.dof
-    hbm_achieved = algo_bytes / (ms_launch / 1e3) / 1e9
+    hbm_achieved = algo_bytes / (ms_factor / 1e3) / 1e9
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -435,10 +451,11 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "DOF-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "ms_per_time_step": t_ms / args.steps / NI,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
             "config": {"workload": f"bilayer1d-2049x2049 {scheme} tau=5e-4", "box": [2049, 2049],
-                       "dof": p.dof, "scheme": scheme, "tau": TAU,
+                       "dof": p.dof, "scheme": scheme, "tau": TAU, "time_steps_per_bench_step": NI,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": "512 MB buffer written between timed steps"},
             "accuracy": {"rel_l2_1step_vs_oracle": relerr, "norm_minus_1": obs["norm"] - 1.0,
@@ -447,16 +464,19 @@ def run_ours(args):
                          "speedup_fp32_over_fp64": value / world / fp64_value},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
-                         "note": f"pass_fast_kernel (convolution form, N={nfft}), {flops:.3e} algorithmic "
-                                 f"flops/launch, {ms_launch * 1e3:.1f} us/launch; FP32 peak derived from "
-                                 f"152 SMs x 128 lanes x 2 x {clk_peak:.0f} MHz"},
+                         "note": f"pass_fast_kernel (convolution form, N={nfft}): {flops:.3e} algorithmic "
+                                 f"flops per layer factor, {ms_factor * 1e3:.1f} us per factor averaged over the "
+                                 f"{nlaunch} launches of a {NI}-step call (a fused launch applies two factors); "
+                                 f"FP32 peak derived from 152 SMs x 128 lanes x 2 x {clk_peak:.0f} MHz"},
             "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
                              "algorithmic_bytes_per_launch": algo_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json)",
                              "note": "psi (33.8 MB) is L2-resident between passes"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "DOF-steps/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
-            "gpu_launches": npass * args.steps,
+            "gpu_launches": nlaunch * args.steps,
+            "single_step_calls": {"value": single_call, "unit": "DOF-steps/s",
+                                  "note": "ls_step(n=1) per call: no cross-step pass fusion"},
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -467,7 +487,9 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=50,
+                    help="timed bench steps; each is one ls_step call of --inner time steps")
+    ap.add_argument("--inner", type=int, default=20, help="time steps per ls_step call")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scheme", default="strang")

@@ -126,6 +126,9 @@ struct PassSpec {
   int32_t now;    // kinetic clock at the layer factor (lazy)
   int pidx;       // index of the layer factor within its step
   int64_t step;   // step index within the call
+  double s2 = 0;      // fused pass: duration of the second factor
+  int64_t mid = 0;    // fused pass: kinetic units between the two factors
+  bool fused = false;
 };
 
 struct ConvTab {
@@ -556,6 +559,27 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     LS_CUDA(lsk::launch_zero_i32((int32_t*)c->touch_col.p, c->M1, st));
     LS_CUDA(lsk::launch_sampler(sa, (const uint64_t*)c->seedbuf.p, (int32_t)(n * npf), (int32_t*)lists->p, st));
   }
+  // Adjacent layer-1 factors of consecutive Strang steps (separated by one
+  // merged kinetic factor) run as one fused pass when the layer takes the
+  // convolution form on the fast path.
+  if (!stoch && base_scheme(scheme) == LS_STRANG && c->conv_form[0] && c->fastW[0] > 0 &&
+      !getenv_flag("LSPLIT_NO_FUSE")) {
+    std::vector<PassSpec> merged;
+    for (size_t i = 0; i < ps.size(); ++i) {
+      if (ps[i].layer == 1 && i + 1 < ps.size() && ps[i + 1].layer == 1) {
+        PassSpec f = ps[i];
+        f.s2 = ps[i + 1].s;
+        f.mid = ps[i].post + ps[i + 1].pre;
+        f.post = ps[i + 1].post;
+        f.fused = true;
+        merged.push_back(f);
+        ++i;
+      } else {
+        merged.push_back(ps[i]);
+      }
+    }
+    ps.swap(merged);
+  }
   for (size_t i = 0; i < ps.size(); ++i) {
     const PassSpec& q = ps[i];
     const int L = q.layer - 1;
@@ -570,6 +594,13 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
         a.Khat = ct.khat->p;
         a.fix0_re = ct.fix_re;
         a.fix0_im = ct.fix_im;
+        if (q.fused) {
+          const ConvTab& c2 = conv_table(c, q.layer, q.s2);
+          a.Khat2 = c2.khat->p;
+          a.fix2_re = c2.fix_re;
+          a.fix2_im = c2.fix_im;
+          a.units_mid = q.mid;
+        }
       }
       a.units_pre = q.pre;
       a.units_post = q.post;
@@ -1054,6 +1085,7 @@ struct ls_batch {
   std::vector<int64_t> off;   // element offset of each instance's array
   int dtype = LS_C64;
   int nthreads = 256;
+  int minb = 4;
   int W[2][1] = {{0}, {0}};
   std::vector<int> Wi[2];     // per instance and layer: slices per tile
   DevBuf args, cum, tsteps, counters, status, touch, seedbuf;
@@ -1154,8 +1186,12 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     if (smem + 4096 > (size_t)dev_max) throw CudaError{cudaErrorInvalidValue, "batched tile exceeds shared memory"};
     b->smem = smem;
     int per_sm = 0;
-    if (b->dtype == LS_C64) LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, &per_sm));
-    else LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, &per_sm));
+    {
+      const char* mb = std::getenv("LSPLIT_BATCH_MINB");
+      b->minb = (mb && std::atoi(mb) == 2) ? 2 : 4;
+    }
+    if (b->dtype == LS_C64) LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, b->minb, &per_sm));
+    else LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, b->minb, &per_sm));
     int sms = 0;
     LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     b->blocks = std::max(1, per_sm) * sms;
@@ -1386,6 +1422,7 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       LS_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device));
       ba.timeout_cycles = (long long)(b->timeout_s * (double)std::max(clk_khz, 1000000) * 1e3);
       ba.unmet = b->unmet;
+      ba.minb = b->minb;
       cudaGraph_t graph = nullptr;
       LS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
       cudaError_t ce = cudaMemsetAsync(b->counters.p, 0, (size_t)(ninst + 1) * sizeof(unsigned long long), b->cap);

@@ -69,6 +69,11 @@ struct PassArgs {
   const void* Khat;        // N entries (complex Real); NULL: Bluestein form
   double fix0_re, fix0_im;
   int64_t list_step;       // batched stochastic runner: list advance per step
+  // fused pass (fast path, convolution form): a second factor of the same layer
+  // after the kinetic phase units_mid; NULL Khat2 = single factor
+  const void* Khat2;
+  double fix2_re, fix2_im;
+  int64_t units_mid;
   int32_t variant;         // fast pass: 0 two shared buffers (2 CTAs/SM), 1 one buffer (3 CTAs/SM)
 };
 
@@ -144,6 +149,7 @@ struct BatchArgs {
   const PassArgs* settle_args;  // [ninst]
   const int64_t* settle_cum;    // [ninst + 1]
   int64_t settle_items;
+  int32_t minb;                 // register budget variant (2 or 4 CTAs per SM)
 };
 
 // Slice samples of a batch: block b draws instance i = b / (nsteps * npf),
@@ -162,7 +168,8 @@ cudaError_t launch_batch_sampler(const BatchSamplerArgs& sa, const uint64_t* see
 cudaError_t batch_sampler_prepare(size_t max_block);
 template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
                                                   cudaStream_t st);
-template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm);
+template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int minb,
+                                                   int* blocks_per_sm);
 
 // Message returned by ls_last_error() on the calling thread.
 void set_last_error(const std::string& msg);

@@ -278,8 +278,15 @@ __host__ __device__ __forceinline__ int stage_bits(int rem) {
   return 3;
 }
 
+// The batched runner inlines the transform into its persistent loop (a call
+// would keep per-thread register arrays in local memory across the call).
+#ifdef LS_INST_BATCH
+#define LS_FFT_INLINE __forceinline__
+#else
+#define LS_FFT_INLINE
+#endif
 template <typename Real, bool INV, bool JFAST, int BPT>
-__device__ void fft_all(typename CT<Real>::C* sm, const FftGeo& f, const typename CT<Real>::C* tw) {
+__device__ LS_FFT_INLINE void fft_all(typename CT<Real>::C* sm, const FftGeo& f, const typename CT<Real>::C* tw) {
   int rem = 31 - __clz(f.n);
   int ns = 1;
   while (rem > 0) {
@@ -787,8 +794,11 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t max_block) 
 // Fast pass: MODE_STEP or MODE_LAZY, 1D slices, N = 2^LOGN, at most NTMAX
 // threads per CTA (256 threads: several CTAs per SM; 512: two slices per CTA
 // for wider row segments in the strided layer).
+// FUSED (convolution form only): two potential factors of the same layer
+// separated by a kinetic factor, P(s2) K(mid) P(s1), in one launch (the two
+// halves of adjacent Strang steps); the intermediate state never leaves the CTA.
 template <typename Real, int LOGN, int MODE, int NTMAX, int NBUF = 2,
-          int MINB = ((NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1)>
+          int MINB = ((NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1), bool FUSED = false>
 __global__ void __launch_bounds__(NTMAX, MINB)
 pass_fast_kernel(const PassArgs a) {
   constexpr bool SINGLE = (NBUF == 1);
@@ -879,6 +889,47 @@ pass_fast_kernel(const PassArgs a) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], Kh[j + r * TPS]);
     fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
+    if constexpr (FUSED) {
+      // x1 = K(mid) (x + c1): through shared memory, then the second factor
+      __shared__ C s_fix1[kMaxTileSlices];
+      if (t < W && s_slice[t] >= 0) {
+        C f;
+        f.x = (Real)a.fix0_re;
+        f.y = (Real)a.fix0_im;
+        s_fix1[t] = cmul(f, xs0[(size_t)t * Q + Q - 1]);
+      }
+      C* buf = (flip & 1) ? bufB : bufA;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) buf[phys(j + r * TPS)] = v[r];
+      __syncthreads();
+      for (int e = t; e < W * N; e += NT) {
+        int ww, i;
+        if (a.strided) { ww = e % W; i = e / W; } else { ww = e / N; i = e - ww * N; }
+        C* bw = smc + (size_t)ww * NBUF * g.sb + (size_t)(buf - bufA) + phys(i);
+        C x = czero<C>();
+        if (i < Q && s_slice[ww] >= 0) {
+          C c = *bw;
+          if (i == 0) c = cadd(c, s_fix1[ww]);
+          x = cadd(xs0[(size_t)ww * Q + i], c);
+          if (a.units_mid != 0) {
+            const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i);
+            const uint64_t qd = g.A_aa * (m * m) + s_la[ww] * m + s_c0[ww];
+            x = apply_phase<Real>(x, phase_of<Real>((uint64_t)0 - (uint64_t)a.units_mid * qd));
+          }
+          xs0[(size_t)ww * Q + i] = x;
+        }
+        *bw = x;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = buf[phys(j + r * TPS)];
+      __syncthreads();
+      const C* Kh2 = reinterpret_cast<const C*>(a.Khat2);
+      fast_fft<Real, LOGN, false, SINGLE>(v, bufA, bufB, flip, tw, j, Kh2);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], Kh2[j + r * TPS]);
+      fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
+    }
   } else if (g.bluestein) {
     const C* bm = reinterpret_cast<const C*>(g.bm);
     const C* bp = reinterpret_cast<const C*>(g.bp);
@@ -918,8 +969,8 @@ pass_fast_kernel(const PassArgs a) {
       if (conv) {
         if (i == 0) {
           C f;
-          f.x = (Real)a.fix0_re;
-          f.y = (Real)a.fix0_im;
+          f.x = (Real)(FUSED ? a.fix2_re : a.fix0_re);
+          f.y = (Real)(FUSED ? a.fix2_im : a.fix0_im);
           c = cadd(c, cmul(f, xs0[(size_t)ww * Q + Q - 1]));
         }
       } else if (g.bluestein) {
@@ -953,6 +1004,7 @@ static cudaError_t launch_fast_n(const PassArgs& a, int64_t ntiles, cudaStream_t
   constexpr int MINB = sizeof(Real) == 4 ? 3 : 1;
   const size_t smem = fast_smem_bytes<Real>(a.g, a.W, NBUF == 1 ? 1 : 0);
   if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256, NBUF, MINB><<<(unsigned)ntiles, nt, smem, st>>>(a);
+  else if (a.Khat2) pass_fast_kernel<Real, LOGN, MODE_STEP, 256, NBUF, MINB, true><<<(unsigned)ntiles, nt, smem, st>>>(a);
   else pass_fast_kernel<Real, LOGN, MODE_STEP, 256, NBUF, MINB><<<(unsigned)ntiles, nt, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -974,6 +1026,7 @@ template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
   constexpr int MINB = sizeof(Real) == 4 ? 3 : 1;
 #define LS_FPREP(L) \
   if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, 256, NBUF, MINB>, max_smem); \
+  if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_STEP, 256, NBUF, MINB, true>, max_smem); \
   if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, 256, NBUF, MINB>, max_smem);
   LS_FPREP(9) LS_FPREP(10) LS_FPREP(11) LS_FPREP(12)
 #undef LS_FPREP
@@ -983,9 +1036,10 @@ template <typename Real> int fast_max_threads() { return 256; }
 
 // ---------------------------------------------------------------- batched runner
 // 256-thread CTAs (the block size the host uses for every tile shape); 1D
-// slices only; STOCH selects the stochastic (lazy + settle) or deterministic body.
-template <typename Real, int BPT, bool STOCH>
-__global__ void __launch_bounds__(256, 2)
+// slices only; STOCH selects the stochastic (lazy + settle) or deterministic
+// body; MINB the resident CTAs per SM the registers are budgeted for.
+template <typename Real, int BPT, bool STOCH, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ PassArgs s_args;
@@ -997,6 +1051,26 @@ batch_kernel(const BatchArgs b) {
   volatile int32_t* status = b.status;
   volatile unsigned long long* done = b.counters + 1;
   __shared__ int s_settle;
+  // small per-pass tables copied to shared memory once: indexing the kernel
+  // parameter arrays with runtime indices would force a local-memory copy of
+  // the whole parameter block
+  __shared__ long long s_pass_items[4];
+  __shared__ int32_t s_units[4][3][2];
+  __shared__ int32_t s_now_off[3];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s_pass_items[q] = b.pass_items[q];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        s_units[v][q][0] = b.units[v][q][0];
+        s_units[v][q][1] = b.units[v][q][1];
+      }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s_now_off[q] = b.now_off[q];
+  }
+  __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) {
       long long it = -1;
@@ -1025,8 +1099,8 @@ batch_kernel(const BatchArgs b) {
           const long long k = s_item / b.step_items;
           long long r = s_item - k * b.step_items;
           int p = 0;
-          while (p + 1 < b.npass && r >= b.pass_items[p]) {
-            r -= b.pass_items[p];
+          while (p + 1 < b.npass && r >= s_pass_items[p]) {
+            r -= s_pass_items[p];
             ++p;
           }
           // instance: largest i with cum[p][i] <= r
@@ -1076,11 +1150,11 @@ batch_kernel(const BatchArgs b) {
         const long long k = s_item / b.step_items;
         if (b.stoch) {
           s_args.list += k * s_args.list_step;
-          s_args.now = (int32_t)(k * b.now_mul + b.now_off[p]);
+          s_args.now = (int32_t)(k * b.now_mul + s_now_off[p]);
         } else {
           const int var = b.nsteps == 1 ? 3 : (k == 0 ? 0 : (k == b.nsteps - 1 ? 2 : 1));
-          s_args.units_pre = b.units[var][p][0];
-          s_args.units_post = b.units[var][p][1];
+          s_args.units_pre = s_units[var][p][0];
+          s_args.units_post = s_units[var][p][1];
         }
       }
       __syncthreads();
@@ -1099,18 +1173,31 @@ batch_kernel(const BatchArgs b) {
 
 template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
                                                   cudaStream_t st) {
-  if (b.stoch) batch_kernel<Real, 2, true><<<nblocks, nthreads, smem, st>>>(b);
-  else batch_kernel<Real, 2, false><<<nblocks, nthreads, smem, st>>>(b);
+  if (b.minb == 4) {
+    if (b.stoch) batch_kernel<Real, 2, true, 4><<<nblocks, nthreads, smem, st>>>(b);
+    else batch_kernel<Real, 2, false, 4><<<nblocks, nthreads, smem, st>>>(b);
+  } else {
+    if (b.stoch) batch_kernel<Real, 2, true, 2><<<nblocks, nthreads, smem, st>>>(b);
+    else batch_kernel<Real, 2, false, 2><<<nblocks, nthreads, smem, st>>>(b);
+  }
   return cudaGetLastError();
 }
 
-template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm) {
-  cudaError_t e = allow_smem(batch_kernel<Real, 2, false>, max_smem);
-  if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true>, max_smem);
-  if (e != cudaSuccess) return e;
+template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int minb,
+                                                   int* blocks_per_sm) {
+  cudaError_t e = cudaSuccess;
   int a = 0, c = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false>, nthreads, smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true>, nthreads, smem);
+  if (minb == 4) {
+    e = allow_smem(batch_kernel<Real, 2, false, 4>, max_smem);
+    if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 4>, max_smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, 4>, nthreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, 4>, nthreads, smem);
+  } else {
+    e = allow_smem(batch_kernel<Real, 2, false, 2>, max_smem);
+    if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 2>, max_smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, 2>, nthreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, 2>, nthreads, smem);
+  }
   *blocks_per_sm = a < c ? a : c;
   return e;
 }
@@ -1458,9 +1545,9 @@ LS_INST(LS_INST_REAL)
 #endif
 #ifdef LS_INST_BATCH
 template cudaError_t launch_batch<float>(const BatchArgs&, int, int, size_t, cudaStream_t);
-template cudaError_t batch_prepare<float>(size_t, int, size_t, int*);
+template cudaError_t batch_prepare<float>(size_t, int, size_t, int, int*);
 template cudaError_t launch_batch<double>(const BatchArgs&, int, int, size_t, cudaStream_t);
-template cudaError_t batch_prepare<double>(size_t, int, size_t, int*);
+template cudaError_t batch_prepare<double>(size_t, int, size_t, int, int*);
 #endif
 
 }  // namespace lsk

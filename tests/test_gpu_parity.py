@@ -245,6 +245,24 @@ def test_fast_and_generic_paths_agree(P, monkeypatch):
         assert rel(a.to_dense(pa), b.to_dense(pb)) < 3e-6
 
 
+def test_fused_strang_passes_match_unfused(P, monkeypatch):
+    """Adjacent layer-1 factors of consecutive Strang steps fused into one pass
+    give the same state as separate passes (and the oracle)."""
+    for p in [W.config_scale_1d(), W.bilayer_1d(256, 40, 1.4, 0.6, ecut=1e9)]:
+        x = W.random_state((p.M2, p.M1), 12)
+        a = P.Context(p, "c64")
+        monkeypatch.setenv("LSPLIT_NO_FUSE", "1")
+        pb = a.from_dense(x)
+        a.step(pb, 5, 5e-4, "strang")
+        monkeypatch.delenv("LSPLIT_NO_FUSE")
+        b = P.Context(p, "c64")
+        pa = b.from_dense(x)
+        b.step(pa, 5, 5e-4, "strang")
+        assert rel(b.to_dense(pa), a.to_dense(pb)) < 3e-6
+        if p.M1 < 1000:
+            assert rel(b.to_dense(pa), O.step(p, x, 5e-4, "strang", 5)) < 3e-5
+
+
 def test_fp64_config_small_100_steps(P):
     """65 x 65 in complex128, 100 Strang steps of 1e-3 (the small FP64 workload)."""
     p = W.config_small_1d()
