@@ -177,7 +177,7 @@ def profile_case(args):
     """ncu targets whose arrays exceed L2 (few GB at most), --steps steps each:
     1d    : 2049 x 8192 lifted box (134 MB complex64); layer-1 slices of length
             2049 use the same convolution-form pass as the bench workload;
-    2d    : the 64^4 twisted bilayer (134 MB), general pass with 64 x 64 slices;
+    2d    : the 64^4 twisted bilayer (134 MB), dedicated pass for 64 x 64 slices;
     batch : 64 uneven instances of the batched workload, one persistent launch."""
     import torch
     import __graft_entry__ as G

@@ -167,6 +167,7 @@ struct ls_ctx {
   lsk::LayerGeom geom[2]{};
   int W[2] = {1, 1}, bpt[2] = {2, 2}, nt[2] = {64, 64};
   int fastW[2] = {0, 0};  // slices per CTA of the fast 1D pass (0: not applicable)
+  bool fast2d[2] = {false, false};  // 64 x 64 slices on the fast 2D pass
   int fast_variant = 0;   // shared-buffer / register-budget variant of the fast pass
   DevBuf tw[2], twb[2], bm[2], bp[2], chirp[2], vgrid[2];
   std::vector<double> vhost[2];
@@ -471,6 +472,10 @@ lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
 }
 
 cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a0, int L, int64_t nitems, cudaStream_t st) {
+  if (c->fast2d[L] && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
+    if (c->dtype == LS_C64) return lsk::launch_fast2d<float>(a0, nitems, st);
+    return lsk::launch_fast2d<double>(a0, nitems, st);
+  }
   if (c->fastW[L] > 0 && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
     lsk::PassArgs a = a0;
     a.W = c->fastW[L];
@@ -777,6 +782,13 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     else LS_CUDA(lsk::pass_prepare<double>(block_max));
     if (c->dtype == LS_C64) LS_CUDA(lsk::fast_prepare<float>(block_max));
     else LS_CUDA(lsk::fast_prepare<double>(block_max));
+    if (c->dtype == LS_C64) LS_CUDA(lsk::fast2d_prepare<float>(block_max));
+    else LS_CUDA(lsk::fast2d_prepare<double>(block_max));
+    for (int L = 0; L < 2; ++L) {
+      const lsk::LayerGeom& g = c->geom[L];
+      const size_t sm = c->dtype == LS_C64 ? lsk::fast2d_smem_bytes<float>(g) : lsk::fast2d_smem_bytes<double>(g);
+      c->fast2d[L] = g.d == 2 && g.qa == 64 && g.qb == 64 && sm <= (size_t)dev_max && !getenv_flag("LSPLIT_NO_FAST");
+    }
     for (int L = 0; L < 2; ++L) {
       const lsk::LayerGeom& g = c->geom[L];
       c->fastW[L] = 0;

@@ -121,6 +121,11 @@ template <typename Real> cudaError_t launch_fast(const PassArgs& a, int64_t ntil
 template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W, int variant);
 template <typename Real> cudaError_t fast_prepare(size_t max_smem);
 template <typename Real> int fast_max_threads();
+// Fast 2D pass for 64 x 64 slices (MODE_STEP / MODE_LAZY): one slice per
+// 256-thread CTA.
+template <typename Real> cudaError_t launch_fast2d(const PassArgs& a, int64_t ntiles, cudaStream_t st);
+template <typename Real> size_t fast2d_smem_bytes(const LayerGeom& g);
+template <typename Real> cudaError_t fast2d_prepare(size_t max_smem);
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
 cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
 

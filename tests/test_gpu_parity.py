@@ -113,6 +113,31 @@ def test_step_parity_2d(P, dtype, scheme):
         assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, p.name
 
 
+def problems_64x64_slices():
+    """Boxes whose layer-1 (or layer-2) slices are 64 x 64, the shape of the
+    dedicated 2D pass, next to a small box on the other layer so the oracle
+    stays quick; every mode kept (large cutoff) and the default cutoff."""
+    import dataclasses
+    base = W.twisted_2d(q=64, hmax=3)
+    return [
+        dataclasses.replace(base, lo2=(-4, -4), q2=(8, 8), ecut=1e9, name="64x64-slices-layer1"),
+        dataclasses.replace(base, lo1=(-4, -4), q1=(8, 8), ecut=1e9, name="64x64-slices-layer2"),
+        dataclasses.replace(base, lo2=(-3, -2), q2=(8, 4), name="64x64-slices-cutoff"),
+    ]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp", "lie_stoch", "strang_stoch"])
+def test_step_parity_64x64_slices(P, dtype, scheme):
+    for p in problems_64x64_slices():
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 5)
+        psi = ctx.from_dense(x)
+        ctx.step(psi, 3, 5e-3, scheme, seed=3, step0=2)
+        ref = O.step(p, x, 5e-3, scheme, 3, seed=3, step0=2)
+        assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, (p.name, rel(ctx.to_dense(psi), ref))
+
+
 def test_large_kinetic_phase_free_particle(P):
     """V = 0 at the 2049-box extremes: every element must be the exact phase
     exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
