@@ -1091,6 +1091,40 @@ struct QuadWalk {
   }
 };
 
+// The correction F diag((T - 1)/M) F^{-1} x of one slice held in buf (row
+// stride 65), in place: inverse transforms along a and b, the potential
+// factor, forward transforms along b and a.  Ends with a barrier.
+template <typename Real>
+__device__ __forceinline__ void f2_correction(typename CT<Real>::C* buf, const typename CT<Real>::C* __restrict__ T,
+                                              const typename CT<Real>::C* __restrict__ twa,
+                                              const typename CT<Real>::C* __restrict__ twb, int sub, int j) {
+  using C = typename CT<Real>::C;
+  C v[16];
+  // inverse transform along a (line = row ib = sub)
+  f2_line_load<Real>(v, buf, sub * kF2Row, 1, j);
+  __syncthreads();
+  fft64_line<Real, true>(v, buf, sub * kF2Row, 1, j, twa);
+  f2_line_store<Real>(v, buf, sub * kF2Row, 1, j);
+  __syncthreads();
+  // inverse along b (line = column ia = sub), potential factor, forward along b
+  f2_line_load<Real>(v, buf, sub, kF2Row, j);
+  __syncthreads();
+  fft64_line<Real, true>(v, buf, sub, kF2Row, j, twb);
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[8 * u + r] = cmul(v[8 * u + r], T[sub + 64 * (j + 4 * u + 8 * r)]);
+  fft64_line<Real, false>(v, buf, sub, kF2Row, j, twb);
+  f2_line_store<Real>(v, buf, sub, kF2Row, j);
+  __syncthreads();
+  // forward along a
+  f2_line_load<Real>(v, buf, sub * kF2Row, 1, j);
+  __syncthreads();
+  fft64_line<Real, false>(v, buf, sub * kF2Row, 1, j, twa);
+  f2_line_store<Real>(v, buf, sub * kF2Row, 1, j);
+  __syncthreads();
+}
+
 template <typename Real, int MODE>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 1)
 pass_fast2d_kernel(const PassArgs a) {
@@ -1167,33 +1201,7 @@ pass_fast2d_kernel(const PassArgs a) {
     }
   }
   __syncthreads();
-  C v[16];
-  // inverse transform along a (line = row ib = sub)
-  f2_line_load<Real>(v, buf, sub * kF2Row, 1, j);
-  __syncthreads();
-  fft64_line<Real, true>(v, buf, sub * kF2Row, 1, j, twa);
-  f2_line_store<Real>(v, buf, sub * kF2Row, 1, j);
-  __syncthreads();
-  // inverse along b (line = column ia = sub), potential factor (T - 1)/M, forward along b
-  f2_line_load<Real>(v, buf, sub, kF2Row, j);
-  __syncthreads();
-  fft64_line<Real, true>(v, buf, sub, kF2Row, j, twb);
-  {
-    const C* T = reinterpret_cast<const C*>(a.T);
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int r = 0; r < 8; ++r) v[8 * u + r] = cmul(v[8 * u + r], T[sub + 64 * (j + 4 * u + 8 * r)]);
-  }
-  fft64_line<Real, false>(v, buf, sub, kF2Row, j, twb);
-  f2_line_store<Real>(v, buf, sub, kF2Row, j);
-  __syncthreads();
-  // forward along a
-  f2_line_load<Real>(v, buf, sub * kF2Row, 1, j);
-  __syncthreads();
-  fft64_line<Real, false>(v, buf, sub * kF2Row, 1, j, twa);
-  f2_line_store<Real>(v, buf, sub * kF2Row, 1, j);
-  __syncthreads();
+  f2_correction<Real>(buf, reinterpret_cast<const C*>(a.T), twa, twb, sub, j);
   // x + correction, kinetic post-phase, store
   {
     const bool post = !lazy && a.units_post != 0;
@@ -1213,6 +1221,116 @@ pass_fast2d_kernel(const PassArgs a) {
   if (lazy && t == 0) a.touch_own[s] = a.now;
 }
 
+// Two adjacent slices per CTA for the strided layer (slice stride 1 element):
+// one 16-byte load or store moves an element of both slices, which halves the
+// requests and doubles the used bytes per sector of the column-wise access.
+// The slices are transformed one after the other in the same buffer; the
+// second slice's input waits in registers, the first slice's result in
+// shared memory.  Full passes (no slice list) in MODE_STEP, complex64.
+template <typename Real>
+__global__ void __launch_bounds__(256, 2) pass_fast2d_pair_kernel(const PassArgs a) {
+  static_assert(sizeof(Real) == 4, "complex64 only");
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const LayerGeom& g = a.g;
+  const int t = threadIdx.x;
+  const int sub = t & 63, j = t >> 6;
+  C* buf = reinterpret_cast<C*>(smraw);
+  C* xs = buf + 64 * kF2Row;
+  __shared__ uint64_t s_la[2], s_lb[2], s_c0[2];
+  const int64_t s0 = 2 * (int64_t)blockIdx.x;
+  if (s0 >= g.nslices) return;
+  const bool has1 = s0 + 1 < g.nslices;
+  if (t < 2) {
+    const int64_t s = s0 + t;
+    const uint64_t ua = (uint64_t)(s % g.oqa + g.olo_a), ub = (uint64_t)(s / g.oqa + g.olo_b);
+    s_la[t] = g.X_aa * ua + g.X_ab * ub;
+    s_lb[t] = g.X_ba * ua + g.X_bb * ub;
+    s_c0[t] = g.C_aa * (ua * ua) + g.C_ab * (ua * ub) + g.C_bb * (ub * ub);
+  }
+  __syncthreads();
+  C* pp = reinterpret_cast<C*>(a.psi) + s0 + sub * g.ea + j * g.eb;
+  const int64_t estep = 4 * g.eb;
+  const C* twa = reinterpret_cast<const C*>(g.tw);
+  const C* twb = reinterpret_cast<const C*>(g.twb);
+  const C* T = reinterpret_cast<const C*>(a.T);
+  C x1[16];
+  {
+    C x0[16];
+    if (has1) {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const float4 q = *reinterpret_cast<const float4*>(pp + m * estep);
+        x0[m] = make_float2(q.x, q.y);
+        x1[m] = make_float2(q.z, q.w);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        x0[m] = pp[m * estep];
+        x1[m] = make_float2(0.f, 0.f);
+      }
+    }
+    if (a.units_pre != 0) {
+      QuadWalk w0(g, sub, j, s_la[0], s_lb[0], s_c0[0]), w1(g, sub, j, s_la[1], s_lb[1], s_c0[1]);
+      w0.scale((uint64_t)0 - (uint64_t)a.units_pre);
+      w1.scale((uint64_t)0 - (uint64_t)a.units_pre);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        x0[m] = apply_phase<float>(x0[m], phase_of<float>(w0.q));
+        x1[m] = apply_phase<float>(x1[m], phase_of<float>(w1.q));
+        w0.next();
+        w1.next();
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int ib = j + 4 * m;
+      xs[sub + 64 * ib] = x0[m];
+      buf[sub + kF2Row * ib] = x0[m];
+    }
+  }
+  __syncthreads();
+  f2_correction<float>(buf, T, twa, twb, sub, j);
+  // first slice: x + correction, post-phase, kept in xs; second slice's input
+  // into buf (each thread touches only its own elements here)
+  {
+    QuadWalk w(g, sub, j, s_la[0], s_lb[0], s_c0[0]);
+    const bool post = a.units_post != 0;
+    if (post) w.scale((uint64_t)0 - (uint64_t)a.units_post);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int ib = j + 4 * m;
+      C x = cadd(xs[sub + 64 * ib], buf[sub + kF2Row * ib]);
+      if (post) {
+        x = apply_phase<float>(x, phase_of<float>(w.q));
+        w.next();
+      }
+      xs[sub + 64 * ib] = x;
+      buf[sub + kF2Row * ib] = x1[m];
+    }
+  }
+  __syncthreads();
+  f2_correction<float>(buf, T, twa, twb, sub, j);
+  {
+    QuadWalk w(g, sub, j, s_la[1], s_lb[1], s_c0[1]);
+    const bool post = a.units_post != 0;
+    if (post) w.scale((uint64_t)0 - (uint64_t)a.units_post);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int ib = j + 4 * m;
+      C x = cadd(x1[m], buf[sub + kF2Row * ib]);
+      if (post) {
+        x = apply_phase<float>(x, phase_of<float>(w.q));
+        w.next();
+      }
+      const C r0 = xs[sub + 64 * ib];
+      if (has1) *reinterpret_cast<float4*>(pp + m * estep) = make_float4(r0.x, r0.y, x.x, x.y);
+      else pp[m * estep] = r0;
+    }
+  }
+}
+
 template <typename Real> size_t fast2d_smem_bytes(const LayerGeom& g) {
   using C = typename CT<Real>::C;
   return ((size_t)64 * kF2Row + (size_t)g.M) * sizeof(C);
@@ -1222,6 +1340,14 @@ template <typename Real> cudaError_t launch_fast2d(const PassArgs& a, int64_t nt
   if (ntiles <= 0) return cudaSuccess;
   if (a.g.d != 2 || a.g.qa != 64 || a.g.qb != 64) return cudaErrorInvalidValue;
   const size_t smem = fast2d_smem_bytes<Real>(a.g);
+  if constexpr (sizeof(Real) == 4) {
+    // strided layer, full pass, 16-byte aligned slice pairs: two slices per CTA
+    if (a.mode == MODE_STEP && a.list == nullptr && a.g.slice_stride == 1 && (a.g.ea % 2) == 0 &&
+        (a.g.eb % 2) == 0 && (reinterpret_cast<uintptr_t>(a.psi) % 16) == 0) {
+      pass_fast2d_pair_kernel<Real><<<(unsigned)((a.g.nslices + 1) / 2), 256, smem, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if (a.mode == MODE_LAZY) pass_fast2d_kernel<Real, MODE_LAZY><<<(unsigned)ntiles, 256, smem, st>>>(a);
   else pass_fast2d_kernel<Real, MODE_STEP><<<(unsigned)ntiles, 256, smem, st>>>(a);
   return cudaGetLastError();
@@ -1229,6 +1355,8 @@ template <typename Real> cudaError_t launch_fast2d(const PassArgs& a, int64_t nt
 
 template <typename Real> cudaError_t fast2d_prepare(size_t max_smem) {
   cudaError_t e = allow_smem(pass_fast2d_kernel<Real, MODE_STEP>, max_smem);
+  if constexpr (sizeof(Real) == 4)
+    if (e == cudaSuccess) e = allow_smem(pass_fast2d_pair_kernel<Real>, max_smem);
   if (e == cudaSuccess) e = allow_smem(pass_fast2d_kernel<Real, MODE_LAZY>, max_smem);
   return e;
 }
