@@ -1361,6 +1361,179 @@ template <typename Real> cudaError_t fast2d_prepare(size_t max_smem) {
   return e;
 }
 
+// Two adjacent columns per CTA for the strided 1D layer (slice stride 1
+// element, transform length 4096, complex64): one 16-byte load or store moves
+// an element of both columns.  The columns are transformed one after the
+// other in one shared buffer (the convolution form, or the plain form for
+// power-of-two lengths); the second column's input waits in registers (NX per
+// thread), the first column's result in shared memory.  Thread t owns
+// elements i = t + 256 k; kinetic phases step along k by exact second
+// differences modulo 2^64.  Full passes in MODE_STEP only.
+struct QuadWalk1 {
+  uint64_t q, d, dd;
+  __device__ __forceinline__ QuadWalk1(const LayerGeom& g, int i0, int step, uint64_t la, uint64_t c0) {
+    const uint64_t m = (uint64_t)(int64_t)(g.lo_a + i0), st = (uint64_t)step;
+    q = g.A_aa * (m * m) + la * m + c0;
+    d = g.A_aa * (2 * m * st + st * st) + la * st;
+    dd = 2 * g.A_aa * (st * st);
+  }
+  __device__ __forceinline__ void scale(uint64_t u) {
+    q *= u;
+    d *= u;
+    dd *= u;
+  }
+  __device__ __forceinline__ void next() {
+    q += d;
+    d += dd;
+  }
+};
+
+template <typename Real, int NX>
+__device__ __forceinline__ void fast_pair_middle(typename CT<Real>::C* buf, const PassArgs& a, bool conv, int j) {
+  using C = typename CT<Real>::C;
+  constexpr int LOGN = 12, TPS = 256;
+  const C* tw = reinterpret_cast<const C*>(a.g.tw);
+  C v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = buf[phys(j + r * TPS)];
+  __syncthreads();
+  int flip = 1;
+  if (conv) {
+    const C* Kh = reinterpret_cast<const C*>(a.Khat);
+    fast_fft<Real, LOGN, false, true>(v, buf, buf, flip, tw, j, Kh);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], Kh[j + r * TPS]);
+    fast_fft<Real, LOGN, true, true>(v, buf, buf, flip, tw, j);
+  } else {
+    const C* T = reinterpret_cast<const C*>(a.T);
+    fast_fft<Real, LOGN, true, true>(v, buf, buf, flip, tw, j);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], T[j + r * TPS]);
+    fast_fft<Real, LOGN, false, true>(v, buf, buf, flip, tw, j);
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) buf[phys(j + r * TPS)] = v[r];
+  __syncthreads();
+}
+
+template <typename Real, int NX>
+__global__ void __launch_bounds__(256, 2) pass_fast_pair_kernel(const PassArgs a) {
+  static_assert(sizeof(Real) == 4, "complex64 only");
+  using C = float2;
+  constexpr int N = 4096;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const LayerGeom& g = a.g;
+  const int Q = g.qa;
+  const int t = threadIdx.x;
+  const bool conv = a.Khat != nullptr;
+  C* buf = reinterpret_cast<C*>(smraw);
+  C* xs = buf + g.sb;
+  __shared__ uint64_t s_la[2], s_c0[2];
+  __shared__ C s_last1;
+  const int64_t s0 = 2 * (int64_t)blockIdx.x;
+  if (s0 >= g.nslices) return;
+  const bool has1 = s0 + 1 < g.nslices;
+  if (t < 2) {
+    const uint64_t ua = (uint64_t)(s0 + t + g.olo_a);
+    s_la[t] = g.X_aa * ua;
+    s_c0[t] = g.C_aa * (ua * ua);
+  }
+  __syncthreads();
+  C* pp = reinterpret_cast<C*>(a.psi) + s0 + (int64_t)t * g.ea;
+  const int64_t estep = 256 * g.ea;
+  C x1[NX];
+  {
+    C x0[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      x0[k] = x1[k] = make_float2(0.f, 0.f);
+      if (t + 256 * k < Q) {
+        if (has1) {
+          const float4 q = *reinterpret_cast<const float4*>(pp + k * estep);
+          x0[k] = make_float2(q.x, q.y);
+          x1[k] = make_float2(q.z, q.w);
+        } else {
+          x0[k] = pp[k * estep];
+        }
+      }
+    }
+    if (a.units_pre != 0) {
+      QuadWalk1 w0(g, t, 256, s_la[0], s_c0[0]), w1(g, t, 256, s_la[1], s_c0[1]);
+      w0.scale((uint64_t)0 - (uint64_t)a.units_pre);
+      w1.scale((uint64_t)0 - (uint64_t)a.units_pre);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        if (t + 256 * k < Q) {
+          x0[k] = apply_phase<float>(x0[k], phase_of<float>(w0.q));
+          x1[k] = apply_phase<float>(x1[k], phase_of<float>(w1.q));
+        }
+        w0.next();
+        w1.next();
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      const int i = t + 256 * k;
+      if (i < Q) {
+        xs[i] = x0[k];
+        if (i == Q - 1) s_last1 = x1[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int i = t + 256 * k;
+      buf[phys(i)] = (k < NX && i < Q) ? x0[k < NX ? k : 0] : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  C last0 = xs[Q - 1];  // the first column's input at Q - 1 (before xs is overwritten)
+  C last1 = s_last1;
+  fast_pair_middle<float, NX>(buf, a, conv, t);
+  const bool post = a.units_post != 0;
+  const C fix = make_float2((float)a.fix0_re, (float)a.fix0_im);
+  // first column: x + correction, post-phase, kept in xs; second column's
+  // input into buf (each thread touches only its own elements here)
+  {
+    QuadWalk1 w(g, t, 256, s_la[0], s_c0[0]);
+    if (post) w.scale((uint64_t)0 - (uint64_t)a.units_post);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int i = t + 256 * k;
+      if (k < NX && i < Q) {
+        C c = buf[phys(i)];
+        if (conv && i == 0) c = cadd(c, cmul(fix, last0));
+        C x = cadd(xs[i], c);
+        if (post) x = apply_phase<float>(x, phase_of<float>(w.q));
+        xs[i] = x;
+        buf[phys(i)] = x1[k < NX ? k : 0];
+      } else {
+        buf[phys(i)] = make_float2(0.f, 0.f);
+      }
+      w.next();
+    }
+  }
+  __syncthreads();
+  fast_pair_middle<float, NX>(buf, a, conv, t);
+  {
+    QuadWalk1 w(g, t, 256, s_la[1], s_c0[1]);
+    if (post) w.scale((uint64_t)0 - (uint64_t)a.units_post);
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      const int i = t + 256 * k;
+      if (i < Q) {
+        C c = buf[phys(i)];
+        if (conv && i == 0) c = cadd(c, cmul(fix, last1));
+        C x = cadd(x1[k], c);
+        if (post) x = apply_phase<float>(x, phase_of<float>(w.q));
+        const C r0 = xs[i];
+        if (has1) *reinterpret_cast<float4*>(pp + k * estep) = make_float4(r0.x, r0.y, x.x, x.y);
+        else pp[k * estep] = r0;
+      }
+      w.next();
+    }
+  }
+}
+
 template <typename Real> size_t fast_smem_bytes(const LayerGeom& g, int W, int variant) {
   using C = typename CT<Real>::C;
   const size_t nbuf = (variant == 0) ? 2 : 1;
@@ -1376,6 +1549,17 @@ static cudaError_t launch_fast_n(const PassArgs& a, int64_t ntiles, cudaStream_t
   constexpr int NBUF = sizeof(Real) == 4 ? 1 : 2;
   constexpr int MINB = sizeof(Real) == 4 ? 3 : 1;
   const size_t smem = fast_smem_bytes<Real>(a.g, a.W, NBUF == 1 ? 1 : 0);
+  if constexpr (sizeof(Real) == 4 && LOGN == 12) {
+    // strided layer, full pass, 16-byte aligned column pairs: two columns per CTA
+    if (a.mode == MODE_STEP && a.list == nullptr && a.W == 1 && a.strided && a.g.slice_stride == 1 &&
+        a.Khat2 == nullptr && (a.Khat != nullptr || !a.g.bluestein) && (a.g.ea % 2) == 0 &&
+        (reinterpret_cast<uintptr_t>(a.psi) % 16) == 0) {
+      const unsigned nb = (unsigned)((a.g.nslices + 1) / 2);
+      if (a.g.qa <= 9 * 256) pass_fast_pair_kernel<Real, 9><<<nb, 256, smem, st>>>(a);
+      else pass_fast_pair_kernel<Real, 16><<<nb, 256, smem, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
   if (a.mode == MODE_LAZY) pass_fast_kernel<Real, LOGN, MODE_LAZY, 256, NBUF, MINB><<<(unsigned)ntiles, nt, smem, st>>>(a);
   else if (a.Khat2) pass_fast_kernel<Real, LOGN, MODE_STEP, 256, NBUF, MINB, true><<<(unsigned)ntiles, nt, smem, st>>>(a);
   else pass_fast_kernel<Real, LOGN, MODE_STEP, 256, NBUF, MINB><<<(unsigned)ntiles, nt, smem, st>>>(a);
@@ -1403,6 +1587,10 @@ template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
   if (e == cudaSuccess) e = allow_smem(pass_fast_kernel<Real, L, MODE_LAZY, 256, NBUF, MINB>, max_smem);
   LS_FPREP(9) LS_FPREP(10) LS_FPREP(11) LS_FPREP(12)
 #undef LS_FPREP
+  if constexpr (sizeof(Real) == 4) {
+    if (e == cudaSuccess) e = allow_smem(pass_fast_pair_kernel<Real, 9>, max_smem);
+    if (e == cudaSuccess) e = allow_smem(pass_fast_pair_kernel<Real, 16>, max_smem);
+  }
   return e;
 }
 template <typename Real> int fast_max_threads() { return 256; }

@@ -138,6 +138,34 @@ def test_step_parity_64x64_slices(P, dtype, scheme):
         assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, (p.name, rel(ctx.to_dense(psi), ref))
 
 
+def problems_strided_4096():
+    """Layer-2 columns of transform length 4096 (the two-column pass of the
+    strided layer): convolution form with an odd column count (the last CTA
+    holds one column), a shorter odd length, and the plain power-of-two form."""
+    return [
+        W.bilayer_1d(8, 1024, 1.3, 0.9, ecut=1e9),       # 17 columns of q = 2049
+        W.bilayer_1d(9, 600, 0.8, 1.1),                  # 19 columns of q = 1201, default cutoff
+        W.Problem(1, np.array([[2 * np.pi]]), np.array([[2 * np.pi / W.GOLDEN]]), (-8,), (16,),
+                  (-2048,), (4096,), 1e9, np.array([[1], [-1]]), np.array([0.6, 0.6], dtype=complex),
+                  np.array([[3], [-3]]), np.array([0.2 + 0.1j, 0.2 - 0.1j]), "pow2-16x4096"),
+    ]
+
+
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
+def test_step_parity_strided_4096(P, scheme):
+    O.use_fft(True)
+    try:
+        for p in problems_strided_4096():
+            ctx = P.Context(p, "c64")
+            x = W.random_state((p.M2, p.M1), 6)
+            psi = ctx.from_dense(x)
+            ctx.step(psi, 3, 2e-3, scheme)
+            ref = O.step(p, x, 2e-3, scheme, 3)
+            assert rel(ctx.to_dense(psi), ref) < TOL1["c64"] * 3, (p.name, rel(ctx.to_dense(psi), ref))
+    finally:
+        O.use_fft(False)
+
+
 def test_large_kinetic_phase_free_particle(P):
     """V = 0 at the 2049-box extremes: every element must be the exact phase
     exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
