@@ -1097,9 +1097,11 @@ struct ls_batch {
   std::vector<int64_t> off;   // element offset of each instance's array
   int dtype = LS_C64;
   int nthreads = 256;
-  int minb = 4;
+  int minb = 3;
   int W[2][1] = {{0}, {0}};
   std::vector<int> Wi[2];     // per instance and layer: slices per tile
+  std::vector<int> Wg;        // per instance: slices per general layer-1 tile (settle phase)
+  std::vector<int> Fi[2];     // per instance and layer: log2 of the fast tile's length (0: general tile)
   DevBuf args, cum, tsteps, counters, status, touch, seedbuf;
   std::vector<int64_t> touch_off;  // per instance: rows at touch_off[i], columns after them
   double timeout_s = 1.0;
@@ -1179,17 +1181,27 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     b->off.push_back(total);
     // slices per tile so that every tile of every instance fits the common block size
     size_t smem = 0;
+    b->Wg.resize(count);
     for (int L = 0; L < 2; ++L) {
       b->Wi[L].resize(count);
+      b->Fi[L].assign(count, 0);
       for (int32_t i = 0; i < count; ++i) {
         const lsk::LayerGeom& g = b->inst[i]->geom[L];
         int W = 1;
         while (W * 2 <= lsk::kMaxTileSlices && W * 2 <= g.nslices && lsk::pass_threads(g, W * 2, 2) <= b->nthreads)
           W *= 2;
         if (lsk::pass_threads(g, W, 2) > b->nthreads) throw CudaError{cudaErrorInvalidValue, "slice too long for the batched runner"};
+        if (L == 0) b->Wg[i] = W;
+        size_t sm = b->dtype == LS_C64 ? lsk::pass_smem_bytes<float>(g, W, lsk::MODE_STEP)
+                                       : lsk::pass_smem_bytes<double>(g, W, lsk::MODE_STEP);
+        // complex64 slices of transform length 512..2048: the fast register
+        // tile, 4096 / N slices per 256-thread tile
+        if (b->dtype == LS_C64 && g.d == 1 && g.np >= 512 && g.np <= 2048 && !getenv_flag("LSPLIT_NO_FAST")) {
+          W = 4096 / g.np;
+          b->Fi[L][i] = log2i(g.np);
+          sm = lsk::fast_smem_bytes<float>(g, W, 1);
+        }
         b->Wi[L][i] = W;
-        const size_t sm = b->dtype == LS_C64 ? lsk::pass_smem_bytes<float>(g, W, lsk::MODE_STEP)
-                                             : lsk::pass_smem_bytes<double>(g, W, lsk::MODE_STEP);
         smem = std::max(smem, sm);
       }
     }
@@ -1200,7 +1212,7 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     int per_sm = 0;
     {
       const char* mb = std::getenv("LSPLIT_BATCH_MINB");
-      b->minb = (mb && std::atoi(mb) == 2) ? 2 : 4;
+      b->minb = (mb && std::atoi(mb) == 2) ? 2 : 3;
     }
     if (b->dtype == LS_C64) LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, b->minb, &per_sm));
     else LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, b->minb, &per_sm));
@@ -1352,16 +1364,31 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
           set_kinetic(c, u);
           lsk::PassArgs a = base_args(c, L, static_cast<char*>(psi) + b->off[i] * es);
           a.W = b->Wi[L][i];
+          a.fast_logn = b->Fi[L][i];
+          a.variant = 1;
+          const bool conv = a.fast_logn && c->conv_form[L];
           int64_t tiles;
           if (!stoch) {
             a.mode = lsk::MODE_STEP;
             a.T = phase_table(c, layer, ps[q].s);
+            if (conv) {
+              const ConvTab& ct = conv_table(c, layer, ps[q].s);
+              a.Khat = ct.khat->p;
+              a.fix0_re = ct.fix_re;
+              a.fix0_im = ct.fix_im;
+            }
             tiles = (c->geom[L].nslices + a.W - 1) / a.W;
           } else {
             const int64_t Sv = c->geom[L].nslices;
             const int32_t pv = sP[(size_t)i * npass + q];
             a.mode = lsk::MODE_LAZY;
             a.T = phase_table(c, layer, ps[q].s * (double)Sv / (double)pv);
+            if (conv) {
+              const ConvTab& ct = conv_table(c, layer, ps[q].s * (double)Sv / (double)pv);
+              a.Khat = ct.khat->p;
+              a.fix0_re = ct.fix_re;
+              a.fix0_im = ct.fix_im;
+            }
             a.list = static_cast<const int32_t*>(e->lists->p) + sBase[i] + sOff[(size_t)i * npass + q];
             a.nlist = pv;
             a.list_step = sStep[i];
@@ -1386,7 +1413,7 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
           ls_ctx* c = b->inst[i];
           lsk::PassArgs a = base_args(c, 0, static_cast<char*>(psi) + b->off[i] * es);
           a.mode = lsk::MODE_KIN;
-          a.W = b->Wi[0][i];
+          a.W = b->Wg[i];
           int32_t* rows = touch + b->touch_off[i];
           a.touch_own = rows;
           a.touch_other = rows + c->M2;

@@ -75,6 +75,7 @@ struct PassArgs {
   double fix2_re, fix2_im;
   int64_t units_mid;
   int32_t variant;         // fast pass: 0 two shared buffers (2 CTAs/SM), 1 one buffer (3 CTAs/SM)
+  int32_t fast_logn;       // batched runner: tile on the fast pass of length 2^fast_logn (0: general tile)
 };
 
 struct ElemArgs {          // elementwise kernels over the whole lifted box
@@ -154,7 +155,7 @@ struct BatchArgs {
   const PassArgs* settle_args;  // [ninst]
   const int64_t* settle_cum;    // [ninst + 1]
   int64_t settle_items;
-  int32_t minb;                 // register budget variant (2 or 4 CTAs per SM)
+  int32_t minb;                 // register budget variant (2 or 3 CTAs per SM)
 };
 
 // Slice samples of a batch: block b draws instance i = b / (nsteps * npf),

@@ -820,15 +820,14 @@ template <typename K> static cudaError_t allow_smem(K kernel, size_t max_block) 
 // FUSED (convolution form only): two potential factors of the same layer
 // separated by a kinetic factor, P(s2) K(mid) P(s1), in one launch (the two
 // halves of adjacent Strang steps); the intermediate state never leaves the CTA.
-template <typename Real, int LOGN, int MODE, int NTMAX, int NBUF = 2,
-          int MINB = ((NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1), bool FUSED = false>
-__global__ void __launch_bounds__(NTMAX, MINB)
-pass_fast_kernel(const PassArgs a) {
+// One tile (W slices) of the fast pass; CG reads psi and the touch times
+// through L2 only (the batched runner, whose other CTAs wrote them).
+template <typename Real, int LOGN, int MODE, int NBUF, bool FUSED, bool CG>
+__device__ __forceinline__ void fast_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   constexpr bool SINGLE = (NBUF == 1);
   using C = typename CT<Real>::C;
   constexpr int N = 1 << LOGN, TPS = N / 16;
   constexpr bool lazy = (MODE == MODE_LAZY);
-  extern __shared__ __align__(16) unsigned char smraw[];
   const LayerGeom& g = a.g;
   const int W = a.W;
   const int Q = g.qa;
@@ -843,10 +842,10 @@ pass_fast_kernel(const PassArgs a) {
   if (t < W) {
     int64_t s = -1;
     if (a.list) {
-      const int64_t li = (int64_t)blockIdx.x * W + t;
+      const int64_t li = tile * W + t;
       if (li < a.nlist) s = a.list[li];
     } else {
-      s = (int64_t)blockIdx.x * W + t;
+      s = tile * W + t;
       if (s >= g.nslices) s = -1;
     }
     s_slice[t] = s;
@@ -856,7 +855,7 @@ pass_fast_kernel(const PassArgs a) {
       const uint64_t ua = (uint64_t)(s + g.olo_a);
       la = g.X_aa * ua;
       c0 = g.C_aa * (ua * ua);
-      if (lazy) touch = a.touch_own[s];
+      if (lazy) touch = CG ? __ldcg(a.touch_own + s) : a.touch_own[s];
     }
     s_la[t] = la;
     s_c0[t] = c0;
@@ -879,10 +878,10 @@ pass_fast_kernel(const PassArgs a) {
     const int64_t ss = s_slice[ww];
     C x = czero<C>();
     if (i < Q && ss >= 0) {
-      x = psi[ss * g.slice_stride + (int64_t)i * g.ea];
+      x = ldpsi<CG>(psi + ss * g.slice_stride + (int64_t)i * g.ea);
       int64_t units = a.units_pre;
       if (lazy) {
-        const int32_t t2 = a.touch_other[i];
+        const int32_t t2 = CG ? __ldcg(a.touch_other + i) : a.touch_other[i];
         units = (int64_t)a.now - (int64_t)(s_touch[ww] > t2 ? s_touch[ww] : t2);
       }
       if (units != 0) {
@@ -1009,6 +1008,14 @@ pass_fast_kernel(const PassArgs a) {
     }
   }
   if (lazy && t < W && s_slice[t] >= 0) a.touch_own[s_slice[t]] = a.now;
+}
+
+template <typename Real, int LOGN, int MODE, int NTMAX, int NBUF = 2,
+          int MINB = ((NTMAX == 256 && sizeof(Real) == 4) ? 2 : 1), bool FUSED = false>
+__global__ void __launch_bounds__(NTMAX, MINB)
+pass_fast_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  fast_tile<Real, LOGN, MODE, NBUF, FUSED, false>(a, (int64_t)blockIdx.x, smraw);
 }
 
 // ---------------------------------------------------------------- fast 2D pass (64 x 64 slices)
@@ -1599,6 +1606,33 @@ template <typename Real> int fast_max_threads() { return 256; }
 // 256-thread CTAs (the block size the host uses for every tile shape); 1D
 // slices only; STOCH selects the stochastic (lazy + settle) or deterministic
 // body; MINB the resident CTAs per SM the registers are budgeted for.
+// Tiles of the batched runner as calls, not inlined into the persistent loop:
+// each tile body then gets the kernel's whole register budget, and the loop
+// keeps only its few scalars across the call.
+template <typename Real, int LOGN, int MODE>
+__device__ __noinline__ void batch_fast_tile_n(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  fast_tile<Real, LOGN, MODE, 1, false, true>(a, tile, smraw);
+}
+template <typename Real, int BPT, int MODE>
+__device__ __noinline__ void batch_general_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  pass_tile<Real, BPT, MODE, true, true>(a, tile, smraw);
+}
+
+// Fast tile of a batched work item (complex64, transform length 2^9..2^11,
+// W = 4096 / N slices so that W N / 16 = 256 threads); false: general tile.
+template <typename Real, int MODE>
+__device__ __forceinline__ bool batch_fast_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  if constexpr (sizeof(Real) == 4) {
+    switch (a.fast_logn) {
+      case 9: batch_fast_tile_n<Real, 9, MODE>(a, tile, smraw); return true;
+      case 10: batch_fast_tile_n<Real, 10, MODE>(a, tile, smraw); return true;
+      case 11: batch_fast_tile_n<Real, 11, MODE>(a, tile, smraw); return true;
+      default: return false;
+    }
+  }
+  return false;
+}
+
 template <typename Real, int BPT, bool STOCH, int MINB>
 __global__ void __launch_bounds__(256, MINB)
 batch_kernel(const BatchArgs b) {
@@ -1721,10 +1755,12 @@ batch_kernel(const BatchArgs b) {
       __syncthreads();
     }
     if constexpr (STOCH) {
-      if (s_settle) pass_tile<Real, BPT, MODE_KIN, true, true>(s_args, s_tile, smraw);
-      else pass_tile<Real, BPT, MODE_LAZY, true, true>(s_args, s_tile, smraw);
+      if (s_settle) batch_general_tile<Real, BPT, MODE_KIN>(s_args, s_tile, smraw);
+      else if (!batch_fast_tile<Real, MODE_LAZY>(s_args, s_tile, smraw))
+        batch_general_tile<Real, BPT, MODE_LAZY>(s_args, s_tile, smraw);
     } else {
-      pass_tile<Real, BPT, MODE_STEP, true, true>(s_args, s_tile, smraw);
+      if (!batch_fast_tile<Real, MODE_STEP>(s_args, s_tile, smraw))
+        batch_general_tile<Real, BPT, MODE_STEP>(s_args, s_tile, smraw);
     }
     __threadfence();
     __syncthreads();
@@ -1734,9 +1770,9 @@ batch_kernel(const BatchArgs b) {
 
 template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
                                                   cudaStream_t st) {
-  if (b.minb == 4) {
-    if (b.stoch) batch_kernel<Real, 2, true, 4><<<nblocks, nthreads, smem, st>>>(b);
-    else batch_kernel<Real, 2, false, 4><<<nblocks, nthreads, smem, st>>>(b);
+  if (b.minb == 3) {
+    if (b.stoch) batch_kernel<Real, 2, true, 3><<<nblocks, nthreads, smem, st>>>(b);
+    else batch_kernel<Real, 2, false, 3><<<nblocks, nthreads, smem, st>>>(b);
   } else {
     if (b.stoch) batch_kernel<Real, 2, true, 2><<<nblocks, nthreads, smem, st>>>(b);
     else batch_kernel<Real, 2, false, 2><<<nblocks, nthreads, smem, st>>>(b);
@@ -1748,11 +1784,11 @@ template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads
                                                    int* blocks_per_sm) {
   cudaError_t e = cudaSuccess;
   int a = 0, c = 0;
-  if (minb == 4) {
-    e = allow_smem(batch_kernel<Real, 2, false, 4>, max_smem);
-    if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 4>, max_smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, 4>, nthreads, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, 4>, nthreads, smem);
+  if (minb == 3) {
+    e = allow_smem(batch_kernel<Real, 2, false, 3>, max_smem);
+    if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 3>, max_smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, 3>, nthreads, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, 3>, nthreads, smem);
   } else {
     e = allow_smem(batch_kernel<Real, 2, false, 2>, max_smem);
     if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 2>, max_smem);
@@ -1794,7 +1830,7 @@ template <typename Real> cudaError_t launch_pass(const PassArgs& a, int bpt, int
                                                  cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   const size_t smem = pass_smem_bytes<Real>(a.g, a.W, a.mode);
-  if (bpt == 4) return launch_pass_b<Real, 4>(a, nthreads, ntiles, smem, st);
+  if (bpt == 4) return launch_pass_b<Real, 3>(a, nthreads, ntiles, smem, st);
   return launch_pass_b<Real, 2>(a, nthreads, ntiles, smem, st);
 }
 

@@ -72,6 +72,26 @@ def test_batched_runner_stochastic_parity(P, dtype, tol, scheme):
         assert rel(b.get_dense(psi, i), ref) < tol * 5
 
 
+@pytest.mark.parametrize("scheme", ["strang", "lie", "strang_stoch"])
+def test_batched_fast_tiles_parity(P, scheme):
+    """Lengths 129..1001 (transforms of 256..2048 points): most slices run on
+    the register-resident fast tiles inside the persistent launch."""
+    probs = W.batch_1d(count=5, seed=8, nmin=64, nmax=500)
+    b = P.Batch(probs, "c64")
+    psi = b.empty()
+    xs = [W.random_state((p.M2, p.M1), 70 + i) for i, p in enumerate(probs)]
+    for i, x in enumerate(xs):
+        b.set_dense(psi, i, x)
+    b.step(psi, 3, 1e-3, scheme, seed=5, step0=1)
+    O.use_fft(True)
+    try:
+        for i, p in enumerate(probs):
+            ref = O.step(p, xs[i], 1e-3, scheme, 3, seed=5 + i, step0=1)
+            assert rel(b.get_dense(psi, i), ref) < 3e-5, (i, p.name, rel(b.get_dense(psi, i), ref))
+    finally:
+        O.use_fft(False)
+
+
 def test_batched_matches_single_contexts(P):
     """The same instances stepped one context at a time agree with the batch."""
     probs = W.batch_1d(count=5, seed=11, nmin=8, nmax=300)
