@@ -178,7 +178,9 @@ def profile_case(args):
     1d    : 2049 x 8192 lifted box (134 MB complex64); layer-1 slices of length
             2049 use the same convolution-form pass as the bench workload;
     2d    : the 64^4 twisted bilayer (134 MB), dedicated pass for 64 x 64 slices;
-    batch : 64 uneven instances of the batched workload, one persistent launch."""
+    batch : 64 uneven instances of the batched workload, one persistent launch;
+    bench : the 2049 x 2049 bench workload itself (33.8 MB, L2-resident like
+            the timed bench), one ls_step call of --steps steps."""
     import torch
     import __graft_entry__ as G
     G.build()
@@ -197,6 +199,9 @@ def profile_case(args):
     if kind == "2d":
         p = W.twisted_2d(q=64)
         x0, k0, tau = [0.0, 0.0], [1.0, 0.0], 1e-3
+    elif kind == "bench":
+        p = W.config_scale_1d()
+        x0, k0, tau = [0.0], [1.0], TAU
     else:
         p = W.Problem(1, np.array([[2 * math.pi]]), np.array([[2 * math.pi / W.GOLDEN]]), (-1024,), (2049,),
                       (-4096,), (8192,), 1e12, np.array([[1], [-1]]), np.array([0.6, 0.6], dtype=complex),
@@ -464,7 +469,8 @@ def run_ours(args):
                          "speedup_fp32_over_fp64": value / world / fp64_value},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": traffic,
-                         "note": f"pass_fast_kernel (convolution form, N={nfft}): {flops:.3e} algorithmic "
+                         "note": f"the 1D pass kernels (fused layer-1 pass_fast_kernel, two-column layer-2 "
+                                 f"pass_fast_pair_kernel; convolution form, N={nfft}): {flops:.3e} algorithmic "
                                  f"flops per layer factor, {ms_factor * 1e3:.1f} us per factor averaged over the "
                                  f"{nlaunch} launches of a {NI}-step call (a fused launch applies two factors); "
                                  f"FP32 peak derived from 152 SMs x 128 lanes x 2 x {clk_peak:.0f} MHz"},
@@ -496,7 +502,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--suite", action="store_true", help="throughput lines of the secondary workloads")
-    ap.add_argument("--profile-case", choices=["1d", "2d", "batch"], default=None,
+    ap.add_argument("--profile-case", choices=["1d", "2d", "batch", "bench"], default=None,
                     help="run an ncu target (array larger than L2) instead of the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:
