@@ -76,7 +76,8 @@ enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_
  *   dtype         LS_C64 (complex float, FP64 phase arithmetic) or LS_C128
  *   frac_den      stochastic sampling denominator (p = max(1, S/frac_den)), >= 1
  * Supported slice shapes: 1D any length (powers of two use a direct radix FFT,
- * others a Bluestein transform of power-of-two length >= 2q-2, at most 8192);
+ * others a Bluestein transform of power-of-two length >= 2q-2, at most 8192
+ * for LS_C64 and 4096 for LS_C128; ls_create returns LS_ERR_INVALID beyond);
  * 2D slices need power-of-two extents with q_1 * q_2 <= 4096. */
 typedef struct ls_problem {
   int32_t d;

@@ -375,6 +375,8 @@ int validate(const ls_problem* p) {
       const int64_t n = q[0];
       const int64_t np = is_pow2(n) ? n : (int64_t(1) << log2i(2 * n - 2));
       if (np > 8192) return fail(LS_ERR_INVALID, "1D slice length too large (transform length > 8192)");
+      if (p->dtype == LS_C128 && np > 4096)
+        return fail(LS_ERR_INVALID, "complex128 1D slices are limited to transform length 4096");
     } else {
       if (!is_pow2(q[0]) || !is_pow2(q[1]))
         return fail(LS_ERR_INVALID, "2D slices need power-of-two extents");

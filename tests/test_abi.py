@@ -51,6 +51,11 @@ def test_invalid_problems_rejected_before_cuda(lib):
     # 1D slice whose Bluestein length exceeds 8192
     st, keep = make_problem_struct(W.bilayer_1d(2100, 4, ecut=1.0))
     assert lib.ls_create(C.byref(st), C.byref(h)) == -1
+    # complex128 slice whose transform length exceeds 4096 (q = 4097 -> 8192)
+    st, keep = make_problem_struct(W.bilayer_1d(2048, 2, ecut=1.0))
+    st.dtype = 1
+    assert lib.ls_create(C.byref(st), C.byref(h)) == -1
+    assert b"complex128" in lib.ls_last_error()
     # bad dtype, bad frac_den, NULL out
     st, keep = make_problem_struct(W.config_small_1d())
     st.dtype = 7
