@@ -568,8 +568,8 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
   }
   // Adjacent layer-1 factors of consecutive Strang steps (separated by one
   // merged kinetic factor) run as one fused pass when the layer takes the
-  // convolution form on the fast path.
-  if (!stoch && base_scheme(scheme) == LS_STRANG && c->conv_form[0] && c->fastW[0] > 0 &&
+  // convolution form on the fast path or the dedicated 64 x 64 pass.
+  if (!stoch && base_scheme(scheme) == LS_STRANG && ((c->conv_form[0] && c->fastW[0] > 0) || c->fast2d[0]) &&
       !getenv_flag("LSPLIT_NO_FUSE")) {
     std::vector<PassSpec> merged;
     for (size_t i = 0; i < ps.size(); ++i) {
@@ -608,6 +608,10 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
           a.fix2_im = c2.fix_im;
           a.units_mid = q.mid;
         }
+      }
+      if (q.fused && c->fast2d[L]) {
+        a.T2 = phase_table(c, q.layer, q.s2);
+        a.units_mid = q.mid;
       }
       a.units_pre = q.pre;
       a.units_post = q.post;

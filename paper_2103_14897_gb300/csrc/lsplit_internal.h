@@ -76,6 +76,7 @@ struct PassArgs {
   int64_t units_mid;
   int32_t variant;         // fast pass: 0 two shared buffers (2 CTAs/SM), 1 one buffer (3 CTAs/SM)
   int32_t fast_logn;       // batched runner: tile on the fast pass of length 2^fast_logn (0: general tile)
+  const void* T2;          // fused 2D pass: (T - 1)/M table of the second factor
 };
 
 struct ElemArgs {          // elementwise kernels over the whole lifted box

@@ -1132,7 +1132,10 @@ __device__ __forceinline__ void f2_correction(typename CT<Real>::C* buf, const t
   __syncthreads();
 }
 
-template <typename Real, int MODE>
+// FUSED: two layer-1 factors of consecutive Strang steps in one launch, with
+// the merged kinetic factor (units_mid) between them and the second factor's
+// table in T2; the intermediate slice stays in shared memory.
+template <typename Real, int MODE, bool FUSED = false>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 3 : 1)
 pass_fast2d_kernel(const PassArgs a) {
   using C = typename CT<Real>::C;
@@ -1209,6 +1212,25 @@ pass_fast2d_kernel(const PassArgs a) {
   }
   __syncthreads();
   f2_correction<Real>(buf, reinterpret_cast<const C*>(a.T), twa, twb, sub, j);
+  if constexpr (FUSED) {
+    // x1 = K(mid) (x + correction): the second factor's input and identity term
+    QuadWalk w(g, sub, j, s_la, s_lb, s_c0);
+    const bool mid = a.units_mid != 0;
+    if (mid) w.scale((uint64_t)0 - (uint64_t)a.units_mid);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int ib = j + 4 * m;
+      C x = cadd(xs[sub + 64 * ib], buf[sub + kF2Row * ib]);
+      if (mid) {
+        x = apply_phase<Real>(x, phase_of<Real>(w.q));
+        w.next();
+      }
+      xs[sub + 64 * ib] = x;
+      buf[sub + kF2Row * ib] = x;
+    }
+    __syncthreads();
+    f2_correction<Real>(buf, reinterpret_cast<const C*>(a.T2), twa, twb, sub, j);
+  }
   // x + correction, kinetic post-phase, store
   {
     const bool post = !lazy && a.units_post != 0;
@@ -1349,19 +1371,21 @@ template <typename Real> cudaError_t launch_fast2d(const PassArgs& a, int64_t nt
   const size_t smem = fast2d_smem_bytes<Real>(a.g);
   if constexpr (sizeof(Real) == 4) {
     // strided layer, full pass, 16-byte aligned slice pairs: two slices per CTA
-    if (a.mode == MODE_STEP && a.list == nullptr && a.g.slice_stride == 1 && (a.g.ea % 2) == 0 &&
-        (a.g.eb % 2) == 0 && (reinterpret_cast<uintptr_t>(a.psi) % 16) == 0) {
+    if (a.mode == MODE_STEP && a.list == nullptr && a.T2 == nullptr && a.g.slice_stride == 1 &&
+        (a.g.ea % 2) == 0 && (a.g.eb % 2) == 0 && (reinterpret_cast<uintptr_t>(a.psi) % 16) == 0) {
       pass_fast2d_pair_kernel<Real><<<(unsigned)((a.g.nslices + 1) / 2), 256, smem, st>>>(a);
       return cudaGetLastError();
     }
   }
   if (a.mode == MODE_LAZY) pass_fast2d_kernel<Real, MODE_LAZY><<<(unsigned)ntiles, 256, smem, st>>>(a);
+  else if (a.T2) pass_fast2d_kernel<Real, MODE_STEP, true><<<(unsigned)ntiles, 256, smem, st>>>(a);
   else pass_fast2d_kernel<Real, MODE_STEP><<<(unsigned)ntiles, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <typename Real> cudaError_t fast2d_prepare(size_t max_smem) {
   cudaError_t e = allow_smem(pass_fast2d_kernel<Real, MODE_STEP>, max_smem);
+  if (e == cudaSuccess) e = allow_smem(pass_fast2d_kernel<Real, MODE_STEP, true>, max_smem);
   if constexpr (sizeof(Real) == 4)
     if (e == cudaSuccess) e = allow_smem(pass_fast2d_pair_kernel<Real>, max_smem);
   if (e == cudaSuccess) e = allow_smem(pass_fast2d_kernel<Real, MODE_LAZY>, max_smem);
