@@ -36,13 +36,13 @@ import numpy as np
 
 __all__ = [
     "box_indices", "wavevectors", "kinetic_energy_diag", "index_mask", "mask_count",
-    "dft_matrix", "grid_potential", "apply_K", "apply_P", "scheme_factors", "step",
+    "dft_matrix", "grid_potential", "apply_K", "apply_P", "scheme_factors", "yoshida_weights", "step",
     "splitmix64_next", "sample_slices", "observables", "gaussian_packet",
     "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient", "use_fft",
     "TRANSFORM", "sample_count", "expanded_factors",
 ]
 
-SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch")
+SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch", "yoshida4")
 MASK64 = (1 << 64) - 1
 
 
@@ -206,6 +206,17 @@ def apply_P(prob, phi: np.ndarray, layer: int, s: float,
     return Y if layer == 1 else Y.T.copy()
 
 
+def yoshida_weights() -> Tuple[float, float]:
+    """Weights of the symmetric fourth-order composition S(w1 t) S(w0 t) S(w1 t)
+    of a symmetric second-order step S (Yoshida 1990, the higher-order
+    splittings cited in Sec. 4.2 and Appendix A): 2 w1 + w0 = 1 keeps the
+    total time, 2 w1^3 + w0^3 = 0 cancels the third-order error, so
+    w1 = 1 / (2 - 2^(1/3)) and w0 = -2^(1/3) w1."""
+    c = 2.0 ** (1.0 / 3.0)
+    w1 = 1.0 / (2.0 - c)
+    return w1, -c * w1
+
+
 def scheme_factors(scheme: str, tau: float) -> List[Tuple]:
     """Factor list of one time step, in application order (rightmost operator
     first).  ('K', s) or ('P', layer, s).
@@ -214,14 +225,20 @@ def scheme_factors(scheme: str, tau: float) -> List[Tuple]:
     strang     : L1(t/2) L2(t) L1(t/2), L_j(s) = K(s/4) P_j(s) K(s/4)
                  (Appendix A Strang over H = H1 + H2, H_j = D/2 + V^j)
     strang_kp  : K(t/2) P2(t) P1(t) K(t/2)             (kinetic/potential Strang)
+    yoshida4   : strang(w1 t) strang(w0 t) strang(w1 t)  (fourth order, see
+                 yoshida_weights)
     *_stoch    : same factor list, potential factors act on sampled slices."""
     base = scheme.replace("_stoch", "")
     t = tau
+    L = lambda j, s: [("K", s / 4), ("P", j, s), ("K", s / 4)]
+    strang = lambda h: L(1, h / 2) + L(2, h) + L(1, h / 2)
     if base == "lie":
         return [("K", t), ("P", 1, t), ("P", 2, t)]
     if base == "strang":
-        L = lambda j, s: [("K", s / 4), ("P", j, s), ("K", s / 4)]
-        return L(1, t / 2) + L(2, t) + L(1, t / 2)
+        return strang(t)
+    if base == "yoshida4":
+        w1, w0 = yoshida_weights()
+        return strang(w1 * t) + strang(w0 * t) + strang(w1 * t)
     if base == "strang_kp":
         return [("K", t / 2), ("P", 1, t), ("P", 2, t), ("K", t / 2)]
     raise ValueError(f"unknown scheme {scheme}")

@@ -25,6 +25,8 @@ PINS = [
     lambda: pins.test_free_particle_exact_phase("strang"),
     lambda: pins.test_convergence_order_against_dense_exponential("strang", 2),
     lambda: pins.test_convergence_order_against_dense_exponential("lie", 1),
+    lambda: pins.test_convergence_order_against_dense_exponential("yoshida4", 4),
+    pins.test_yoshida_weights_conditions,
     pins.test_adjoint_matches_central_differences,
     pins.test_one_step_equals_dense_factor_product,
 ]
@@ -35,6 +37,7 @@ _orig_axis = L._axis_dft
 _orig_grid = L.grid_potential
 _orig_factors = L.scheme_factors
 _orig_P = L.apply_P
+_orig_yw = L.yoshida_weights
 
 
 def _strang_wrong(scheme, tau):
@@ -64,6 +67,8 @@ MUTANTS = {
                        _orig_P(p, phi, 3 - layer, s, slices, None)),
     "strang_wrong_duration": ("scheme_factors", _strang_wrong),
     "lie_wrong_order": ("scheme_factors", _lie_wrong_order),
+    "yoshida_weights_swapped": ("yoshida_weights", lambda: _orig_yw()[::-1]),
+    "yoshida_middle_forward": ("yoshida_weights", lambda: (_orig_yw()[0], -_orig_yw()[1])),
 }
 
 

@@ -135,6 +135,25 @@ def test_layer_factors_commute():
     np.testing.assert_allclose(a, b, atol=1e-13)
 
 
+def test_yoshida_weights_conditions():
+    """The composition keeps the total time (2 w1 + w0 = 1) and cancels the
+    third-order term (2 w1^3 + w0^3 = 0); the middle step runs backward."""
+    w1, w0 = O.yoshida_weights()
+    assert abs(2 * w1 + w0 - 1) < 1e-15
+    assert abs(2 * w1 ** 3 + w0 ** 3) < 1e-14
+    assert w0 < 0 < w1
+    f = O.scheme_factors("yoshida4", 0.3)
+    assert abs(sum(x[1] for x in f if x[0] == "K") - 0.3) < 1e-15
+    assert abs(sum(x[2] for x in f if x[0] == "P" and x[1] == 2) - 0.3) < 1e-15
+
+
+def test_yoshida_time_reversible():
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 8)
+    y = O.step(p, O.step(p, x, 0.01, "yoshida4", 3), -0.01, "yoshida4", 3)
+    np.testing.assert_allclose(y, x, atol=1e-13)
+
+
 def test_strang_time_reversible():
     p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
     x = rand_state(p, 8)
@@ -147,10 +166,12 @@ def _errors(prob, scheme, T, ns, phi0, exact):
     return [np.linalg.norm(O.step(prob, phi0, T / n, scheme, n) - exact) for n in ns]
 
 
-@pytest.mark.parametrize("scheme,order", [("lie", 1), ("strang", 2), ("strang_kp", 2)])
+@pytest.mark.parametrize("scheme,order", [("lie", 1), ("strang", 2), ("strang_kp", 2), ("yoshida4", 4)])
 def test_convergence_order_against_dense_exponential(scheme, order):
-    """Theorem 4.5 (order 1 for the Lie form of Algorithm 3) and Strang order 2
-    (Appendix A), against exp(-i T H) of the dense lifted H from coefficients."""
+    """Theorem 4.5 (order 1 for the Lie form of Algorithm 3), Strang order 2
+    (Appendix A) and order 4 for the Yoshida composition of Strang steps (the
+    higher-order splittings of Sec. 4.2 and Appendix A), against exp(-i T H)
+    of the dense lifted H from coefficients."""
     p = small_1d()
     H = dense_H_1d(p)
     phi0 = rand_state(p, 9)
@@ -160,7 +181,7 @@ def test_convergence_order_against_dense_exponential(scheme, order):
     err = _errors(p, scheme, T, ns, phi0, exact)
     slope = np.polyfit(np.log([T / n for n in ns]), np.log(err), 1)[0]
     assert abs(slope - order) < 0.1, (scheme, slope, err)
-    assert err[-1] < (1e-2 if order == 1 else 1e-4)
+    assert err[-1] < {1: 1e-2, 2: 1e-4, 4: 1e-7}[order]
 
 
 def test_one_step_equals_dense_factor_product():
