@@ -59,8 +59,13 @@ enum { LS_C64 = 0, LS_C128 = 1 };
  *   LS_STRANG_KP    K(tau/2), P1(tau), P2(tau), K(tau/2)
  *   LS_LIE_STOCH, LS_STRANG_STOCH: as above, but every layer factor acts on
  *                   p = max(1, S/frac_den) seeded random slices out of S with
- *                   duration s*S/p (Algorithm 4); kinetic factors act on all. */
-enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_STOCH = 4 };
+ *                   duration s*S/p (Algorithm 4); kinetic factors act on all.
+ *   LS_YOSHIDA4     fourth order: three LS_STRANG steps of w1 tau, w0 tau, w1 tau,
+ *                   w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3) w1 (the higher-order
+ *                   splittings of Sec. 4.2 and Appendix A, by Yoshida's symmetric
+ *                   composition); ls_step only (not the batched runner or
+ *                   ls_adjoint, which return LS_ERR_INVALID). */
+enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_STOCH = 4, LS_YOSHIDA4 = 5 };
 
 /* Problem description (Sec. 2-3).  All arrays are read during ls_create only
  * and stay owned by the caller.

@@ -129,6 +129,7 @@ struct PassSpec {
   double s2 = 0;      // fused pass: duration of the second factor
   int64_t mid = 0;    // fused pass: kinetic units between the two factors
   bool fused = false;
+  double unit = 0;    // kinetic unit of this pass's pre/post factors (0: the call's unit)
 };
 
 struct ConvTab {
@@ -521,6 +522,30 @@ double build_passes(int scheme, double tau, int64_t n, std::vector<PassSpec>& ou
     end_time = (int32_t)(8 * n);
     return tau / 8;
   }
+  if (scheme == LS_YOSHIDA4) {
+    // three Strang sub-steps of w1 tau, w0 tau, w1 tau; each sub-step h has the
+    // kinetic factors h/8, 3h/8, 3h/8, h/8, and the last one merges with the
+    // first of the next sub-step.  The durations are incommensurate, so every
+    // pass carries its own kinetic unit.
+    const double cr = std::cbrt(2.0), w1 = 1.0 / (2.0 - cr), w0 = -cr * w1;
+    const double h[3] = {w1 * tau, w0 * tau, w1 * tau};
+    int pidx = 0;
+    for (int64_t k = 0; k < n; ++k)
+      for (int j = 0; j < 3; ++j) {
+        const bool first = k == 0 && j == 0, last = k == n - 1 && j == 2;
+        PassSpec a{1, h[j] / 2, first ? 1 : 0, 3, 0, pidx++, k};
+        a.unit = h[j] / 8;
+        PassSpec b{2, h[j], 0, 3, 0, pidx++, k};
+        b.unit = h[j] / 8;
+        PassSpec e{1, h[j] / 2, 0, 1, 0, pidx++, k};
+        e.unit = last ? h[j] / 8 : (h[j] + h[(j + 1) % 3]) / 8;
+        out.push_back(a);
+        out.push_back(b);
+        out.push_back(e);
+      }
+    end_time = 0;
+    return tau / 8;
+  }
   // LS_STRANG_KP
   for (int64_t k = 0; k < n; ++k) {
     out.push_back({1, tau, k == 0 ? 1 : 0, 0, (int32_t)(2 * k + 1), 0, k});
@@ -530,7 +555,10 @@ double build_passes(int scheme, double tau, int64_t n, std::vector<PassSpec>& ou
   return tau / 2;
 }
 
-int factors_per_step(int scheme) { return base_scheme(scheme) == LS_STRANG ? 3 : 2; }
+int factors_per_step(int scheme) {
+  if (scheme == LS_YOSHIDA4) return 9;
+  return base_scheme(scheme) == LS_STRANG ? 3 : 2;
+}
 
 lsk::SamplerArgs sampler_args(ls_ctx* c, int scheme, int& npf) {
   lsk::SamplerArgs sa;
@@ -592,6 +620,7 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     const int L = q.layer - 1;
     const int64_t S = c->geom[L].nslices;
     const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
+    if (q.unit != 0) set_kinetic(c, q.unit);
     lsk::PassArgs a = base_args(c, L, psi);
     if (!stoch) {
       a.mode = lsk::MODE_STEP;
@@ -912,7 +941,7 @@ int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_
   if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
   if (n < 0) return fail(LS_ERR_INVALID, "nsteps < 0");
   if (!std::isfinite(tau)) return fail(LS_ERR_INVALID, "tau is not finite");
-  if (scheme < LS_LIE || scheme > LS_STRANG_STOCH) return fail(LS_ERR_INVALID, "unknown scheme");
+  if (scheme < LS_LIE || scheme > LS_YOSHIDA4) return fail(LS_ERR_INVALID, "unknown scheme");
   if (n == 0) return LS_OK;
   if (n > (1 << 26) / 8) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
   return guarded([&]() -> int {
@@ -1035,7 +1064,7 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
   if (!c) return fail(LS_ERR_STATE, "context is NULL");
   if (!psi || !lam || !gv1 || !gv2) return fail(LS_ERR_INVALID, "NULL argument");
   if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP)
-    return fail(LS_ERR_INVALID, "adjoint supports the deterministic schemes only");
+    return fail(LS_ERR_INVALID, "adjoint supports LIE, STRANG and STRANG_KP only");
   if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
@@ -1301,7 +1330,8 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
   if (!b) return fail(LS_ERR_STATE, "batch is NULL");
   if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
   if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
-  if (scheme < LS_LIE || scheme > LS_STRANG_STOCH) return fail(LS_ERR_INVALID, "unknown scheme");
+  if (scheme < LS_LIE || scheme > LS_STRANG_STOCH)
+    return fail(LS_ERR_INVALID, "the batched runner takes LIE, STRANG, STRANG_KP and the stochastic schemes");
   if (n == 0) return LS_OK;
   if (n > (int64_t)1 << 24) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
   const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;

@@ -166,6 +166,27 @@ def test_step_parity_strided_4096(P, scheme):
         O.use_fft(False)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_step_parity_yoshida4(P, dtype):
+    """Fourth-order composition: every pass carries its own kinetic unit (the
+    three sub-step durations are incommensurate); general, fast, pair and
+    64 x 64 passes."""
+    probs = problems_1d() + problems_2d() + problems_64x64_slices()[:1]
+    if dtype == "c64":
+        probs.append(problems_strided_4096()[0])
+    O.use_fft(True)
+    try:
+        for p in probs:
+            ctx = P.Context(p, dtype)
+            x = W.random_state((p.M2, p.M1), 14)
+            psi = ctx.from_dense(x)
+            ctx.step(psi, 3, 5e-3, "yoshida4")
+            ref = O.step(p, x, 5e-3, "yoshida4", 3)
+            assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 5, (p.name, rel(ctx.to_dense(psi), ref))
+    finally:
+        O.use_fft(False)
+
+
 def test_large_kinetic_phase_free_particle(P):
     """V = 0 at the 2049-box extremes: every element must be the exact phase
     exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
