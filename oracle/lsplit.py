@@ -37,12 +37,13 @@ import numpy as np
 __all__ = [
     "box_indices", "wavevectors", "kinetic_energy_diag", "index_mask", "mask_count",
     "dft_matrix", "grid_potential", "apply_K", "apply_P", "scheme_factors", "yoshida_weights", "step",
+    "toeplitz_potential", "apply_C",
     "splitmix64_next", "sample_slices", "observables", "gaussian_packet",
     "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient", "use_fft",
     "TRANSFORM", "sample_count", "expanded_factors",
 ]
 
-SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch", "yoshida4")
+SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch", "yoshida4", "cn_strang")
 MASK64 = (1 << 64) - 1
 
 
@@ -227,6 +228,8 @@ def scheme_factors(scheme: str, tau: float) -> List[Tuple]:
     strang_kp  : K(t/2) P2(t) P1(t) K(t/2)             (kinetic/potential Strang)
     yoshida4   : strang(w1 t) strang(w0 t) strang(w1 t)  (fourth order, see
                  yoshida_weights)
+    cn_strang  : C1(t/2) C2(t) C1(t/2), the Crank-Nicolson factors of Eq. (tsCN)
+                 (see apply_C)
     *_stoch    : same factor list, potential factors act on sampled slices."""
     base = scheme.replace("_stoch", "")
     t = tau
@@ -239,9 +242,50 @@ def scheme_factors(scheme: str, tau: float) -> List[Tuple]:
     if base == "yoshida4":
         w1, w0 = yoshida_weights()
         return strang(w1 * t) + strang(w0 * t) + strang(w1 * t)
+    if base == "cn_strang":
+        return [("C", 1, t / 2), ("C", 2, t), ("C", 1, t / 2)]
     if base == "strang_kp":
         return [("K", t / 2), ("P", 1, t), ("P", 2, t), ("K", t / 2)]
     raise ValueError(f"unknown scheme {scheme}")
+
+
+# --------------------------------------------------------------------------
+# Crank-Nicolson layer splitting (Sec. 4.2.1, Eq. (tsCN)); 1D boxes
+# --------------------------------------------------------------------------
+def toeplitz_potential(h, c, q: int) -> np.ndarray:
+    """The plane-wave matrix of a layer potential on its 1D index box (Sec. 3,
+    the matrices V^1, V^2 below Eq. (3.5)): V[m, m'] = vhat(m - m'), zero
+    where m - m' carries no coefficient; no wrap across the box ends."""
+    V = np.zeros((q, q), dtype=np.complex128)
+    for hh, cc in zip(np.asarray(h, dtype=np.int64).reshape(-1), c):
+        for m in range(q):
+            if 0 <= m - hh < q:
+                V[m, m - hh] += cc
+    return V
+
+
+def apply_C(prob, phi: np.ndarray, layer: int, s: float, _kin=None) -> np.ndarray:
+    """One Crank-Nicolson factor of duration s for H_j = D/2 + V^j (Eq. (tsCN)):
+    every slice x (fixed index of the other layer) becomes the solution y of
+    (I + i s A/2) y = (I - i s A/2) x, A = diag(|k|^2/4) + V^j the slice's block.
+    With s = tau/2 this is (4I + i tau H_1)^{-1} (4I - i tau H_1) of the first
+    and third lines of Eq. (tsCN); with s = tau, (2I + i tau H_2)^{-1}
+    (2I - i tau H_2) of the second.  Dense solves (np.linalg.solve)."""
+    if prob.d != 1:
+        raise ValueError("the Crank-Nicolson splitting is implemented for 1D boxes")
+    kin = kinetic_energy_diag(prob) if _kin is None else _kin
+    if layer == 1:
+        V = toeplitz_potential(prob.v1_h, prob.v1_c, prob.q1[0])
+        X, dk = phi, kin
+    else:
+        V = toeplitz_potential(prob.v2_h, prob.v2_c, prob.q2[0])
+        X, dk = phi.T, kin.T
+    eye = np.eye(X.shape[1])
+    out = np.empty_like(X)
+    for r in range(X.shape[0]):
+        A = np.diag(dk[r] / 2.0) + V
+        out[r] = np.linalg.solve(eye + 0.5j * s * A, (eye - 0.5j * s * A) @ X[r])
+    return out if layer == 1 else np.ascontiguousarray(out.T)
 
 
 # --------------------------------------------------------------------------
@@ -296,6 +340,9 @@ def expanded_factors(prob, scheme: str, tau: float, nsteps: int, seed: int = 0,
             if f[0] == "K":
                 out.append(("K", f[1]))
                 continue
+            if f[0] == "C":
+                out.append(f)
+                continue
             layer, s = f[1], f[2]
             if stoch:
                 S = prob.M2 if layer == 1 else prob.M1
@@ -325,6 +372,8 @@ def step(prob, phi: np.ndarray, tau: float, scheme: str = "strang", nsteps: int 
     for i, f in enumerate(fl):
         if f[0] == "K":
             phi = apply_K(prob, phi, f[1], kin)
+        elif f[0] == "C":
+            phi = apply_C(prob, phi, f[1], f[2], kin)
         else:
             phi = apply_P(prob, phi, f[1], f[2], f[3], v1 if f[1] == 1 else v2)
         if project and (i + 1) % per == 0:

@@ -27,6 +27,10 @@ PINS = [
     lambda: pins.test_convergence_order_against_dense_exponential("lie", 1),
     lambda: pins.test_convergence_order_against_dense_exponential("yoshida4", 4),
     pins.test_yoshida_weights_conditions,
+    pins.test_toeplitz_potential_matches_quadrature,
+    pins.test_cn_mass_conservation,
+    pins.test_cn_free_particle_cayley_phases,
+    pins.test_cn_second_order_against_dense_galerkin_exponential,
     pins.test_adjoint_matches_central_differences,
     pins.test_one_step_equals_dense_factor_product,
 ]
@@ -38,6 +42,8 @@ _orig_grid = L.grid_potential
 _orig_factors = L.scheme_factors
 _orig_P = L.apply_P
 _orig_yw = L.yoshida_weights
+_orig_toep = L.toeplitz_potential
+_orig_C = L.apply_C
 
 
 def _strang_wrong(scheme, tau):
@@ -69,6 +75,12 @@ MUTANTS = {
     "lie_wrong_order": ("scheme_factors", _lie_wrong_order),
     "yoshida_weights_swapped": ("yoshida_weights", lambda: _orig_yw()[::-1]),
     "yoshida_middle_forward": ("yoshida_weights", lambda: (_orig_yw()[0], -_orig_yw()[1])),
+    "toeplitz_transposed": ("toeplitz_potential", lambda h, c, q: _orig_toep(h, c, q).T),
+    "toeplitz_wrapped": ("toeplitz_potential", lambda h, c, q: _orig_toep(np.asarray(h) - q, c, q)
+                         + _orig_toep(h, c, q) + _orig_toep(np.asarray(h) + q, c, q)),
+    "cn_half_duration": ("apply_C", lambda p, phi, layer, s, _kin=None: _orig_C(p, phi, layer, s / 2, _kin)),
+    "cn_layer2_half": ("apply_C", lambda p, phi, layer, s, _kin=None:
+                       _orig_C(p, phi, layer, s / 2 if layer == 2 else s, _kin)),
 }
 
 

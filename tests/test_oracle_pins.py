@@ -80,9 +80,10 @@ def test_2d_separable_transform_equals_kronecker_matrix():
 
 
 # ---------------------------------------------------------------- closed forms
-@pytest.mark.parametrize("scheme", O.SCHEMES)
+@pytest.mark.parametrize("scheme", [s for s in O.SCHEMES if s != "cn_strang"])
 def test_free_particle_exact_phase(scheme):
-    """V = 0: every scheme is exact, phi(T) = exp(-i T |k|^2 / 2) phi0."""
+    """V = 0: every exponential scheme is exact, phi(T) = exp(-i T |k|^2 / 2)
+    phi0 (the Crank-Nicolson split has its own closed form, below)."""
     p = W.bilayer_1d(6, 5, 0.0, 0.0, ecut=1e9)
     phi0 = rand_state(p, 3)
     tau, n = 0.013, 7
@@ -514,3 +515,79 @@ def test_fft_backend_equals_dense_definition():
             O.use_fft(False)
         np.testing.assert_allclose(got, ref, atol=1e-13)
         assert abs(og["energy"] - ob["energy"]) < 1e-12
+
+
+# ---------------------------------------------------------------- Crank-Nicolson layer splitting
+def galerkin_by_quadrature(h, c, q, L=1.0, npts=256):
+    """V[m, m'] = (1/L) int_0^L v(x) e^{-i G_m x} e^{i G_m' x} dx with
+    v(x) = sum_h vhat_h e^{i 2 pi h x / L}, by the trapezoidal rule on npts
+    points (exact for these trigonometric polynomials): the plane-wave matrix of
+    Sec. 3 computed from the potential function, not from its index formula."""
+    x = np.arange(npts) * L / npts
+    v = np.zeros(npts, dtype=np.complex128)
+    for hh, cc in zip(np.asarray(h).reshape(-1), c):
+        v += cc * np.exp(2j * np.pi * hh * x / L)
+    G = 2 * np.pi * np.arange(q) / L
+    E = np.exp(1j * np.outer(G, x))              # e^{i G_m x}
+    return (E.conj() * v) @ E.T / npts
+
+
+def dense_H_1d_galerkin(prob):
+    m = np.arange(prob.q1[0]) + prob.lo1[0]
+    n = np.arange(prob.q2[0]) + prob.lo2[0]
+    k = prob.B1[0, 0] * m[None, :] + prob.B2[0, 0] * n[:, None]
+    D = np.diag(0.5 * (k ** 2).reshape(-1))
+    V1 = galerkin_by_quadrature(prob.v1_h, prob.v1_c, prob.q1[0])
+    V2 = galerkin_by_quadrature(prob.v2_h, prob.v2_c, prob.q2[0])
+    return D + np.kron(np.eye(prob.q2[0]), V1) + np.kron(V2, np.eye(prob.q1[0]))
+
+
+def test_toeplitz_potential_matches_quadrature():
+    """Orientation and values of the plane-wave potential matrix, with complex
+    (non-symmetric) coefficients so that a transposition would show."""
+    h = np.array([[1], [-1], [2], [-2], [0]])
+    c = np.array([0.3 + 0.2j, 0.3 - 0.2j, -0.1j, 0.1j, 0.25])
+    for q in (1, 2, 5, 9):
+        np.testing.assert_allclose(O.lsplit.toeplitz_potential(h, c, q), galerkin_by_quadrature(h, c, q), atol=1e-13)
+
+
+def test_cn_mass_conservation():
+    """Theorem 4.4 (mass conservation of Eq. (tsCN)): every factor is a
+    Cayley transform of a Hermitian block, so the norm is kept to rounding."""
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 21)
+    y = O.step(p, x, 0.05, "cn_strang", 20)
+    assert abs(np.linalg.norm(y) - np.linalg.norm(x)) < 1e-13
+
+
+def test_cn_free_particle_cayley_phases():
+    """V = 0: each element is multiplied per step by C(tau/2) C(tau) C(tau/2)
+    with C(s) = (1 - i s kin/4) / (1 + i s kin/4) (H_j = D/2, kin = |k|^2/2)."""
+    p = W.bilayer_1d(8, 6, 0.0, 0.0, ecut=1e9)
+    x = rand_state(p, 22)
+    tau, n = 0.03, 4
+    kin = O.kinetic_energy_diag(p)
+    C = lambda s: (1 - 0.25j * s * kin) / (1 + 0.25j * s * kin)
+    np.testing.assert_allclose(O.step(p, x, tau, "cn_strang", n), x * (C(tau / 2) ** 2 * C(tau)) ** n, atol=1e-13)
+
+
+def test_cn_second_order_against_dense_galerkin_exponential():
+    """Theorem 4.3 (second order of Eq. (tsCN)) against exp(-i T H) with the
+    plane-wave potential matrices built by quadrature."""
+    p = small_1d()
+    H = dense_H_1d_galerkin(p)
+    phi0 = rand_state(p, 9)
+    T = 0.2
+    exact = (expm_herm(H, T) @ phi0.reshape(-1)).reshape(phi0.shape)
+    ns = [16, 32, 64, 128]
+    err = _errors(p, "cn_strang", T, ns, phi0, exact)
+    slope = np.polyfit(np.log([T / n for n in ns]), np.log(err), 1)[0]
+    assert abs(slope - 2) < 0.1, (slope, err)
+    assert err[-1] < 1e-3
+
+
+def test_cn_time_reversible():
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 23)
+    y = O.step(p, O.step(p, x, 0.02, "cn_strang", 4), -0.02, "cn_strang", 4)
+    np.testing.assert_allclose(y, x, atol=1e-13)
