@@ -269,7 +269,7 @@ def run_suite(args):
 
     p = W.config_scale_1d()
     for scheme, n in (("strang_stoch", 20), ("lie_stoch", 20), ("strang_kp", 20), ("lie", 20), ("strang", 20),
-                      ("yoshida4", 20)):
+                      ("yoshida4", 20), ("cn_strang", 20)):
         c = P.Context(p, "c64")
         psi = c.empty()
         c.init_gaussian(psi, [0.0], 2.0, [1.0])

@@ -64,8 +64,17 @@ enum { LS_C64 = 0, LS_C128 = 1 };
  *                   w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3) w1 (the higher-order
  *                   splittings of Sec. 4.2 and Appendix A, by Yoshida's symmetric
  *                   composition); ls_step only (not the batched runner or
- *                   ls_adjoint, which return LS_ERR_INVALID). */
-enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_STOCH = 4, LS_YOSHIDA4 = 5 };
+ *                   ls_adjoint, which return LS_ERR_INVALID).
+ *   LS_CN_STRANG    Crank-Nicolson layer splitting (Sec. 4.2.1, Eq. (tsCN)):
+ *                   C1(tau/2) C2(tau) C1(tau/2), C_j(s) = (I + i s H_j/2)^{-1}
+ *                   (I - i s H_j/2), H_j = D/2 + V^j with V^j the plane-wave
+ *                   potential matrix of Sec. 3 (no wrap at the box ends).  Second
+ *                   order and mass conserving.  1D boxes, potentials with
+ *                   |h| <= 8 and |tau| sum_{h != 0} |vhat_h| < 1 (each factor is
+ *                   solved by Jacobi sweeps to working precision); otherwise
+ *                   ls_step returns LS_ERR_INVALID.  ls_step only. */
+enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_STOCH = 4, LS_YOSHIDA4 = 5,
+       LS_CN_STRANG = 6 };
 
 /* Problem description (Sec. 2-3).  All arrays are read during ls_create only
  * and stay owned by the caller.

@@ -579,9 +579,96 @@ lsk::SamplerArgs sampler_args(ls_ctx* c, int scheme, int& npf) {
   return sa;
 }
 
+// Arguments of a Crank-Nicolson layer factor of duration s (Eq. (tsCN)):
+// potential band, Jacobi sweep count from the diagonal-dominance ratio, tile
+// shape.  Returns LS_OK or LS_ERR_INVALID with a message.
+int cn_args(ls_ctx* c, int layer, double s, void* psi, lsk::CnArgs& a) {
+  std::memset(&a, 0, sizeof(a));
+  if (c->d != 1) return fail(LS_ERR_INVALID, "the Crank-Nicolson scheme takes 1D boxes");
+  const ls_problem& p = c->p;
+  const int L = layer - 1;
+  // the context's own copies of the coefficients (the caller's arrays are
+  // read during ls_create only)
+  const int32_t nv = L == 0 ? p.nv1 : p.nv2;
+  const int32_t* vh = L == 0 ? c->h1.data() : c->h2.data();
+  const double* vc = L == 0 ? c->c1.data() : c->c2.data();
+  int hb = 0;
+  for (int32_t t = 0; t < nv; ++t) {
+    const int h = vh[t];
+    if (h < -lsk::kCnMaxBand || h > lsk::kCnMaxBand)
+      return fail(LS_ERR_INVALID, "the Crank-Nicolson scheme takes potentials with |h| <= 8");
+    a.v_re[h + lsk::kCnMaxBand] += vc[2 * t];
+    a.v_im[h + lsk::kCnMaxBand] += vc[2 * t + 1];
+    hb = std::max(hb, std::abs(h));
+  }
+  const lsk::LayerGeom& g = c->geom[L];
+  const double hs = 0.5 * s;
+  double off = 0;
+  for (int h = -hb; h <= hb; ++h)
+    if (h != 0) off += std::hypot(a.v_re[h + lsk::kCnMaxBand], a.v_im[h + lsk::kCnMaxBand]);
+  const double amin = 1.0 - std::fabs(hs * a.v_im[lsk::kCnMaxBand]);
+  const double rho = amin > 0 ? std::fabs(hs) * off / amin : 1.0;
+  if (!(rho < 0.5)) return fail(LS_ERR_INVALID, "time step too large for the Crank-Nicolson solver (needs |tau| sum|vhat_h| < 1)");
+  const double eps = c->dtype == LS_C64 ? std::ldexp(1.0, -25) : std::ldexp(1.0, -54);
+  const int niter = (rho == 0 || hb == 0) ? 0 : std::min(48, (int)std::ceil(std::log(eps) / std::log(rho)));
+  a.psi = psi;
+  a.nslices = g.nslices;
+  a.slice_stride = g.slice_stride;
+  a.ea = g.ea;
+  a.q = g.qa;
+  a.strided = L == 1 ? 1 : 0;
+  a.hb = hb;
+  a.niter = niter;
+  a.halo = hb * (niter + 1);
+  a.half_s = hs;
+  a.b_own = L == 0 ? p.B1[0] : p.B2[0];
+  a.b_oth = L == 0 ? p.B2[0] : p.B1[0];
+  a.lo = L == 0 ? p.lo1[0] : p.lo2[0];
+  a.olo = L == 0 ? p.lo2[0] : p.lo1[0];
+  auto split = [](double x, float* out) {
+    out[0] = (float)x;
+    out[1] = (float)(x - (double)out[0]);
+  };
+  split(hs * 0.25 * a.b_own * a.b_own, a.za);
+  split(hs * 0.5 * a.b_own * a.b_oth, a.zb);
+  split(hs * 0.25 * a.b_oth * a.b_oth, a.zc);
+  split(hs * a.v_re[lsk::kCnMaxBand], a.zd);
+  const int cap = 256 * lsk::kCnPerThread;
+  if (a.strided) {
+    int W = 32;
+    while (W > 1 && cap / W - 2 * a.halo < 8) W /= 2;
+    a.W = W;
+    a.TI = std::min<int>(cap / W - 2 * a.halo, a.q);
+  } else {
+    a.W = 1;
+    a.TI = std::min(a.q, cap - 2 * a.halo);
+  }
+  if (a.TI < 1) return fail(LS_ERR_INVALID, "Crank-Nicolson halo wider than a tile");
+  a.nchunks = (a.q + a.TI - 1) / a.TI;
+  return LS_OK;
+}
+
 // Enqueue the whole call on stream st (used both for capture and direct runs).
 void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaStream_t st,
                   DevBuf* lists) {
+  if (scheme == LS_CN_STRANG) {
+    // C1(tau/2) C2(tau) C1(tau/2) per step (Eq. (tsCN)); arguments checked by ls_step
+    lsk::CnArgs a1, a2;
+    if (cn_args(c, 1, tau / 2, psi, a1) != LS_OK || cn_args(c, 2, tau, psi, a2) != LS_OK)
+      throw CudaError{cudaErrorInvalidValue, "Crank-Nicolson arguments"};
+    for (int64_t k = 0; k < n; ++k) {
+      if (c->dtype == LS_C64) {
+        LS_CUDA(lsk::launch_cn<float>(a1, st));
+        LS_CUDA(lsk::launch_cn<float>(a2, st));
+        LS_CUDA(lsk::launch_cn<float>(a1, st));
+      } else {
+        LS_CUDA(lsk::launch_cn<double>(a1, st));
+        LS_CUDA(lsk::launch_cn<double>(a2, st));
+        LS_CUDA(lsk::launch_cn<double>(a1, st));
+      }
+    }
+    return;
+  }
   std::vector<PassSpec> ps;
   int32_t end_time = 0;
   const double u = build_passes(scheme, tau, n, ps, end_time);
@@ -676,6 +763,7 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
 }
 
 void prepare_tables(ls_ctx* c, int64_t n, double tau, int scheme) {
+  if (scheme == LS_CN_STRANG) return;  // no tables
   std::vector<PassSpec> ps;
   int32_t end_time = 0;
   build_passes(scheme, tau, std::min<int64_t>(n, 2), ps, end_time);
@@ -817,6 +905,8 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     else LS_CUDA(lsk::pass_prepare<double>(block_max));
     if (c->dtype == LS_C64) LS_CUDA(lsk::fast_prepare<float>(block_max));
     else LS_CUDA(lsk::fast_prepare<double>(block_max));
+    if (c->dtype == LS_C64) LS_CUDA(lsk::cn_prepare<float>(block_max));
+    else LS_CUDA(lsk::cn_prepare<double>(block_max));
     if (c->dtype == LS_C64) LS_CUDA(lsk::fast2d_prepare<float>(block_max));
     else LS_CUDA(lsk::fast2d_prepare<double>(block_max));
     for (int L = 0; L < 2; ++L) {
@@ -941,8 +1031,14 @@ int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_
   if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
   if (n < 0) return fail(LS_ERR_INVALID, "nsteps < 0");
   if (!std::isfinite(tau)) return fail(LS_ERR_INVALID, "tau is not finite");
-  if (scheme < LS_LIE || scheme > LS_YOSHIDA4) return fail(LS_ERR_INVALID, "unknown scheme");
+  if (scheme < LS_LIE || scheme > LS_CN_STRANG) return fail(LS_ERR_INVALID, "unknown scheme");
   if (n == 0) return LS_OK;
+  if (scheme == LS_CN_STRANG) {
+    lsk::CnArgs a;
+    int rc = cn_args(c, 1, tau / 2, psi, a);
+    if (rc == LS_OK) rc = cn_args(c, 2, tau, psi, a);
+    if (rc != LS_OK) return rc;
+  }
   if (n > (1 << 26) / 8) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);

@@ -178,6 +178,32 @@ template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthrea
 template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int minb,
                                                    int* blocks_per_sm);
 
+// Crank-Nicolson layer factor (Sec. 4.2.1, Eq. (tsCN)) over every slice of
+// one layer of a 1D box: (I + i s A/2) y = (I - i s A/2) x, A = diag(|k|^2/4)
+// + the banded plane-wave potential matrix (half-width hb), by niter Jacobi
+// sweeps on tiles of W slices x (TI + 2 halo) indices.
+constexpr int kCnMaxBand = 8;
+constexpr int kCnPerThread = 10;      // tile elements per thread (256 threads)
+struct CnArgs {
+  void* psi;
+  int64_t nslices;                    // slices of the layer
+  int64_t slice_stride, ea;           // element (slice, i) at slice * slice_stride + i * ea
+  int64_t nchunks;                    // index chunks per slice group
+  int32_t q;                          // slice length
+  int32_t strided;                    // 1: the W slices of a tile are adjacent in memory
+  int32_t W, TI, halo, hb, niter;
+  double half_s;                      // s / 2
+  double b_own, b_oth;                // k = b_own (lo + i) + b_oth (olo + slice)
+  int32_t lo, olo;
+  // z = (s/2)(|k|^2/4 + Re vhat_0) = za m^2 + zb m n + zc n^2 + zd with
+  // m = lo + i, n = olo + slice; each coefficient split into float hi + lo
+  float za[2], zb[2], zc[2], zd[2];
+  double v_re[2 * kCnMaxBand + 1], v_im[2 * kCnMaxBand + 1];  // vhat_h at h + kCnMaxBand
+};
+template <typename Real> cudaError_t launch_cn(const CnArgs& a, cudaStream_t st);
+template <typename Real> cudaError_t cn_prepare(size_t max_smem);
+size_t cn_smem_bytes(const CnArgs& a, size_t elem_bytes);
+
 // Message returned by ls_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -187,6 +187,68 @@ def test_step_parity_yoshida4(P, dtype):
         O.use_fft(False)
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_step_parity_cn_strang(P, dtype):
+    """Crank-Nicolson layer splitting (Eq. (tsCN)): Jacobi-swept banded
+    factors against the oracle's dense per-slice solves; potentials with one,
+    two and three harmonics, odd and even lengths, rows and columns on tiles."""
+    for p in problems_1d():
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 15)
+        psi = ctx.from_dense(x)
+        ctx.step(psi, 3, 5e-3, "cn_strang")
+        ref = O.step(p, x, 5e-3, "cn_strang", 3)
+        assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, (p.name, rel(ctx.to_dense(psi), ref))
+
+
+def test_cn_strang_full_size_properties(P):
+    """2049 x 2049: the factors are Cayley transforms, so the norm is kept and
+    C(-s) C(s) = I makes 10 steps back undo 10 steps forward."""
+    import torch
+    p = W.config_scale_1d()
+    ctx = P.Context(p, "c64")
+    psi = ctx.from_dense(W.random_state((p.M2, p.M1), 16))
+    x = psi.clone()
+    n0 = float(torch.linalg.vector_norm(x))
+    ctx.step(psi, 10, 5e-4, "cn_strang")
+    moved = float(torch.linalg.vector_norm(psi - x)) / n0
+    assert abs(float(torch.linalg.vector_norm(psi)) / n0 - 1) < 1e-5
+    ctx.step(psi, 10, -5e-4, "cn_strang")
+    assert moved > 0.1
+    assert float(torch.linalg.vector_norm(psi - x)) / n0 < 1e-5
+
+
+def test_cn_strang_1000_steps(P):
+    """The accuracy gate of the FP32 path over a long run, for the
+    Crank-Nicolson splitting: rel-L2 <= 1e-4 after 1000 steps and
+    | ||psi|| - 1 | <= 1e-5 (65 x 65 box, random state)."""
+    p = W.config_small_1d()
+    ctx = P.Context(p, "c64")
+    x = W.random_state((p.M2, p.M1), 3)
+    psi = ctx.from_dense(x)
+    ctx.step(psi, 1000, 1e-3, "cn_strang")
+    ref = O.step(p, x, 1e-3, "cn_strang", 1000)
+    got = ctx.to_dense(psi)
+    assert rel(got, ref) < 1e-4
+    assert abs(np.linalg.norm(got) / np.linalg.norm(x) - 1) < 1e-5
+
+
+def test_cn_strang_rejects_unsupported(P):
+    p2 = W.twisted_2d(q=8, hmax=2)
+    ctx = P.Context(p2, "c64")
+    with pytest.raises(P.LsplitError) as e:
+        ctx.step(ctx.empty(), 1, 1e-3, "cn_strang")
+    assert e.value.code == P.LS_ERR_INVALID
+    p = W.config_small_1d()
+    ctx = P.Context(p, "c64")
+    with pytest.raises(P.LsplitError):
+        ctx.step(ctx.empty(), 1, 10.0, "cn_strang")        # tau sum |vhat| >= 1
+    wide = p.with_potentials(v1_h=[[9], [-9]], v1_c=[0.1, 0.1])
+    ctx = P.Context(wide, "c64")
+    with pytest.raises(P.LsplitError):
+        ctx.step(ctx.empty(), 1, 1e-3, "cn_strang")        # band wider than 8
+
+
 def test_large_kinetic_phase_free_particle(P):
     """V = 0 at the 2049-box extremes: every element must be the exact phase
     exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
