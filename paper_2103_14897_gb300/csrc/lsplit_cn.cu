@@ -150,12 +150,16 @@ __global__ void __launch_bounds__(256) cn_pass_kernel(const CnArgs a) {
     nxt[-1 - e] = z;
     nxt[span + e] = z;
   }
-  const int64_t grp = blockIdx.x / a.nchunks, ch = blockIdx.x - grp * a.nchunks;
-  const int64_t s0 = grp * W;
-  const int i0 = (int)(ch * a.TI) - a.halo;
+  // 32-bit index arithmetic (a 64-bit division runs on the FP64 pipe)
+  const unsigned nch = (unsigned)a.nchunks;
+  const unsigned grp = blockIdx.x / nch, ch = blockIdx.x - grp * nch;
+  const int64_t s0 = (int64_t)grp * W;
+  const int i0 = (int)(ch * (unsigned)a.TI) - a.halo;
   C* psi = reinterpret_cast<C*>(a.psi);
-  const Real hs = (Real)a.half_s;
-  const bool unitary = a.v_im[kCnMaxBand] == 0.0;
+  Real hs;
+  if constexpr (sizeof(Real) == 4) hs = a.half_s_f;
+  else hs = a.half_s;
+  const bool unitary = a.unitary != 0;
 
   C xk[KE];
 #pragma unroll

@@ -633,6 +633,8 @@ int cn_args(ls_ctx* c, int layer, double s, void* psi, lsk::CnArgs& a) {
   split(hs * 0.5 * a.b_own * a.b_oth, a.zb);
   split(hs * 0.25 * a.b_oth * a.b_oth, a.zc);
   split(hs * a.v_re[lsk::kCnMaxBand], a.zd);
+  a.half_s_f = (float)hs;
+  a.unitary = a.v_im[lsk::kCnMaxBand] == 0.0 ? 1 : 0;
   const int cap = 256 * lsk::kCnPerThread;
   if (a.strided) {
     int W = 32;

@@ -198,6 +198,8 @@ struct CnArgs {
   // z = (s/2)(|k|^2/4 + Re vhat_0) = za m^2 + zb m n + zc n^2 + zd with
   // m = lo + i, n = olo + slice; each coefficient split into float hi + lo
   float za[2], zb[2], zc[2], zd[2];
+  float half_s_f;                     // s / 2 in single precision
+  int32_t unitary;                    // 1: vhat_0 real (the diagonal multiplier has modulus 1)
   double v_re[2 * kCnMaxBand + 1], v_im[2 * kCnMaxBand + 1];  // vhat_h at h + kCnMaxBand
 };
 template <typename Real> cudaError_t launch_cn(const CnArgs& a, cudaStream_t st);
