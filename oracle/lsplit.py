@@ -37,13 +37,14 @@ import numpy as np
 __all__ = [
     "box_indices", "wavevectors", "kinetic_energy_diag", "index_mask", "mask_count",
     "dft_matrix", "grid_potential", "apply_K", "apply_P", "scheme_factors", "yoshida_weights", "step",
-    "toeplitz_potential", "apply_C",
+    "toeplitz_potential", "apply_C", "apply_semi_implicit",
     "splitmix64_next", "sample_slices", "observables", "gaussian_packet",
     "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient", "use_fft",
     "TRANSFORM", "sample_count", "expanded_factors",
 ]
 
-SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch", "yoshida4", "cn_strang")
+SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch", "yoshida4", "cn_strang",
+           "semi_implicit", "random_batch")
 MASK64 = (1 << 64) - 1
 
 
@@ -230,6 +231,8 @@ def scheme_factors(scheme: str, tau: float) -> List[Tuple]:
                  yoshida_weights)
     cn_strang  : C1(t/2) C2(t) C1(t/2), the Crank-Nicolson factors of Eq. (tsCN)
                  (see apply_C)
+    semi_implicit, random_batch : one explicit-potential / implicit-kinetic
+                 step (Algorithms 1 and 4, see apply_semi_implicit)
     *_stoch    : same factor list, potential factors act on sampled slices."""
     base = scheme.replace("_stoch", "")
     t = tau
@@ -244,6 +247,8 @@ def scheme_factors(scheme: str, tau: float) -> List[Tuple]:
         return strang(w1 * t) + strang(w0 * t) + strang(w1 * t)
     if base == "cn_strang":
         return [("C", 1, t / 2), ("C", 2, t), ("C", 1, t / 2)]
+    if base in ("semi_implicit", "random_batch"):
+        return [("S", t)]
     if base == "strang_kp":
         return [("K", t / 2), ("P", 1, t), ("P", 2, t), ("K", t / 2)]
     raise ValueError(f"unknown scheme {scheme}")
@@ -286,6 +291,34 @@ def apply_C(prob, phi: np.ndarray, layer: int, s: float, _kin=None) -> np.ndarra
         A = np.diag(dk[r] / 2.0) + V
         out[r] = np.linalg.solve(eye + 0.5j * s * A, (eye - 0.5j * s * A) @ X[r])
     return out if layer == 1 else np.ascontiguousarray(out.T)
+
+
+# --------------------------------------------------------------------------
+# Semi-implicit step and its random batch form (Sec. 4.1 Algorithm 1,
+# Sec. 4.3 Algorithm 4); 1D boxes
+# --------------------------------------------------------------------------
+def apply_semi_implicit(prob, phi: np.ndarray, tau: float, rows=None, cols=None, _kin=None) -> np.ndarray:
+    """phi <- (I + i tau D)^{-1} (phi - Psi_1 - Psi_2), Psi_1 = i tau V^1 phi
+    slice by slice along m (every row n), Psi_2 = i tau V^2 phi along n (every
+    column m); V^j the plane-wave potential matrices (Algorithm 1).
+    rows / cols given (Algorithm 4): Psi_1 only on the rows n in rows, scaled by
+    M2 / len(rows); Psi_2 only on the columns m in cols, scaled by M1 / len(cols)."""
+    if prob.d != 1:
+        raise ValueError("the semi-implicit step is implemented for 1D boxes")
+    kin = kinetic_energy_diag(prob) if _kin is None else _kin
+    V1 = toeplitz_potential(prob.v1_h, prob.v1_c, prob.q1[0])
+    V2 = toeplitz_potential(prob.v2_h, prob.v2_c, prob.q2[0])
+    psi1 = 1j * tau * (phi @ V1.T)            # row n: V1 @ phi[n, :]
+    psi2 = 1j * tau * (V2 @ phi)              # column m: V2 @ phi[:, m]
+    if rows is not None:
+        w = np.zeros(prob.M2)
+        w[np.asarray(rows)] = prob.M2 / len(rows)
+        psi1 = psi1 * w[:, None]
+    if cols is not None:
+        w = np.zeros(prob.M1)
+        w[np.asarray(cols)] = prob.M1 / len(cols)
+        psi2 = psi2 * w[None, :]
+    return (phi - psi1 - psi2) / (1.0 + 1j * tau * kin)
 
 
 # --------------------------------------------------------------------------
@@ -343,6 +376,14 @@ def expanded_factors(prob, scheme: str, tau: float, nsteps: int, seed: int = 0,
             if f[0] == "C":
                 out.append(f)
                 continue
+            if f[0] == "S":
+                rows = cols = None
+                if scheme == "random_batch":
+                    g = (step0 + k) * 2
+                    rows = sample_slices(prob.M2, sample_count(prob.M2, frac_den), seed, g)
+                    cols = sample_slices(prob.M1, sample_count(prob.M1, frac_den), seed, g + 1)
+                out.append(("S", f[1], rows, cols))
+                continue
             layer, s = f[1], f[2]
             if stoch:
                 S = prob.M2 if layer == 1 else prob.M1
@@ -374,6 +415,8 @@ def step(prob, phi: np.ndarray, tau: float, scheme: str = "strang", nsteps: int 
             phi = apply_K(prob, phi, f[1], kin)
         elif f[0] == "C":
             phi = apply_C(prob, phi, f[1], f[2], kin)
+        elif f[0] == "S":
+            phi = apply_semi_implicit(prob, phi, f[1], f[2], f[3], kin)
         else:
             phi = apply_P(prob, phi, f[1], f[2], f[3], v1 if f[1] == 1 else v2)
         if project and (i + 1) % per == 0:

@@ -31,6 +31,9 @@ PINS = [
     pins.test_cn_mass_conservation,
     pins.test_cn_free_particle_cayley_phases,
     pins.test_cn_second_order_against_dense_galerkin_exponential,
+    pins.test_semi_implicit_step_matches_dense_formula,
+    pins.test_semi_implicit_free_particle_closed_form,
+    pins.test_random_batch_is_unbiased,
     pins.test_adjoint_matches_central_differences,
     pins.test_one_step_equals_dense_factor_product,
 ]
@@ -44,6 +47,7 @@ _orig_P = L.apply_P
 _orig_yw = L.yoshida_weights
 _orig_toep = L.toeplitz_potential
 _orig_C = L.apply_C
+_orig_SI = L.apply_semi_implicit
 
 
 def _strang_wrong(scheme, tau):
@@ -79,6 +83,10 @@ MUTANTS = {
     "toeplitz_wrapped": ("toeplitz_potential", lambda h, c, q: _orig_toep(np.asarray(h) - q, c, q)
                          + _orig_toep(h, c, q) + _orig_toep(np.asarray(h) + q, c, q)),
     "cn_half_duration": ("apply_C", lambda p, phi, layer, s, _kin=None: _orig_C(p, phi, layer, s / 2, _kin)),
+    "semi_implicit_no_kinetic_solve": ("apply_semi_implicit", lambda p, phi, tau, rows=None, cols=None, _kin=None:
+                                       _orig_SI(p, phi, tau, rows, cols, _kin) * (1 + 1j * tau * L.kinetic_energy_diag(p))),
+    "random_batch_ignores_sample": ("apply_semi_implicit", lambda p, phi, tau, rows=None, cols=None, _kin=None:
+                                    _orig_SI(p, phi, tau, None, None, _kin)),
     "cn_layer2_half": ("apply_C", lambda p, phi, layer, s, _kin=None:
                        _orig_C(p, phi, layer, s / 2 if layer == 2 else s, _kin)),
 }
