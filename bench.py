@@ -269,15 +269,17 @@ def run_suite(args):
 
     p = W.config_scale_1d()
     for scheme, n in (("strang_stoch", 20), ("lie_stoch", 20), ("strang_kp", 20), ("lie", 20), ("strang", 20),
-                      ("yoshida4", 20), ("cn_strang", 20)):
+                      ("yoshida4", 20), ("cn_strang", 20), ("semi_implicit", 20), ("random_batch", 20)):
         c = P.Context(p, "c64")
         psi = c.empty()
         c.init_gaussian(psi, [0.0], 2.0, [1.0])
         t = _timed(lambda: c.step(psi, n, TAU, scheme, seed=7))
-        npass = {"yoshida4": 9, "strang_kp": 2, "lie": 2, "lie_stoch": 2}.get(scheme, 3)
+        npass = {"yoshida4": 9, "strang_kp": 2, "lie": 2, "lie_stoch": 2, "semi_implicit": 1,
+                 "random_batch": 1}.get(scheme, 3)
         line(f"bilayer1d-2049x2049 {scheme} c64 tau=5e-4", p.dof, n, t,
              {"norm_minus_1": c.observables(psi)["norm"] - 1,
-              "hbm_frac_algorithmic": (16 * p.dof * npass * n / t / 1e9) / hbm if not scheme.endswith("stoch") else None})
+              "hbm_frac_algorithmic": (16 * p.dof * npass * n / t / 1e9) / hbm
+              if not scheme.endswith("stoch") and scheme != "random_batch" else None})
 
     p = W.twisted_2d(q=64)
     c = P.Context(p, "c64")

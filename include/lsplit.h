@@ -72,9 +72,20 @@ enum { LS_C64 = 0, LS_C128 = 1 };
  *                   order and mass conserving.  1D boxes, potentials with
  *                   |h| <= 8 and |tau| sum_{h != 0} |vhat_h| < 1 (each factor is
  *                   solved by Jacobi sweeps to working precision); otherwise
- *                   ls_step returns LS_ERR_INVALID.  ls_step only. */
+ *                   ls_step returns LS_ERR_INVALID.  ls_step only.
+ *   LS_SEMI_IMPLICIT  phi <- (I + i tau D)^{-1} (phi - i tau (V^1 + V^2) phi)
+ *                   (Sec. 4.1, Algorithm 1): explicit banded plane-wave potential
+ *                   products along both layers, implicit kinetic part.  First
+ *                   order; does not conserve the mass.
+ *   LS_RANDOM_BATCH Algorithm 4 (Sec. 4.3): as LS_SEMI_IMPLICIT, but the V^1
+ *                   product acts on p1 = max(1, M2/frac_den) seeded rows and the
+ *                   V^2 product on p2 = max(1, M1/frac_den) seeded columns,
+ *                   weighted M2/p1 and M1/p2 (samples: the LS_*_STOCH rule with
+ *                   two sub-steps per step, rows first).
+ *                   Both: 1D boxes, potentials with |h| <= 8, ls_step only; the
+ *                   context allocates a second state array on first use. */
 enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_STOCH = 4, LS_YOSHIDA4 = 5,
-       LS_CN_STRANG = 6 };
+       LS_CN_STRANG = 6, LS_SEMI_IMPLICIT = 7, LS_RANDOM_BATCH = 8 };
 
 /* Problem description (Sec. 2-3).  All arrays are read during ls_create only
  * and stay owned by the caller.

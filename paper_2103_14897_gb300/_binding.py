@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblsplit.so")
 
 LS_OK, LS_ERR_INVALID, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT, LS_ERR_STATE = 0, -1, -2, -3, -4, -5
 LS_C64, LS_C128 = 0, 1
-SCHEMES = {"lie": 0, "strang": 1, "strang_kp": 2, "lie_stoch": 3, "strang_stoch": 4, "yoshida4": 5, "cn_strang": 6}
+SCHEMES = {"lie": 0, "strang": 1, "strang_kp": 2, "lie_stoch": 3, "strang_stoch": 4, "yoshida4": 5, "cn_strang": 6,
+           "semi_implicit": 7, "random_batch": 8}
 
 # Every entry point declared in include/lsplit.h.
 EXPORTS = ["ls_last_error", "ls_create", "ls_destroy", "ls_layout", "ls_index_set",

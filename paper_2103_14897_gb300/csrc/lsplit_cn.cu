@@ -247,6 +247,118 @@ __global__ void __launch_bounds__(256) cn_pass_kernel(const CnArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- semi-implicit step
+// One CTA: a column tile of 256 consecutive m by kSiRows consecutive rows n;
+// thread t owns column m0 + t.  Neighbours come through the read-only cache
+// (the step is out of place).  Row / column weights of the random batch form
+// are looked up once per CTA by binary search in the sorted sample lists.
+constexpr int kSiRows = 4;
+
+__device__ __forceinline__ bool si_member(const int32_t* list, int32_t n, int32_t v) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int32_t x = __ldg(list + mid);
+    if (x == v) return true;
+    if (x < v) lo = mid + 1;
+    else hi = mid - 1;
+  }
+  return false;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) si_kernel(const SiArgs a) {
+  using C = typename CT<Real>::C;
+  __shared__ C s_v1[2 * kCnMaxBand + 1], s_v2[2 * kCnMaxBand + 1];
+  __shared__ Real s_wr[kSiRows];
+  const int t = threadIdx.x;
+  if (t < 2 * kCnMaxBand + 1) {
+    s_v1[t].x = (Real)a.v1_re[t];
+    s_v1[t].y = (Real)a.v1_im[t];
+    s_v2[t].x = (Real)a.v2_re[t];
+    s_v2[t].y = (Real)a.v2_im[t];
+  }
+  const int64_t m = (int64_t)blockIdx.x * 256 + t;
+  const int64_t n0 = (int64_t)blockIdx.y * kSiRows;
+  if (t < kSiRows) {
+    Real w = 1;
+    if (a.rows) w = (n0 + t < a.M2 && si_member(a.rows, a.nrows, (int32_t)(n0 + t))) ? (Real)a.w_row : (Real)0;
+    s_wr[t] = w;
+  }
+  __syncthreads();
+  if (m >= a.M1) return;
+  Real wc = 1;
+  if (a.cols) wc = si_member(a.cols, a.ncols, (int32_t)m) ? (Real)a.w_col : (Real)0;
+  const C* src = reinterpret_cast<const C*>(a.src);
+  C* dst = reinterpret_cast<C*>(a.dst);
+  Real tau;
+  if constexpr (sizeof(Real) == 4) tau = a.tau_f;
+  else tau = a.tau;
+  const int32_t mi = a.lo1 + (int32_t)m;
+  for (int r = 0; r < kSiRows; ++r) {
+    const int64_t n = n0 + r;
+    if (n >= a.M2) break;
+    const C* row = src + n * a.pitch;
+    // s1 = sum_h vhat1_h x[n][m - h], s2 = sum_h vhat2_h x[n - h][m]
+    C s1, s2;
+    s1.x = s1.y = 0;
+    s2.x = s2.y = 0;
+    for (int h = -a.hb1; h <= a.hb1; ++h) {
+      const int64_t mm = m - h;
+      if (mm < 0 || mm >= a.M1) continue;
+      const C x = __ldg(row + mm), v = s_v1[h + kCnMaxBand];
+      s1.x += v.x * x.x - v.y * x.y;
+      s1.y += v.x * x.y + v.y * x.x;
+    }
+    for (int h = -a.hb2; h <= a.hb2; ++h) {
+      const int64_t nn = n - h;
+      if (nn < 0 || nn >= a.M2) continue;
+      const C x = __ldg(src + nn * a.pitch + m), v = s_v2[h + kCnMaxBand];
+      s2.x += v.x * x.x - v.y * x.y;
+      s2.y += v.x * x.y + v.y * x.x;
+    }
+    const Real wr = s_wr[r];
+    C acc;
+    acc.x = wr * s1.x + wc * s2.x;
+    acc.y = wr * s1.y + wc * s2.y;
+    const C x = __ldg(row + m);
+    // num = x - i tau acc
+    C num;
+    num.x = x.x + tau * acc.y;
+    num.y = x.y - tau * acc.x;
+    // z = tau |k|^2 / 2; dst = num (1 - i z) / (1 + z^2)
+    Real z, zlo;
+    if constexpr (sizeof(Real) == 4) {
+      CnArgs q;
+      q.za[0] = a.za[0]; q.za[1] = a.za[1];
+      q.zb[0] = a.zb[0]; q.zb[1] = a.zb[1];
+      q.zc[0] = a.zc[0]; q.zc[1] = a.zc[1];
+      q.zd[0] = 0.0f; q.zd[1] = 0.0f;
+      cn_z<float>(q, mi, a.lo2 + (int32_t)n, z, zlo);
+    } else {
+      const double md = (double)mi, nd = (double)(a.lo2 + n);
+      z = a.zad * md * md + a.zbd * md * nd + a.zcd * nd * nd;
+      zlo = 0;
+    }
+    (void)zlo;
+    const Real rr = (Real)1 / ((Real)1 + z * z);
+    C y;
+    y.x = (num.x + z * num.y) * rr;
+    y.y = (num.y - z * num.x) * rr;
+    dst[n * a.pitch + m] = y;
+  }
+}
+
+template <typename Real> cudaError_t launch_si(const SiArgs& a, cudaStream_t st) {
+  if (a.hb1 > kCnMaxBand || a.hb2 > kCnMaxBand) return cudaErrorInvalidValue;
+  if (a.M1 <= 0 || a.M2 <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((a.M1 + 255) / 256), (unsigned)((a.M2 + kSiRows - 1) / kSiRows));
+  si_kernel<Real><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+template cudaError_t launch_si<float>(const SiArgs&, cudaStream_t);
+template cudaError_t launch_si<double>(const SiArgs&, cudaStream_t);
+
 size_t cn_smem_bytes(const CnArgs& a, size_t elem_bytes) {
   // two tile buffers, each with kCnMaxBand * W zero entries on both sides
   return 2 * ((size_t)a.W * (size_t)(a.TI + 2 * a.halo) + 2 * (size_t)kCnMaxBand * a.W) * elem_bytes;

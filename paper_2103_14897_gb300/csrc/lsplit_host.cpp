@@ -176,6 +176,7 @@ struct ls_ctx {
   std::map<std::pair<int, uint64_t>, ConvTab> ctab;                   // convolution-form tables
   bool conv_form[2] = {false, false};
   DevBuf partials, result, touch_row, touch_col, seedbuf, grad[2];
+  DevBuf scratch;   // second state array of the out-of-place semi-implicit step (allocated on first use)
   int nblk_elem = 0;
   size_t partial_count = 0;
   std::list<std::unique_ptr<GraphEntry>> graphs;
@@ -650,9 +651,82 @@ int cn_args(ls_ctx* c, int layer, double s, void* psi, lsk::CnArgs& a) {
   return LS_OK;
 }
 
+// Arguments of the semi-implicit step (Algorithms 1 and 4): potential bands
+// and coefficients of both layers, the kinetic quadratic form times tau.
+int si_args(ls_ctx* c, double tau, lsk::SiArgs& a) {
+  std::memset(&a, 0, sizeof(a));
+  if (c->d != 1) return fail(LS_ERR_INVALID, "the semi-implicit and random batch schemes take 1D boxes");
+  const ls_problem& p = c->p;
+  for (int L = 0; L < 2; ++L) {
+    const int32_t nv = L == 0 ? p.nv1 : p.nv2;
+    const int32_t* vh = L == 0 ? c->h1.data() : c->h2.data();
+    const double* vc = L == 0 ? c->c1.data() : c->c2.data();
+    double* re = L == 0 ? a.v1_re : a.v2_re;
+    double* im = L == 0 ? a.v1_im : a.v2_im;
+    int hb = 0;
+    for (int32_t t = 0; t < nv; ++t) {
+      const int h = vh[t];
+      if (h < -lsk::kCnMaxBand || h > lsk::kCnMaxBand)
+        return fail(LS_ERR_INVALID, "the semi-implicit and random batch schemes take potentials with |h| <= 8");
+      re[h + lsk::kCnMaxBand] += vc[2 * t];
+      im[h + lsk::kCnMaxBand] += vc[2 * t + 1];
+      hb = std::max(hb, std::abs(h));
+    }
+    (L == 0 ? a.hb1 : a.hb2) = hb;
+  }
+  a.M1 = c->M1;
+  a.M2 = c->M2;
+  a.pitch = c->pitch;
+  a.lo1 = p.lo1[0];
+  a.lo2 = p.lo2[0];
+  a.tau = tau;
+  a.tau_f = (float)tau;
+  const double b1 = p.B1[0], b2 = p.B2[0];
+  a.zad = tau * 0.5 * b1 * b1;
+  a.zbd = tau * b1 * b2;
+  a.zcd = tau * 0.5 * b2 * b2;
+  auto split = [](double x, float* out) {
+    out[0] = (float)x;
+    out[1] = (float)(x - (double)out[0]);
+  };
+  split(a.zad, a.za);
+  split(a.zbd, a.zb);
+  split(a.zcd, a.zc);
+  return LS_OK;
+}
+
 // Enqueue the whole call on stream st (used both for capture and direct runs).
 void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaStream_t st,
                   DevBuf* lists) {
+  if (scheme == LS_SEMI_IMPLICIT || scheme == LS_RANDOM_BATCH) {
+    // out of place, alternating between psi and the scratch array
+    lsk::SiArgs a;
+    if (si_args(c, tau, a) != LS_OK) throw CudaError{cudaErrorInvalidValue, "semi-implicit arguments"};
+    int npf = 0;
+    lsk::SamplerArgs sa = sampler_args(c, scheme, npf);
+    const bool rb = scheme == LS_RANDOM_BATCH;
+    if (rb) LS_CUDA(lsk::launch_sampler(sa, (const uint64_t*)c->seedbuf.p, (int32_t)(n * npf), (int32_t*)lists->p, st));
+    void* bufs[2] = {psi, c->scratch.p};
+    for (int64_t k = 0; k < n; ++k) {
+      a.src = bufs[k & 1];
+      a.dst = bufs[(k + 1) & 1];
+      if (rb) {
+        // factor 0 of step k: rows (layer-1 slices), factor 1: columns
+        a.rows = (const int32_t*)lists->p + (k * npf + 0) * sa.pmax;
+        a.cols = (const int32_t*)lists->p + (k * npf + 1) * sa.pmax;
+        a.nrows = sa.p1;
+        a.ncols = sa.p2;
+        a.w_row = (double)sa.S1 / sa.p1;
+        a.w_col = (double)sa.S2 / sa.p2;
+      }
+      if (c->dtype == LS_C64) LS_CUDA(lsk::launch_si<float>(a, st));
+      else LS_CUDA(lsk::launch_si<double>(a, st));
+    }
+    if (n & 1)  // the last step wrote the scratch array: copy the M1 columns of every row back
+      LS_CUDA(cudaMemcpy2DAsync(psi, c->pitch * c->esize, c->scratch.p, c->pitch * c->esize, c->M1 * c->esize,
+                                c->M2, cudaMemcpyDeviceToDevice, st));
+    return;
+  }
   if (scheme == LS_CN_STRANG) {
     // C1(tau/2) C2(tau) C1(tau/2) per step (Eq. (tsCN)); arguments checked by ls_step
     lsk::CnArgs a1, a2;
@@ -766,6 +840,14 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
 
 void prepare_tables(ls_ctx* c, int64_t n, double tau, int scheme) {
   if (scheme == LS_CN_STRANG) return;  // no tables
+  if (scheme == LS_SEMI_IMPLICIT || scheme == LS_RANDOM_BATCH) {
+    // the second state array, zeroed once so its pitch padding stays zero
+    if (!c->scratch.p) {
+      c->scratch.alloc((size_t)c->pitch * c->M2 * c->esize);
+      LS_CUDA(cudaMemset(c->scratch.p, 0, (size_t)c->pitch * c->M2 * c->esize));
+    }
+    return;
+  }
   std::vector<PassSpec> ps;
   int32_t end_time = 0;
   build_passes(scheme, tau, std::min<int64_t>(n, 2), ps, end_time);
@@ -1033,8 +1115,13 @@ int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_
   if (!psi) return fail(LS_ERR_INVALID, "psi is NULL");
   if (n < 0) return fail(LS_ERR_INVALID, "nsteps < 0");
   if (!std::isfinite(tau)) return fail(LS_ERR_INVALID, "tau is not finite");
-  if (scheme < LS_LIE || scheme > LS_CN_STRANG) return fail(LS_ERR_INVALID, "unknown scheme");
+  if (scheme < LS_LIE || scheme > LS_RANDOM_BATCH) return fail(LS_ERR_INVALID, "unknown scheme");
   if (n == 0) return LS_OK;
+  if (scheme == LS_SEMI_IMPLICIT || scheme == LS_RANDOM_BATCH) {
+    lsk::SiArgs a;
+    int rc = si_args(c, tau, a);
+    if (rc != LS_OK) return rc;
+  }
   if (scheme == LS_CN_STRANG) {
     lsk::CnArgs a;
     int rc = cn_args(c, 1, tau / 2, psi, a);
@@ -1044,7 +1131,7 @@ int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_
   if (n > (1 << 26) / 8) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
-    const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+    const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH || scheme == LS_RANDOM_BATCH;
     if (stoch) {
       const uint64_t hp[2] = {seed, step0 * (uint64_t)factors_per_step(scheme)};
       // pageable source: staged before the call returns, safe to reuse

@@ -206,6 +206,31 @@ template <typename Real> cudaError_t launch_cn(const CnArgs& a, cudaStream_t st)
 template <typename Real> cudaError_t cn_prepare(size_t max_smem);
 size_t cn_smem_bytes(const CnArgs& a, size_t elem_bytes);
 
+// Semi-implicit step (Sec. 4.1, Algorithm 1) and its random batch form
+// (Sec. 4.3, Algorithm 4) on a 1D box, out of place:
+//   dst = (I + i tau D)^{-1} (src - i tau (w_row V^1 + w_col V^2) src),
+// V^j the banded plane-wave potential matrices along m (rows) and n (columns);
+// w_row / w_col: 1 (Algorithm 1), or weight on the sampled rows / columns and
+// 0 elsewhere (Algorithm 4).
+struct SiArgs {
+  const void* src;
+  void* dst;
+  int64_t M1, M2, pitch;
+  int32_t hb1, hb2;                   // band half-widths of V^1, V^2
+  int32_t lo1, lo2;
+  double tau;
+  float tau_f;
+  float za[2], zb[2], zc[2];          // tau |k|^2 / 2 = za m^2 + zb m n + zc n^2 (float hi + lo)
+  double zad, zbd, zcd;               // the same coefficients in double
+  double v1_re[2 * kCnMaxBand + 1], v1_im[2 * kCnMaxBand + 1];
+  double v2_re[2 * kCnMaxBand + 1], v2_im[2 * kCnMaxBand + 1];
+  const int32_t* rows;                // sorted sampled rows (NULL: every row, weight 1)
+  const int32_t* cols;                // sorted sampled columns (NULL: every column, weight 1)
+  int32_t nrows, ncols;
+  double w_row, w_col;                // weights of sampled rows / columns
+};
+template <typename Real> cudaError_t launch_si(const SiArgs& a, cudaStream_t st);
+
 // Message returned by ls_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -249,6 +249,26 @@ def test_cn_strang_rejects_unsupported(P):
         ctx.step(ctx.empty(), 1, 1e-3, "cn_strang")        # band wider than 8
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("scheme", ["semi_implicit", "random_batch"])
+def test_step_parity_semi_implicit(P, dtype, scheme):
+    """Algorithms 1 and 4: out-of-place stencil steps (odd and even step
+    counts, so that both the copy back and the plain ping-pong end are
+    covered), sampled rows and columns bit-identical to the oracle's."""
+    for p in problems_1d():
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 17)
+        for n in (3, 4):
+            psi = ctx.from_dense(x)
+            ctx.step(psi, n, 2e-3, scheme, seed=7, step0=2)
+            ref = O.step(p, x, 2e-3, scheme, n, seed=7, step0=2)
+            assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 3, (p.name, n, rel(ctx.to_dense(psi), ref))
+            assert np.all(psi[:, p.M1:].cpu().numpy() == 0)   # padding untouched
+    with pytest.raises(P.LsplitError):
+        c2 = P.Context(W.twisted_2d(q=8, hmax=2), dtype)
+        c2.step(c2.empty(), 1, 1e-3, scheme)
+
+
 def test_large_kinetic_phase_free_particle(P):
     """V = 0 at the 2049-box extremes: every element must be the exact phase
     exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
