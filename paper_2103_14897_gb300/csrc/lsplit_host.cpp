@@ -1646,13 +1646,46 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
         scum[ninst] = acc;
         ba.settle_items = acc;
       }
+      // deterministic Strang: adjacent layer-1 factors of consecutive steps
+      // become one item (a fused tile, or the two factors back to back)
+      const bool fused = !stoch && scheme == LS_STRANG && !getenv_flag("LSPLIT_NO_FUSE");
+      std::vector<int64_t> t1(ninst), t2(ninst);
+      if (fused) {
+        std::vector<lsk::PassArgs> fa((size_t)5 * ninst);
+        for (int i = 0; i < ninst; ++i) {
+          const lsk::PassArgs& l1 = args[(size_t)0 * ninst + i];
+          const lsk::PassArgs& l2 = args[(size_t)1 * ninst + i];
+          auto with = [](lsk::PassArgs a, int64_t pre, int64_t post) {
+            a.units_pre = pre;
+            a.units_post = post;
+            return a;
+          };
+          fa[(size_t)0 * ninst + i] = with(l1, 1, 3);
+          fa[(size_t)1 * ninst + i] = with(l2, 0, 3);
+          lsk::PassArgs f = with(l1, 0, 2);
+          if (l1.fast_logn && l1.Khat) {
+            f.units_post = 3;
+            f.Khat2 = l1.Khat;      // the second factor has the same duration tau/2
+            f.fix2_re = l1.fix0_re;
+            f.fix2_im = l1.fix0_im;
+            f.units_mid = 2;
+          }
+          fa[(size_t)2 * ninst + i] = f;
+          fa[(size_t)3 * ninst + i] = with(l1, 0, 1);
+          fa[(size_t)4 * ninst + i] = with(l1, 0, 3);
+          t1[i] = cum[(size_t)0 * (ninst + 1) + i + 1] - cum[(size_t)0 * (ninst + 1) + i];
+          t2[i] = cum[(size_t)1 * (ninst + 1) + i + 1] - cum[(size_t)1 * (ninst + 1) + i];
+        }
+        args.swap(fa);
+      }
       e->args = std::make_shared<DevBuf>();
       const size_t b_args = args.size() * sizeof(lsk::PassArgs), b_cum = cum.size() * sizeof(int64_t);
       const size_t b_ts = tsteps.size() * sizeof(int64_t), b_sargs = sargs.size() * sizeof(lsk::PassArgs);
       const size_t b_scum = scum.size() * sizeof(int64_t);
       const size_t b_si = sS.size() * sizeof(int32_t), b_sl = sBase.size() * sizeof(int64_t);
       const size_t b_so = sOff.size() * sizeof(int64_t);
-      const size_t total_b = b_args + b_cum + b_ts + b_sargs + b_scum + 2 * b_si + 2 * b_sl + b_so;
+      const size_t b_t12 = (size_t)ninst * sizeof(int64_t);
+      const size_t total_b = b_args + b_cum + b_ts + b_sargs + b_scum + 2 * b_si + 2 * b_sl + b_so + 2 * b_t12;
       e->args->alloc(total_b);
       char* base = static_cast<char*>(e->args->p);
       size_t o = 0;
@@ -1667,6 +1700,9 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       ba.cum = static_cast<const int64_t*>(put(cum.data(), b_cum));
       ba.tiles_step = static_cast<const int64_t*>(put(tsteps.data(), b_ts));
       ba.settle_cum = static_cast<const int64_t*>(put(scum.data(), b_scum));
+      ba.tiles1 = static_cast<const int64_t*>(put(t1.data(), b_t12));
+      ba.tiles2 = static_cast<const int64_t*>(put(t2.data(), b_t12));
+      ba.fused = fused ? 1 : 0;
       lsk::BatchSamplerArgs sa;
       sa.base = static_cast<const int64_t*>(put(sBase.data(), b_sl));
       sa.step_len = static_cast<const int64_t*>(put(sStep.data(), b_sl));

@@ -157,6 +157,14 @@ struct BatchArgs {
   const int64_t* settle_cum;    // [ninst + 1]
   int64_t settle_items;
   int32_t minb;                 // register budget variant (2 or 3 CTAs per SM)
+  // deterministic Strang with fused layer-1 factors (fused != 0): passes of a
+  // call are [first L1] then per step [L2, fused L1 (plain L1 in the last
+  // step)]; args kinds [5][ninst]: 0 first L1, 1 L2, 2 fused L1 (fused tile
+  // when Khat2 is set, else its first factor), 3 last L1, 4 second factor of
+  // a fused item without a fused tile; cum rows 0 (layer 1) and 1 (layer 2)
+  int32_t fused;
+  const int64_t* tiles1;        // [ninst] layer-1 tiles of instance i
+  const int64_t* tiles2;        // [ninst] layer-2 tiles of instance i
 };
 
 // Slice samples of a batch: block b draws instance i = b / (nsteps * npf),

@@ -1633,9 +1633,9 @@ template <typename Real> int fast_max_threads() { return 256; }
 // Tiles of the batched runner as calls, not inlined into the persistent loop:
 // each tile body then gets the kernel's whole register budget, and the loop
 // keeps only its few scalars across the call.
-template <typename Real, int LOGN, int MODE>
+template <typename Real, int LOGN, int MODE, bool FUSED = false>
 __device__ __noinline__ void batch_fast_tile_n(const PassArgs& a, int64_t tile, unsigned char* smraw) {
-  fast_tile<Real, LOGN, MODE, 1, false, true>(a, tile, smraw);
+  fast_tile<Real, LOGN, MODE, 1, FUSED, true>(a, tile, smraw);
 }
 template <typename Real, int BPT, int MODE>
 __device__ __noinline__ void batch_general_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
@@ -1647,6 +1647,15 @@ __device__ __noinline__ void batch_general_tile(const PassArgs& a, int64_t tile,
 template <typename Real, int MODE>
 __device__ __forceinline__ bool batch_fast_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   if constexpr (sizeof(Real) == 4) {
+    if (MODE == MODE_STEP && a.Khat2 != nullptr) {
+      // two layer-1 factors of consecutive Strang steps (convolution form)
+      switch (a.fast_logn) {
+        case 9: batch_fast_tile_n<Real, 9, MODE, true>(a, tile, smraw); return true;
+        case 10: batch_fast_tile_n<Real, 10, MODE, true>(a, tile, smraw); return true;
+        case 11: batch_fast_tile_n<Real, 11, MODE, true>(a, tile, smraw); return true;
+        default: return false;
+      }
+    }
     switch (a.fast_logn) {
       case 9: batch_fast_tile_n<Real, 9, MODE>(a, tile, smraw); return true;
       case 10: batch_fast_tile_n<Real, 10, MODE>(a, tile, smraw); return true;
@@ -1665,7 +1674,9 @@ batch_kernel(const BatchArgs b) {
   __shared__ long long s_item;
   __shared__ int s_stop, s_inst, s_pass;
   __shared__ long long s_tile;
-  const long long steps_total = b.step_items * (long long)b.nsteps;
+  // fused Strang: [first L1] then per step [L2, fused L1 (last step: plain L1)]
+  const long long steps_total = b.fused ? b.pass_items[0] + (long long)b.nsteps * (b.pass_items[0] + b.pass_items[1])
+                                        : b.step_items * (long long)b.nsteps;
   const long long total = steps_total + (b.stoch ? b.settle_items : 0);
   volatile int32_t* status = b.status;
   volatile unsigned long long* done = b.counters + 1;
@@ -1714,6 +1725,38 @@ batch_kernel(const BatchArgs b) {
           s_pass = 0;
           s_tile = r - b.settle_cum[i];
           need = (unsigned long long)((long long)b.nsteps * b.tiles_step[i]);
+        } else if (b.fused) {
+          const long long I1 = s_pass_items[0], I2 = s_pass_items[1];
+          long long r = s_item, nl1 = 0, nl2 = 0;
+          int kind = 0, layer = 0;
+          if (r >= I1) {
+            r -= I1;
+            const long long k = r / (I1 + I2);
+            r -= k * (I1 + I2);
+            if (r < I2) {
+              kind = 1;
+              layer = 1;
+              nl1 = k + 1;
+              nl2 = k;
+            } else {
+              r -= I2;
+              kind = k == b.nsteps - 1 ? 3 : 2;
+              nl1 = k + 1;
+              nl2 = k + 1;
+            }
+          }
+          const int64_t* cum = b.cum + (size_t)layer * (b.ninst + 1);
+          int lo = 0, hi = b.ninst - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cum[mid] <= r) lo = mid; else hi = mid - 1;
+          }
+          i = lo;
+          s_inst = i;
+          s_pass = kind;
+          s_tile = r - cum[i];
+          need = (unsigned long long)(nl1 * b.tiles1[i] + nl2 * b.tiles2[i]);
+          if (b.unmet && i == 0 && kind == 1 && nl2 == 0) need += 1;  // test hook
         } else {
           const long long k = s_item / b.step_items;
           long long r = s_item - k * b.step_items;
@@ -1765,7 +1808,7 @@ batch_kernel(const BatchArgs b) {
       int* dst = reinterpret_cast<int*>(&s_args);
       for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / 4); w += blockDim.x) dst[w] = src[w];
       __syncthreads();
-      if (threadIdx.x == 0 && !s_settle) {
+      if (threadIdx.x == 0 && !s_settle && !b.fused) {
         const long long k = s_item / b.step_items;
         if (b.stoch) {
           s_args.list += k * s_args.list_step;
@@ -1785,6 +1828,18 @@ batch_kernel(const BatchArgs b) {
     } else {
       if (!batch_fast_tile<Real, MODE_STEP>(s_args, s_tile, smraw))
         batch_general_tile<Real, BPT, MODE_STEP>(s_args, s_tile, smraw);
+      if (b.fused && s_pass == 2 && s_args.Khat2 == nullptr) {
+        // fused item without a fused tile body: the second factor on the same
+        // slices, after the first is complete in this CTA
+        __threadfence();
+        __syncthreads();
+        const int* src = reinterpret_cast<const int*>(b.args + (size_t)4 * b.ninst + s_inst);
+        int* dst = reinterpret_cast<int*>(&s_args);
+        for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / 4); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        if (!batch_fast_tile<Real, MODE_STEP>(s_args, s_tile, smraw))
+          batch_general_tile<Real, BPT, MODE_STEP>(s_args, s_tile, smraw);
+      }
     }
     __threadfence();
     __syncthreads();
