@@ -37,7 +37,7 @@ import numpy as np
 __all__ = [
     "box_indices", "wavevectors", "kinetic_energy_diag", "index_mask", "mask_count",
     "dft_matrix", "grid_potential", "apply_K", "apply_P", "scheme_factors", "yoshida_weights", "step",
-    "toeplitz_potential", "apply_C", "apply_semi_implicit",
+    "toeplitz_potential", "apply_C", "apply_semi_implicit", "density_on_line",
     "splitmix64_next", "sample_slices", "observables", "gaussian_packet",
     "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient", "use_fft",
     "TRANSFORM", "sample_count", "expanded_factors",
@@ -319,6 +319,24 @@ def apply_semi_implicit(prob, phi: np.ndarray, tau: float, rows=None, cols=None,
         w[np.asarray(cols)] = prob.M1 / len(cols)
         psi2 = psi2 * w[None, :]
     return (phi - psi1 - psi2) / (1.0 + 1j * tau * kin)
+
+
+# --------------------------------------------------------------------------
+# Real-space wave function on a line (Sec. 3 expansion; the localisation
+# plots of Sec. 5)
+# --------------------------------------------------------------------------
+def density_on_line(prob, phi: np.ndarray, x: Sequence[float]) -> np.ndarray:
+    """psi(x_j) = sum_{m,n} phi[n, m] exp(i k_mn x_j) for a 1D box, the
+    plane-wave expansion of the wave function (Sec. 3), evaluated point by
+    point; the phase k x is formed in FP64 from k of wavevectors()."""
+    if prob.d != 1:
+        raise ValueError("density_on_line: 1D boxes")
+    k = wavevectors(prob)[..., 0]
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    out = np.empty(len(x), dtype=np.complex128)
+    for j, xj in enumerate(x):
+        out[j] = np.sum(phi * np.exp(1j * k * xj))
+    return out
 
 
 # --------------------------------------------------------------------------

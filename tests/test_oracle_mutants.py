@@ -34,6 +34,8 @@ PINS = [
     pins.test_semi_implicit_step_matches_dense_formula,
     pins.test_semi_implicit_free_particle_closed_form,
     pins.test_random_batch_is_unbiased,
+    pins.test_density_single_plane_wave,
+    pins.test_density_periodic_for_commensurate_layers,
     pins.test_adjoint_matches_central_differences,
     pins.test_one_step_equals_dense_factor_product,
 ]
@@ -48,6 +50,8 @@ _orig_yw = L.yoshida_weights
 _orig_toep = L.toeplitz_potential
 _orig_C = L.apply_C
 _orig_SI = L.apply_semi_implicit
+_orig_dens = L.density_on_line
+_orig_wv = L.wavevectors
 
 
 def _strang_wrong(scheme, tau):
@@ -83,6 +87,8 @@ MUTANTS = {
     "toeplitz_wrapped": ("toeplitz_potential", lambda h, c, q: _orig_toep(np.asarray(h) - q, c, q)
                          + _orig_toep(h, c, q) + _orig_toep(np.asarray(h) + q, c, q)),
     "cn_half_duration": ("apply_C", lambda p, phi, layer, s, _kin=None: _orig_C(p, phi, layer, s / 2, _kin)),
+    "density_conjugate_phase": ("density_on_line", lambda p, phi, x: np.conj(_orig_dens(p, np.conj(phi), x))),
+    "density_wrong_wavevector": ("wavevectors", lambda p: _orig_wv(p) * 1.0001),
     "semi_implicit_no_kinetic_solve": ("apply_semi_implicit", lambda p, phi, tau, rows=None, cols=None, _kin=None:
                                        _orig_SI(p, phi, tau, rows, cols, _kin) * (1 + 1j * tau * L.kinetic_energy_diag(p))),
     "random_batch_ignores_sample": ("apply_semi_implicit", lambda p, phi, tau, rows=None, cols=None, _kin=None:

@@ -662,3 +662,33 @@ def test_random_batch_is_unbiased():
     spread = np.linalg.norm(one - ref)
     assert spread > 1e-3                       # a single draw differs
     assert np.linalg.norm(mean - ref) < 5 * spread / np.sqrt(n)
+
+
+# ---------------------------------------------------------------- real-space wave function on a line
+def test_density_single_plane_wave():
+    """One coefficient: psi(x) = phi_mn exp(i (B1 m + B2 n) x) exactly."""
+    p = W.bilayer_1d(5, 4, 1.0, 1.0, ecut=1e9)
+    phi = np.zeros((p.M2, p.M1), dtype=np.complex128)
+    phi[1, 7] = 0.3 - 0.4j
+    m, n = 7 + p.lo1[0], 1 + p.lo2[0]
+    x = np.array([-3.7, 0.0, 0.25, 11.0])
+    k = p.B1[0, 0] * m + p.B2[0, 0] * n
+    np.testing.assert_allclose(O.lsplit.density_on_line(p, phi, x), (0.3 - 0.4j) * np.exp(1j * k * x), atol=1e-13)
+
+
+def test_density_real_for_conjugate_symmetric_state():
+    """phi(-m, -n) = conj(phi(m, n)) (a real wave function) gives a real psi(x)."""
+    p = W.bilayer_1d(5, 4, 1.0, 1.0, ecut=1e9)
+    a = rand_state(p, 41)
+    phi = 0.5 * (a + np.conj(a[::-1, ::-1]))       # the boxes are symmetric about 0
+    vals = O.lsplit.density_on_line(p, phi, np.linspace(-5, 5, 17))
+    assert np.abs(vals.imag).max() < 1e-12 * np.abs(vals).max()
+
+
+def test_density_periodic_for_commensurate_layers():
+    """L2 = 2 L1 / 3: every k_mn is a multiple of 2 pi / (2 L1), so psi has
+    period 2 L1."""
+    p = W.bilayer_1d(4, 3, 1.0, 1.0, L1=1.0, L2=2.0 / 3.0, ecut=1e9)
+    phi = rand_state(p, 42)
+    x = np.array([0.1, 0.37, 1.3])
+    np.testing.assert_allclose(O.lsplit.density_on_line(p, phi, x + 2.0), O.lsplit.density_on_line(p, phi, x), atol=1e-11)
