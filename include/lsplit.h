@@ -178,6 +178,17 @@ int ls_step(ls_ctx* ctx, void* psi_dev, int64_t nsteps, double tau, int32_t sche
 int ls_observables(ls_ctx* ctx, const void* psi_dev, const void* chi_dev, ls_obs* out,
                    void* stream);
 
+/* Wave function on a real-space line from the plane-wave expansion (Sec. 3;
+ * the localisation plots of Sec. 5), 1D boxes:
+ *   psi(x_j) = sum_{m,n} phi[n][m] exp(i (B1 m + B2 n) x_j),  j < nx.
+ * x_host: nx doubles; out_host: 2 nx doubles (re, im per point).  The phases
+ * are exact (64-bit fixed-point turns); the sum over m runs in the context's
+ * precision, the sum over n in FP64.  Allocates temporary device buffers of
+ * about nx (M1 + 2 M2) complex elements and synchronises the stream.
+ * LS_ERR_INVALID for 2D boxes or nx beyond 2^22. */
+int ls_density(ls_ctx* ctx, const void* psi_dev, const double* x_host, int64_t nx, double* out_host,
+               void* stream);
+
 /* Slice samples of the stochastic variant (Algorithm 4) as drawn on the device:
  * for sub-steps g0 .. g0+count-1 of the given layer (1 or 2) writes count * p
  * sorted slice indices to out_host (int32), p = max(1, S/frac_den).

@@ -24,7 +24,7 @@ SCHEMES = {"lie": 0, "strang": 1, "strang_kp": 2, "lie_stoch": 3, "strang_stoch"
 
 # Every entry point declared in include/lsplit.h.
 EXPORTS = ["ls_last_error", "ls_create", "ls_destroy", "ls_layout", "ls_index_set",
-           "ls_init_gaussian", "ls_step", "ls_observables", "ls_samples", "ls_adjoint",
+           "ls_init_gaussian", "ls_step", "ls_observables", "ls_density", "ls_samples", "ls_adjoint",
            "ls_mass_noalloc", "ls_batch_create", "ls_batch_destroy", "ls_batch_layout",
            "ls_batch_init_gaussian", "ls_batch_step", "ls_batch_observables", "ls_batch_debug"]
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.ls_destroy.argtypes = [vp]
     lib.ls_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
     lib.ls_index_set.argtypes = [vp, C.POINTER(C.c_uint8), C.POINTER(i64)]
+    lib.ls_density.argtypes = [vp, vp, C.POINTER(C.c_double), i64, C.POINTER(C.c_double), vp]
     lib.ls_init_gaussian.argtypes = [vp, vp, C.POINTER(dbl), dbl, C.POINTER(dbl), vp]
     lib.ls_step.argtypes = [vp, vp, i64, dbl, i32, u64, u64, vp]
     lib.ls_observables.argtypes = [vp, vp, vp, C.POINTER(LsObs), vp]
@@ -215,6 +216,14 @@ class Context:
              step0: int = 0, stream=None):
         _check(_lib.ls_step(self._h, _ptr(psi), int(nsteps), float(tau), SCHEMES[scheme],
                             int(seed) & (2 ** 64 - 1), int(step0), _stream_handle(stream)))
+
+    def density(self, psi, x, stream=None) -> np.ndarray:
+        """psi(x_j) on real-space points x (1D boxes), complex128 array."""
+        xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+        out = np.zeros(2 * len(xs), dtype=np.float64)
+        _check(_lib.ls_density(self._h, _ptr(psi), xs.ctypes.data_as(C.POINTER(C.c_double)), len(xs),
+                               out.ctypes.data_as(C.POINTER(C.c_double)), _stream_handle(stream)))
+        return out[0::2] + 1j * out[1::2]
 
     def observables(self, psi, chi=None, stream=None) -> dict:
         o = LsObs()

@@ -1216,6 +1216,49 @@ int ls_observables(ls_ctx* c, const void* psi, const void* chi, ls_obs* out, voi
   });
 }
 
+int ls_density(ls_ctx* c, const void* psi, const double* x, int64_t nx, double* out, void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (!psi || (nx > 0 && (!x || !out))) return fail(LS_ERR_INVALID, "NULL argument");
+  if (c->d != 1) return fail(LS_ERR_INVALID, "ls_density takes 1D boxes");
+  if (nx < 0 || nx > ((int64_t)1 << 22)) return fail(LS_ERR_INVALID, "nx must be in [0, 2^22]");
+  if (nx == 0) return LS_OK;
+  return guarded([&]() -> int {
+    cudaStream_t st = S(stream);
+    std::vector<uint64_t> f((size_t)2 * nx);
+    for (int64_t j = 0; j < nx; ++j) {
+      if (!std::isfinite(x[j])) return fail(LS_ERR_INVALID, "x is not finite");
+      f[(size_t)j] = to_fixed(c->p.B1[0] * x[j] / (2.0 * kPi));
+      f[(size_t)(nx + j)] = to_fixed(c->p.B2[0] * x[j] / (2.0 * kPi));
+    }
+    DevBuf fb, e1, e2, t, ob;
+    fb.alloc(f.size() * sizeof(uint64_t));
+    e1.alloc((size_t)nx * c->M1 * c->esize);
+    e2.alloc((size_t)nx * c->M2 * c->esize);
+    t.alloc((size_t)nx * c->M2 * c->esize);
+    ob.alloc((size_t)2 * nx * sizeof(double));
+    LS_CUDA(cudaMemcpyAsync(fb.p, f.data(), f.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    lsk::DensityArgs d;
+    d.psi = psi;
+    d.M1 = c->M1;
+    d.M2 = c->M2;
+    d.pitch = c->pitch;
+    d.nx = nx;
+    d.lo1 = c->p.lo1[0];
+    d.lo2 = c->p.lo2[0];
+    d.f1 = static_cast<const uint64_t*>(fb.p);
+    d.f2 = static_cast<const uint64_t*>(fb.p) + nx;
+    d.e1 = e1.p;
+    d.e2 = e2.p;
+    d.t = t.p;
+    d.out = static_cast<double*>(ob.p);
+    if (c->dtype == LS_C64) LS_CUDA(lsk::launch_density<float>(d, st));
+    else LS_CUDA(lsk::launch_density<double>(d, st));
+    LS_CUDA(cudaMemcpyAsync(out, ob.p, (size_t)2 * nx * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaStreamSynchronize(st));
+    return LS_OK;
+  });
+}
+
 int ls_samples(ls_ctx* c, int32_t layer, uint64_t seed, uint64_t g0, int32_t count, int32_t* out,
                int32_t* p_out, void* stream) {
   if (!c) return fail(LS_ERR_STATE, "context is NULL");

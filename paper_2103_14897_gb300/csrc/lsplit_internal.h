@@ -239,6 +239,20 @@ struct SiArgs {
 };
 template <typename Real> cudaError_t launch_si(const SiArgs& a, cudaStream_t st);
 
+// Wave function on a real-space line (1D boxes): device buffers of the
+// phase tables E1 (nx x M1), E2 (nx x M2), the partial sums T (nx x M2) and
+// the output (2 nx doubles); f1/f2: B x_j / 2 pi as 64-bit fractions per point.
+struct DensityArgs {
+  const void* psi;
+  int64_t M1, M2, pitch, nx;
+  int32_t lo1, lo2;
+  const uint64_t* f1;
+  const uint64_t* f2;
+  void *e1, *e2, *t;
+  double* out;
+};
+template <typename Real> cudaError_t launch_density(const DensityArgs& d, cudaStream_t st);
+
 // Message returned by ls_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -269,6 +269,32 @@ def test_step_parity_semi_implicit(P, dtype, scheme):
         c2.step(c2.empty(), 1, 1e-3, scheme)
 
 
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
+def test_density_on_line_parity(P, dtype, tol):
+    """psi(x) on a line from the plane-wave expansion: exact fixed-point phase
+    tables, tiled contraction over m, FP64 sum over n; small boxes with many
+    points (several 64 x 64 tiles and ragged edges) and the 2049 x 2049 box
+    at a few points, including large |x|."""
+    x = np.concatenate([np.linspace(-20.0, 20.0, 301), [1234.5, -987.25]])
+    for p in [W.config_small_1d(), W.bilayer_1d(256, 12, 1.0, 1.4, ecut=1e9), problems_1d()[4]]:
+        ctx = P.Context(p, dtype)
+        phi = W.random_state((p.M2, p.M1), 18)
+        got = ctx.density(ctx.from_dense(phi), x)
+        ref = O.density_on_line(p, phi, x)
+        assert rel(got, ref) < tol, (p.name, rel(got, ref))
+    p = W.config_scale_1d()
+    ctx = P.Context(p, dtype)
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
+    xs = np.array([-3.0, 0.0, 0.5, 2.25, 40.0])
+    got = ctx.density(psi, xs)
+    ref = O.density_on_line(p, ctx.to_dense(psi), xs)
+    assert rel(got, ref) < tol * 10, rel(got, ref)
+    with pytest.raises(P.LsplitError):
+        c2 = P.Context(W.twisted_2d(q=8, hmax=2), dtype)
+        c2.density(c2.empty(), [0.0])
+
+
 def test_large_kinetic_phase_free_particle(P):
     """V = 0 at the 2049-box extremes: every element must be the exact phase
     exp(-i T |k|^2/2) (argument reduction of |theta| up to ~1e4 rad)."""
