@@ -53,6 +53,23 @@ def test_single_plane_wave_layer(P, dtype, scheme):
         assert run_vs_oracle(P, p, dtype, scheme, seed=2) < TOL[dtype] * 3, p.name
 
 
+def test_largest_1d_box_one_step(P):
+    """4097 x 4097 lifted box (16.8 M DOF, 134 MB complex64): both layers on
+    the general pass with transforms of 8192, one Strang step against the
+    oracle's FFT backend."""
+    p = W.bilayer_1d(2048, 2048, 1.0, 0.8, ecut=1e9)
+    ctx = P.Context(p, "c64")
+    x = W.random_state((p.M2, p.M1), 19)
+    psi = ctx.from_dense(x)
+    ctx.step(psi, 1, 5e-4, "strang")
+    O.use_fft(True)
+    try:
+        ref = O.step(p, x, 5e-4, "strang", 1)
+    finally:
+        O.use_fft(False)
+    assert rel(ctx.to_dense(psi), ref) < TOL["c64"] * 3
+
+
 @pytest.mark.parametrize("dtype", ["c64"])
 def test_longest_1d_slices(P, dtype):
     """The largest accepted complex64 1D slices: q = 4097 (transform length
