@@ -168,7 +168,7 @@ def run_reference(args):
     tot = sum(times)
     val = p.dof * args.steps / tot
     line = {
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF-steps/s", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
