@@ -10,7 +10,7 @@ the coefficient array phi[n, m] (Sec. 3): the row index is the linear layer-2
 index n, the column index the linear layer-1 index m (for d = 2 the first
 component is fastest).  The wavevector of phi[n, m] is k = B1 m + B2 n.
 
-Readings of passages the paper leaves open (listed again in the design doc):
+Readings of passages the paper leaves open:
 
 * The lifted array is the full index box; the joint cutoff |k|^2/2 <= Ec of the
   index sets (Sec. 3) is a mask used for the initial state, the index-set query
