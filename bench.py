@@ -126,6 +126,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_job_time(t_ms: float, world: int, device: str) -> float:
+    """The job's time: the longest per-rank timed region (MAX over ranks)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return t_ms
+
+
+def job_value(dof: int, time_steps: int, world: int, t_ms: float) -> float:
+    """Whole-job DOF-steps/s: each of the world ranks advances its own replica
+    (the path does not shard) by time_steps steps within t_ms."""
+    return world * dof * time_steps / (t_ms / 1e3)
+
+
 def dist_env():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -373,11 +390,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     per = [a.elapsed_time(b) for a, b in ev]
-    t_ms = float(sum(per))
-    if world > 1:
-        t = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
+    t_ms = reduce_job_time(float(sum(per)), world, "cuda")
     # one-time-step calls (no cross-step fusion), for reference
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t1 = 0.0
@@ -390,7 +403,7 @@ def run_ours(args):
         t1 += e0.elapsed_time(e1)
     single_call = p.dof * 20 / (t1 / 1e3)
     obs = ctx.observables(psi)
-    value = world * p.dof * args.steps * NI / (t_ms / 1e3)
+    value = job_value(p.dof, args.steps * NI, world, t_ms)
 
     # plain FP64 GPU form (same kernels in complex128)
     ctx64 = P.Context(p, "c128")
