@@ -92,6 +92,27 @@ def test_batched_fast_tiles_parity(P, scheme):
         O.use_fft(False)
 
 
+def test_batched_fused_walk_matches_unfused(P, monkeypatch):
+    """Deterministic Strang in the persistent launch fuses adjacent layer-1
+    factors of consecutive steps (fused tiles for the convolution-form
+    instances, back-to-back factors for the others); the state is the same
+    as with the plain walk."""
+    import torch
+    probs = W.batch_1d(count=6, seed=12, nmin=40, nmax=400)
+    outs = []
+    for flag in (None, "1"):
+        if flag:
+            monkeypatch.setenv("LSPLIT_NO_FUSE", flag)
+        else:
+            monkeypatch.delenv("LSPLIT_NO_FUSE", raising=False)
+        b = P.Batch(probs, "c64")
+        psi = b.empty()
+        b.init_gaussian(psi, [0.0], 2.0, [1.0])
+        b.step(psi, 5, 1e-3, "strang")
+        outs.append(psi)
+    assert float(torch.linalg.vector_norm(outs[0] - outs[1])) <= 1e-6 * float(torch.linalg.vector_norm(outs[1]))
+
+
 def test_batched_matches_single_contexts(P):
     """The same instances stepped one context at a time agree with the batch."""
     probs = W.batch_1d(count=5, seed=11, nmin=8, nmax=300)
