@@ -132,3 +132,23 @@ def test_strang_time_reversal_full_size(P, dtype, tol):
     err = float(torch.linalg.vector_norm(psi - x) / torch.linalg.vector_norm(x))
     assert moved > 0.1, moved
     assert err < tol, err
+
+
+@pytest.mark.parametrize("dtype,tol", [("c64", 2e-6), ("c128", 1e-12)])
+def test_cn_and_semi_implicit_free_particle_closed_forms(P, dtype, tol):
+    """V = 0, checked against closed forms rather than the oracle: the
+    Crank-Nicolson split multiplies each element per step by
+    C(tau/2)^2 C(tau), C(s) = (1 - i s kin/4)/(1 + i s kin/4) (no Jacobi sweep
+    is needed); the semi-implicit step divides by (1 + i tau kin)."""
+    p = W.bilayer_1d(300, 200, 0.0, 0.0, ecut=1e9)
+    kin = O.kinetic_energy_diag(p)
+    x = W.random_state((p.M2, p.M1), 21)
+    tau, n = 2e-4, 3
+    ctx = P.Context(p, dtype)
+    psi = ctx.from_dense(x)
+    ctx.step(psi, n, tau, "cn_strang")
+    C = lambda s: (1 - 0.25j * s * kin) / (1 + 0.25j * s * kin)
+    assert rel(ctx.to_dense(psi), x * (C(tau / 2) ** 2 * C(tau)) ** n) < tol
+    psi = ctx.from_dense(x)
+    ctx.step(psi, n, tau, "semi_implicit")
+    assert rel(ctx.to_dense(psi), x / (1 + 1j * tau * kin) ** n) < tol
