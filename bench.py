@@ -333,6 +333,21 @@ def run_suite(args):
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     line("adjoint bilayer1d-513x513 500 steps forward+backward c64 (host wall clock)", prob.dof, 500, t, {})
+
+    # wave function on a real-space line: 4096 points on the 2049^2 box
+    p = W.config_scale_1d()
+    c = P.Context(p, "c64")
+    psi = c.empty()
+    c.init_gaussian(psi, [0.0], 2.0, [1.0])
+    xs = np.linspace(-50.0, 50.0, 4096)
+    c.density(psi, xs)
+    t0 = time.perf_counter()
+    c.density(psi, xs)
+    t = time.perf_counter() - t0
+    out.append({"workload": "density on a line, 4096 points, bilayer1d-2049x2049 c64 (host wall clock incl. "
+                            "allocation and copy-back)", "points": len(xs), "dof": p.dof, "seconds": t,
+                "point_dof_per_s": len(xs) * p.dof / t})
+    print(json.dumps(out[-1]), flush=True)
     return out
 
 
