@@ -63,8 +63,8 @@ enum { LS_C64 = 0, LS_C128 = 1 };
  *   LS_YOSHIDA4     fourth order: three LS_STRANG steps of w1 tau, w0 tau, w1 tau,
  *                   w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3) w1 (the higher-order
  *                   splittings of Sec. 4.2 and Appendix A, by Yoshida's symmetric
- *                   composition); ls_step only (not the batched runner or
- *                   ls_adjoint, which return LS_ERR_INVALID).
+ *                   composition); ls_step and ls_adjoint (the batched runner
+ *                   returns LS_ERR_INVALID).
  *   LS_CN_STRANG    Crank-Nicolson layer splitting (Sec. 4.2.1, Eq. (tsCN)):
  *                   C1(tau/2) C2(tau) C1(tau/2), C_j(s) = (I + i s H_j/2)^{-1}
  *                   (I - i s H_j/2), H_j = D/2 + V^j with V^j the plane-wave
@@ -206,7 +206,8 @@ int ls_samples(ls_ctx* ctx, int32_t layer, uint64_t seed, uint64_t g0, int32_t c
  * gradients; grad_c1_host / grad_c2_host (2*nv doubles, may be NULL) receive
  * (dL/dRe vhat_h, dL/dIm vhat_h) for every coefficient.  On return psi_dev
  * holds the rebuilt phi_0 and lam_dev the gradient with respect to
- * conj(phi_0).  Deterministic schemes only.  Synchronises the stream. */
+ * conj(phi_0).  Schemes LS_LIE, LS_STRANG, LS_STRANG_KP and LS_YOSHIDA4
+ * (otherwise LS_ERR_INVALID).  Synchronises the stream. */
 int ls_adjoint(ls_ctx* ctx, void* psi_dev, void* lam_dev, int64_t nsteps, double tau,
                int32_t scheme, double* grad_v1_host, double* grad_v2_host,
                double* grad_c1_host, double* grad_c2_host, void* stream);

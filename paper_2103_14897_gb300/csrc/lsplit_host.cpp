@@ -1291,8 +1291,8 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
                double* gc1, double* gc2, void* stream) {
   if (!c) return fail(LS_ERR_STATE, "context is NULL");
   if (!psi || !lam || !gv1 || !gv2) return fail(LS_ERR_INVALID, "NULL argument");
-  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP)
-    return fail(LS_ERR_INVALID, "adjoint supports LIE, STRANG and STRANG_KP only");
+  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP && scheme != LS_YOSHIDA4)
+    return fail(LS_ERR_INVALID, "adjoint supports LIE, STRANG, STRANG_KP and YOSHIDA4 only");
   if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
@@ -1308,6 +1308,7 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
     for (size_t i = ps.size(); i-- > 0;) {
       const PassSpec& q = ps[i];
       const int L = q.layer - 1;
+      if (q.unit != 0) set_kinetic(c, q.unit);  // per-pass kinetic unit (fourth-order scheme)
       lsk::PassArgs a = base_args(c, L, psi);
       a.mode = lsk::MODE_ADJOINT;
       a.lam = lam;

@@ -489,7 +489,7 @@ def test_adjoint_parity(P):
     p = base.with_potentials(c1, c2, h1, h2)
     phi0 = O.gaussian_packet(p, [0.0], 0.8, [1.0])
     chi = O.gaussian_packet(p, [0.3], 0.8, [1.2])
-    for scheme in ("strang", "lie", "strang_kp"):
+    for scheme in ("strang", "lie", "strang_kp", "yoshida4"):
         L, phiT, g1, g2 = O.adjoint(p, phi0, 0.02, scheme, 6, lambda f: O.overlap_loss(chi, f))
         for dtype, tol in (("c64", 2e-5), ("c128", 1e-10)):
             ctx = P.Context(p, dtype)
