@@ -325,17 +325,16 @@ def apply_semi_implicit(prob, phi: np.ndarray, tau: float, rows=None, cols=None,
 # Real-space wave function on a line (Sec. 3 expansion; the localisation
 # plots of Sec. 5)
 # --------------------------------------------------------------------------
-def density_on_line(prob, phi: np.ndarray, x: Sequence[float]) -> np.ndarray:
-    """psi(x_j) = sum_{m,n} phi[n, m] exp(i k_mn x_j) for a 1D box, the
-    plane-wave expansion of the wave function (Sec. 3), evaluated point by
-    point; the phase k x is formed in FP64 from k of wavevectors()."""
-    if prob.d != 1:
-        raise ValueError("density_on_line: 1D boxes")
-    k = wavevectors(prob)[..., 0]
-    x = np.asarray(x, dtype=np.float64).reshape(-1)
+def density_on_line(prob, phi: np.ndarray, x) -> np.ndarray:
+    """psi(x_j) = sum_{m,n} phi[n, m] exp(i k_mn . x_j), the plane-wave
+    expansion of the wave function (Sec. 3), evaluated point by point; the
+    phase k . x is formed in FP64 from k of wavevectors().  x: (npts,) for 1D
+    boxes, (npts, 2) for 2D boxes."""
+    k = wavevectors(prob)
+    x = np.asarray(x, dtype=np.float64).reshape(-1, prob.d)
     out = np.empty(len(x), dtype=np.complex128)
     for j, xj in enumerate(x):
-        out[j] = np.sum(phi * np.exp(1j * k * xj))
+        out[j] = np.sum(phi * np.exp(1j * (k @ xj)))
     return out
 
 

@@ -692,3 +692,15 @@ def test_density_periodic_for_commensurate_layers():
     phi = rand_state(p, 42)
     x = np.array([0.1, 0.37, 1.3])
     np.testing.assert_allclose(O.lsplit.density_on_line(p, phi, x + 2.0), O.lsplit.density_on_line(p, phi, x), atol=1e-11)
+
+
+def test_density_2d_single_plane_wave():
+    """2D box: one coefficient gives phi_mn exp(i (B1 m + B2 n) . x)."""
+    p = W.twisted_2d(q=4, hmax=1)
+    phi = np.zeros((p.M2, p.M1), dtype=np.complex128)
+    phi[5, 9] = 0.7 + 0.1j
+    m = np.array([9 % 4, 9 // 4]) + np.array(p.lo1)
+    n = np.array([5 % 4, 5 // 4]) + np.array(p.lo2)
+    k = p.B1 @ m + p.B2 @ n
+    x = np.array([[0.3, -1.2], [4.0, 2.5]])
+    np.testing.assert_allclose(O.lsplit.density_on_line(p, phi, x), (0.7 + 0.1j) * np.exp(1j * (x @ k)), atol=1e-13)
