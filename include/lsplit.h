@@ -178,14 +178,14 @@ int ls_step(ls_ctx* ctx, void* psi_dev, int64_t nsteps, double tau, int32_t sche
 int ls_observables(ls_ctx* ctx, const void* psi_dev, const void* chi_dev, ls_obs* out,
                    void* stream);
 
-/* Wave function on a real-space line from the plane-wave expansion (Sec. 3;
- * the localisation plots of Sec. 5), 1D boxes:
- *   psi(x_j) = sum_{m,n} phi[n][m] exp(i (B1 m + B2 n) x_j),  j < nx.
- * x_host: nx doubles; out_host: 2 nx doubles (re, im per point).  The phases
- * are exact (64-bit fixed-point turns); the sum over m runs in the context's
- * precision, the sum over n in FP64.  Allocates temporary device buffers of
- * about nx (M1 + 2 M2) complex elements and synchronises the stream.
- * LS_ERR_INVALID for 2D boxes or nx beyond 2^22. */
+/* Wave function at real-space points from the plane-wave expansion (Sec. 3;
+ * the localisation plots of Sec. 5):
+ *   psi(x_j) = sum_{m,n} phi[n][m] exp(i (B1 m + B2 n) . x_j),  j < nx.
+ * x_host: nx points of d doubles each; out_host: 2 nx doubles (re, im per
+ * point).  The phases are exact (64-bit fixed-point turns); the sum over m
+ * runs in the context's precision, the sum over n in FP64.  Allocates
+ * temporary device buffers of about nx (M1 + 2 M2) complex elements and
+ * synchronises the stream.  LS_ERR_INVALID for nx beyond 2^22. */
 int ls_density(ls_ctx* ctx, const void* psi_dev, const double* x_host, int64_t nx, double* out_host,
                void* stream);
 

@@ -218,8 +218,10 @@ class Context:
                             int(seed) & (2 ** 64 - 1), int(step0), _stream_handle(stream)))
 
     def density(self, psi, x, stream=None) -> np.ndarray:
-        """psi(x_j) on real-space points x (1D boxes), complex128 array."""
-        xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+        """psi(x_j) at real-space points x ((npts,) for 1D boxes, (npts, 2)
+        for 2D boxes), complex128 array."""
+        d = self.prob.d
+        xs = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, d))
         out = np.zeros(2 * len(xs), dtype=np.float64)
         _check(_lib.ls_density(self._h, _ptr(psi), xs.ctypes.data_as(C.POINTER(C.c_double)), len(xs),
                                out.ctypes.data_as(C.POINTER(C.c_double)), _stream_handle(stream)))

@@ -1,25 +1,28 @@
-// Wave function on a real-space line from the plane-wave expansion (Sec. 3):
-//   psi(x_j) = sum_{m,n} phi[n][m] exp(i k_mn x_j),  k_mn = B1 m + B2 n  (1D).
-// The phase factorises, exp(i k x) = exp(i B1 m x) exp(i B2 n x), so
+// Wave function at real-space points from the plane-wave expansion (Sec. 3):
+//   psi(x_j) = sum_{m,n} phi[n][m] exp(i k_mn . x_j),  k_mn = B1 m + B2 n.
+// The phase factorises, exp(i k . x) = exp(i m . B1^T x) exp(i n . B2^T x), so
 //   T[j][n] = sum_m E1[j][m] phi[n][m],   psi_j = sum_n E2[j][n] T[j][n],
-// with E1[j][m] = exp(i B1 (lo1 + m) x_j), E2[j][n] = exp(i B2 (lo2 + n) x_j).
-// The tables come from exact fixed-point turns (the host gives B x_j / 2 pi
-// as a 64-bit fraction per point; the integer index multiplies it modulo
-// 2^64), the contraction over m is a tiled complex product (64 x 64 outputs
-// per CTA, 16-wide slabs of m in shared memory), the sum over n is one warp
-// per point with FP64 accumulation.
+// with E1[j][m] = exp(i m . B1^T x_j), E2[j][n] = exp(i n . B2^T x_j).
+// The tables come from exact fixed-point turns (the host gives the components
+// of B^T x_j / 2 pi as 64-bit fractions per point; the integer index
+// components multiply them modulo 2^64), the contraction over m is a tiled
+// complex product (64 x 64 outputs per CTA, 16-wide slabs of m in shared
+// memory), the sum over n is one warp per point with FP64 accumulation.
 #include "lsplit_kernels.cuh"
 
 namespace lsk {
 
+// E[j][m] = exp(2 pi i (ma fa_j + mb fb_j)), ma = lo_a + m % qa, mb = lo_b + m / qa
+// (1D: qa = q and mb = 0), turns modulo 2^64
 template <typename Real>
-__global__ void density_table_kernel(const uint64_t* __restrict__ f, int64_t nx, int64_t q, int32_t lo,
-                                     typename CT<Real>::C* __restrict__ E) {
+__global__ void density_table_kernel(const uint64_t* __restrict__ f, int64_t nx, int64_t q, int32_t qa,
+                                     int32_t lo_a, int32_t lo_b, typename CT<Real>::C* __restrict__ E) {
   const int64_t total = nx * q;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = idx / q, m = idx - j * q;
-    const uint64_t t = (uint64_t)(int64_t)(lo + m) * f[j];
+    const int64_t ma = lo_a + m % qa, mb = lo_b + m / qa;
+    const uint64_t t = (uint64_t)ma * f[j] + (uint64_t)mb * f[nx + j];
     E[idx] = phase_of<Real>(t).v;
   }
 }
@@ -114,9 +117,9 @@ cudaError_t launch_density(const DensityArgs& d, cudaStream_t st) {
   C* T = static_cast<C*>(d.t);
   const int64_t n1 = d.nx * d.M1, n2 = d.nx * d.M2;
   density_table_kernel<Real><<<(unsigned)std::min<int64_t>((n1 + 255) / 256, 152 * 16), 256, 0, st>>>(
-      d.f1, d.nx, d.M1, d.lo1, E1);
+      d.f1, d.nx, d.M1, d.q1a, d.lo1a, d.lo1b, E1);
   density_table_kernel<Real><<<(unsigned)std::min<int64_t>((n2 + 255) / 256, 152 * 16), 256, 0, st>>>(
-      d.f2, d.nx, d.M2, d.lo2, E2);
+      d.f2, d.nx, d.M2, d.q2a, d.lo2a, d.lo2b, E2);
   const dim3 grid((unsigned)((d.nx + 63) / 64), (unsigned)((d.M2 + 63) / 64));
   density_contract_kernel<Real><<<grid, 256, 0, st>>>(E1, static_cast<const C*>(d.psi), d.nx, d.M1, d.M2, d.pitch, T);
   density_reduce_kernel<Real><<<(unsigned)((d.nx + 7) / 8), 256, 0, st>>>(E2, T, d.nx, d.M2, d.out);

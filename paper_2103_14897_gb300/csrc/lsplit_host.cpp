@@ -1219,16 +1219,24 @@ int ls_observables(ls_ctx* c, const void* psi, const void* chi, ls_obs* out, voi
 int ls_density(ls_ctx* c, const void* psi, const double* x, int64_t nx, double* out, void* stream) {
   if (!c) return fail(LS_ERR_STATE, "context is NULL");
   if (!psi || (nx > 0 && (!x || !out))) return fail(LS_ERR_INVALID, "NULL argument");
-  if (c->d != 1) return fail(LS_ERR_INVALID, "ls_density takes 1D boxes");
   if (nx < 0 || nx > ((int64_t)1 << 22)) return fail(LS_ERR_INVALID, "nx must be in [0, 2^22]");
   if (nx == 0) return LS_OK;
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
-    std::vector<uint64_t> f((size_t)2 * nx);
+    const int dim = c->d;
+    // f[layer][component][j] = (B^T x_j)_component / 2 pi as 64-bit fractions
+    std::vector<uint64_t> f((size_t)4 * nx, 0);
     for (int64_t j = 0; j < nx; ++j) {
-      if (!std::isfinite(x[j])) return fail(LS_ERR_INVALID, "x is not finite");
-      f[(size_t)j] = to_fixed(c->p.B1[0] * x[j] / (2.0 * kPi));
-      f[(size_t)(nx + j)] = to_fixed(c->p.B2[0] * x[j] / (2.0 * kPi));
+      for (int i = 0; i < dim; ++i)
+        if (!std::isfinite(x[j * dim + i])) return fail(LS_ERR_INVALID, "x is not finite");
+      for (int L = 0; L < 2; ++L) {
+        const double* B = L == 0 ? c->p.B1 : c->p.B2;
+        for (int a = 0; a < dim; ++a) {
+          double v = 0;
+          for (int i = 0; i < dim; ++i) v += B[i * dim + a] * x[j * dim + i];
+          f[(size_t)((2 * L + a) * nx + j)] = to_fixed(v / (2.0 * kPi));
+        }
+      }
     }
     DevBuf fb, e1, e2, t, ob;
     fb.alloc(f.size() * sizeof(uint64_t));
@@ -1243,10 +1251,14 @@ int ls_density(ls_ctx* c, const void* psi, const double* x, int64_t nx, double* 
     d.M2 = c->M2;
     d.pitch = c->pitch;
     d.nx = nx;
-    d.lo1 = c->p.lo1[0];
-    d.lo2 = c->p.lo2[0];
+    d.q1a = c->p.q1[0];
+    d.q2a = c->p.q2[0];
+    d.lo1a = c->p.lo1[0];
+    d.lo1b = dim > 1 ? c->p.lo1[1] : 0;
+    d.lo2a = c->p.lo2[0];
+    d.lo2b = dim > 1 ? c->p.lo2[1] : 0;
     d.f1 = static_cast<const uint64_t*>(fb.p);
-    d.f2 = static_cast<const uint64_t*>(fb.p) + nx;
+    d.f2 = static_cast<const uint64_t*>(fb.p) + 2 * nx;
     d.e1 = e1.p;
     d.e2 = e2.p;
     d.t = t.p;

@@ -239,15 +239,16 @@ struct SiArgs {
 };
 template <typename Real> cudaError_t launch_si(const SiArgs& a, cudaStream_t st);
 
-// Wave function on a real-space line (1D boxes): device buffers of the
-// phase tables E1 (nx x M1), E2 (nx x M2), the partial sums T (nx x M2) and
-// the output (2 nx doubles); f1/f2: B x_j / 2 pi as 64-bit fractions per point.
+// Wave function at real-space points: device buffers of the phase tables
+// E1 (nx x M1), E2 (nx x M2), the partial sums T (nx x M2) and the output
+// (2 nx doubles); f1/f2: B^T x_j / 2 pi as 64-bit fractions per point.
 struct DensityArgs {
   const void* psi;
   int64_t M1, M2, pitch, nx;
-  int32_t lo1, lo2;
-  const uint64_t* f1;
-  const uint64_t* f2;
+  int32_t q1a, q2a;                   // first extent of each layer box (the linear index is a + q_a b)
+  int32_t lo1a, lo1b, lo2a, lo2b;
+  const uint64_t* f1;                 // [2 nx]: (B1^T x_j)_a / 2 pi at j, (B1^T x_j)_b / 2 pi at nx + j
+  const uint64_t* f2;                 // [2 nx]: the same with B2
   void *e1, *e2, *t;
   double* out;
 };

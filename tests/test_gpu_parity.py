@@ -271,10 +271,10 @@ def test_step_parity_semi_implicit(P, dtype, scheme):
 
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
 def test_density_on_line_parity(P, dtype, tol):
-    """psi(x) on a line from the plane-wave expansion: exact fixed-point phase
-    tables, tiled contraction over m, FP64 sum over n; small boxes with many
-    points (several 64 x 64 tiles and ragged edges) and the 2049 x 2049 box
-    at a few points, including large |x|."""
+    """psi(x) from the plane-wave expansion: exact fixed-point phase tables,
+    tiled contraction over m, FP64 sum over n; small 1D boxes with many points
+    (several 64 x 64 tiles and ragged edges), the 2049 x 2049 box at a few
+    points, large |x|, and 2D boxes at points in the plane."""
     x = np.concatenate([np.linspace(-20.0, 20.0, 301), [1234.5, -987.25]])
     for p in [W.config_small_1d(), W.bilayer_1d(256, 12, 1.0, 1.4, ecut=1e9), problems_1d()[4]]:
         ctx = P.Context(p, dtype)
@@ -290,9 +290,15 @@ def test_density_on_line_parity(P, dtype, tol):
     got = ctx.density(psi, xs)
     ref = O.density_on_line(p, ctx.to_dense(psi), xs)
     assert rel(got, ref) < tol * 10, rel(got, ref)
-    with pytest.raises(P.LsplitError):
-        c2 = P.Context(W.twisted_2d(q=8, hmax=2), dtype)
-        c2.density(c2.empty(), [0.0])
+    # 2D boxes: points in the plane
+    rng = np.random.default_rng(22)
+    x2 = np.concatenate([rng.uniform(-6, 6, size=(129, 2)), [[150.0, -80.5]]])
+    for p in [W.twisted_2d(q=8, hmax=2), W.twisted_2d(q=16, hmax=3)]:
+        ctx = P.Context(p, dtype)
+        phi = W.random_state((p.M2, p.M1), 23)
+        got = ctx.density(ctx.from_dense(phi), x2)
+        ref = O.density_on_line(p, phi, x2)
+        assert rel(got, ref) < tol, (p.name, rel(got, ref))
 
 
 def test_large_kinetic_phase_free_particle(P):
