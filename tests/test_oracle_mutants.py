@@ -38,6 +38,9 @@ PINS = [
     pins.test_density_periodic_for_commensurate_layers,
     pins.test_adjoint_matches_central_differences,
     pins.test_one_step_equals_dense_factor_product,
+    lambda: pins.test_stochastic_steps_match_dense_sampled_factors("strang_stoch"),
+    lambda: pins.test_stochastic_steps_match_dense_sampled_factors("lie_stoch"),
+    pins.test_gaussian_packet_position_and_momentum,
 ]
 
 _orig_dft = L.dft_matrix
@@ -52,6 +55,20 @@ _orig_C = L.apply_C
 _orig_SI = L.apply_semi_implicit
 _orig_dens = L.density_on_line
 _orig_wv = L.wavevectors
+_orig_exp = L.expanded_factors
+_orig_gp = L.gaussian_packet
+
+
+def _stoch_scale_inverted(prob, scheme, tau, nsteps, seed=0, step0=0, frac_den=8):
+    # sampled factors with duration s p / S instead of s S / p
+    out = []
+    for f in _orig_exp(prob, scheme, tau, nsteps, seed, step0, frac_den):
+        if f[0] == "P" and f[3] is not None:
+            S = prob.M2 if f[1] == 1 else prob.M1
+            r = len(f[3]) / S
+            f = ("P", f[1], f[2] * r * r, f[3])
+        out.append(f)
+    return out
 
 
 def _strang_wrong(scheme, tau):
@@ -93,6 +110,13 @@ MUTANTS = {
                                        _orig_SI(p, phi, tau, rows, cols, _kin) * (1 + 1j * tau * L.kinetic_energy_diag(p))),
     "random_batch_ignores_sample": ("apply_semi_implicit", lambda p, phi, tau, rows=None, cols=None, _kin=None:
                                     _orig_SI(p, phi, tau, None, None, _kin)),
+    "stoch_scale_inverted": ("expanded_factors", _stoch_scale_inverted),
+    "stoch_scale_dropped": ("expanded_factors", lambda prob, scheme, tau, nsteps, seed=0, step0=0, frac_den=8: [
+        ("P", f[1], f[2] * len(f[3]) / (prob.M2 if f[1] == 1 else prob.M1), f[3])
+        if f[0] == "P" and f[3] is not None else f
+        for f in _orig_exp(prob, scheme, tau, nsteps, seed, step0, frac_den)]),
+    "packet_x0_sign": ("gaussian_packet", lambda prob, x0, w, k0: _orig_gp(prob, -np.asarray(x0, dtype=float), w, k0)),
+    "packet_k0_sign": ("gaussian_packet", lambda prob, x0, w, k0: _orig_gp(prob, x0, w, -np.asarray(k0, dtype=float))),
     "cn_layer2_half": ("apply_C", lambda p, phi, layer, s, _kin=None:
                        _orig_C(p, phi, layer, s / 2 if layer == 2 else s, _kin)),
 }

@@ -237,6 +237,56 @@ def test_stochastic_sampled_factor_matches_dense():
     np.testing.assert_allclose(y, ref, atol=1e-13)
 
 
+def _dense_stochastic_steps(p, x, tau, scheme, nsteps, seed, step0, frac_den):
+    """Dense stand-in for the stochastic schemes: every potential factor of
+    duration s is exp(-i s (S/p) C_j) (C_j the circulant built from the Fourier
+    coefficients) on the p sampled slices and the identity on the others
+    (Algorithm 4: the sampled part is amplified by |I|/p), the kinetic factors
+    exp(-i s |k|^2/2) act on every element; Strang or Lie order."""
+    m = np.arange(p.q1[0]) + p.lo1[0]
+    n = np.arange(p.q2[0]) + p.lo2[0]
+    k = p.B1[0, 0] * m[None, :] + p.B2[0, 0] * n[:, None]
+    kin = 0.5 * k ** 2
+    C = {1: circulant_from_coeffs(p.v1_h, p.v1_c, p.q1[0]), 2: circulant_from_coeffs(p.v2_h, p.v2_c, p.q2[0])}
+    if scheme == "strang_stoch":
+        seq = []
+        for j, s in ((1, tau / 2), (2, tau), (1, tau / 2)):
+            seq += [("K", s / 4), ("P", j, s), ("K", s / 4)]
+    else:
+        seq = [("K", tau), ("P", 1, tau), ("P", 2, tau)]
+    y = np.array(x, dtype=np.complex128)
+    for st in range(nsteps):
+        pi = 0
+        for f in seq:
+            if f[0] == "K":
+                y = y * np.exp(-1j * f[1] * kin)
+                continue
+            j, s = f[1], f[2]
+            S = p.M2 if j == 1 else p.M1
+            cnt = max(1, S // frac_den)
+            sl = O.sample_slices(S, cnt, seed, (step0 + st) * (3 if scheme == "strang_stoch" else 2) + pi)
+            U = expm_herm(C[j], s * S / cnt)
+            if j == 1:
+                y[sl] = (U @ y[sl].T).T
+            else:
+                y[:, sl] = U @ y[:, sl]
+            pi += 1
+    return y
+
+
+@pytest.mark.parametrize("scheme", ["strang_stoch", "lie_stoch"])
+def test_stochastic_steps_match_dense_sampled_factors(scheme):
+    """p < S (frac_den = 3, so S/p = 11/3 and 13/4): the oracle's stochastic
+    steps equal the dense construction above, which fixes the duration scale
+    S/p of the sampled factors and the sub-step numbering of the samples."""
+    p = W.bilayer_1d(6, 5, 1.3, 0.9, ecut=1e9)
+    x = rand_state(p, 31)
+    for nsteps, step0 in ((1, 0), (2, 3)):
+        got = O.step(p, x, 0.02, scheme, nsteps, seed=9, step0=step0, frac_den=3)
+        ref = _dense_stochastic_steps(p, x, 0.02, scheme, nsteps, 9, step0, 3)
+        np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
 # ---------------------------------------------------------------- physics pins
 def test_commensurate_fiber_sum_matches_supercell():
     """L2 = 2/3: k = pi (2m + 3n).  The fiber sum c_j = sum_{2m+3n=j} phi_mn of
@@ -341,6 +391,39 @@ def test_gaussian_packet_reduces_to_paper_initial_state():
     k = 2 * np.pi * m[None, :] + 2 * np.pi / W.GOLDEN * nn[:, None]
     ref = np.exp(-(w * w / 2) * k ** 2) * (0.5 * k ** 2 <= 200.0)
     np.testing.assert_allclose(phi, ref / np.linalg.norm(ref), atol=1e-15)
+
+
+def test_gaussian_packet_position_and_momentum():
+    """The packet in real space, through its plane-wave expansion (Sec. 3):
+    every amplitude exp(-w^2 |k - k0|^2 / 2) is positive, so |psi(x)| <= sum |phi|
+    with equality exactly at x = x0 (triangle inequality); moving the centre is
+    a translation, psi_{x0}(x) = psi_0(x - x0); and the phase of psi advances at
+    the mean momentum, close to k0, around x0."""
+    p = W.config_small_1d()
+    for x0, k0 in ((0.7, 1.0), (-1.3, -2.0)):
+        phi = O.lsplit.gaussian_packet(p, [x0], 2.0, [k0])
+        top = float(np.abs(phi).sum())
+        xs = x0 + np.linspace(-3.0, 3.0, 61)
+        d = np.abs(O.lsplit.density_on_line(p, phi, xs))
+        assert abs(d[30] - top) < 1e-12 * top
+        assert np.all(np.delete(d, 30) < top * (1 - 1e-6))
+        np.testing.assert_allclose(O.lsplit.density_on_line(p, phi, xs),
+                                   O.lsplit.density_on_line(p, O.lsplit.gaussian_packet(p, [0.0], 2.0, [k0]), xs - x0),
+                                   atol=1e-10)
+        e = O.lsplit.density_on_line(p, phi, [x0 - 1e-3, x0 + 1e-3])
+        slope = float(np.angle(e[1] / e[0])) / 2e-3
+        assert abs(slope - k0) < 0.03 * max(1.0, abs(k0)), (slope, k0)
+    # 2D: the same peak and translation identities in the plane
+    q = W.twisted_2d(q=8, ecut=30.0)
+    x0 = np.array([0.1, -0.2])
+    phi = O.lsplit.gaussian_packet(q, x0, 2.0, [1.0, 0.0])
+    rng = np.random.default_rng(3)
+    pts = np.concatenate([x0[None, :], x0 + rng.uniform(-2, 2, size=(40, 2))])
+    d = np.abs(O.lsplit.density_on_line(q, phi, pts))
+    assert abs(d[0] - np.abs(phi).sum()) < 1e-12 * d[0] and np.all(d[1:] < d[0])
+    np.testing.assert_allclose(O.lsplit.density_on_line(q, phi, pts),
+                               O.lsplit.density_on_line(q, O.lsplit.gaussian_packet(q, [0.0, 0.0], 2.0, [1.0, 0.0]), pts - x0),
+                               atol=1e-10)
 
 
 # ---------------------------------------------------------------- index set
