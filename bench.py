@@ -1,24 +1,27 @@
 """Throughput of the layer-split step on one GB300 (or N replicas).
 
-Workload: the 2049 x 2049 lifted 1D incommensurate bilayer (L1 = 1,
-L2 = (sqrt5-1)/2, v_j = a_j cos(2 pi x / L_j), a_j ~ U(0.5, 2) seed 2,
-joint cutoff Ec = 204800), complex64 with FP64-derived tables, Gaussian packet
-(x0 = 0, w = 2, k0 = 1), tau = 5e-4, second-order (Strang) layer split.
+Headline workload: 256 independent, uneven 1D incommensurate bilayers
+(L2/L1 ~ U(0.3, 0.9), box half-widths N1, N2 ~ U{16..512}, v_j = a_j
+cos(2 pi x / L_j) with a_j ~ U(0.5, 2), seed 4; 67.4 M lifted DOF, 540 MB in
+complex64), the second-order (Strang) layer split with tau = 1e-3, all
+instances advanced by ONE persistent launch per call (ls_batch_step).  One
+bench step = one call of --inner time steps on device-resident data; psi is
+larger than L2, so no flush is needed.  Metric: lifted DOF-steps/s =
+(total DOF * time steps) / seconds.
 
-One bench step = one time step of the scheme (3 fused slice passes) through
-ls_step on device-resident data.  psi (33.8 MB) fits in L2, so a 512 MB buffer
-is written between timed steps (L2 flush, untimed).  Metric: lifted
-DOF-steps/s = (M1 * M2 * steps) / seconds.
-
-Also reported: the same metric for the plain FP64 (complex128) GPU form, the
-end-to-end figure through the C ABI with host buffers (H2D copy, step, D2H
-copy inside the timed region), the roofline of the pass kernel, the accuracy
-gate against the oracle, and the FP64 CPU oracle on the host cores.
+Also reported: the roofline of the persistent batched kernel (48 algorithmic
+bytes per DOF-step against the measured HBM copy bandwidth); the accuracy gate
+(one step of sampled instances against the oracle); the plain FP64
+(complex128) GPU form of the same batch; the end-to-end figure through the C
+ABI with host buffers (ls_batch_step_host: H2D copy, steps, D2H copy inside the
+timed region); the oracle on the host cores for a bounded sample of the
+instances; and two sub-workloads with their own rooflines: the 2049 x 2049
+bilayer (L2-resident) and the 64^4 twisted bilayer.
 
 --impl reference: times the FP64 CPU oracle (the reference arm of this
-repository) on the same workload.
-Multi-GPU: the workload does not shard (one lifted array), so N ranks run N
-independent replicas ("replicas only"); value sums all ranks' DOF-steps.
+repository) on a bounded sample of the same batched workload.
+Multi-GPU: the instances are independent, but each rank runs the whole set
+("replicas only", no data-path collective); value sums all ranks' DOF-steps.
 """
 from __future__ import annotations
 
@@ -150,12 +153,12 @@ def dist_env():
     return r, w, lr
 
 
-def oracle_step_rate(prob, x, steps, scheme="strang"):
+def oracle_step_rate(prob, x, steps, scheme="strang", tau=TAU):
     import oracle as O
     O.use_fft(True)
     try:
         t0 = time.perf_counter()
-        y = O.step(prob, x, TAU, scheme, steps)
+        y = O.step(prob, x, tau, scheme, steps)
         dt = time.perf_counter() - t0
     finally:
         O.use_fft(False)
@@ -169,31 +172,53 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
+BATCH_TAU = 1e-3
+BATCH_SAMPLE = 4   # instances of the batched workload the oracle times per step
+
+
+def batch_config(scheme, inner):
+    probs = W.batch_1d()
+    return probs, {"workload": f"batch1d-256 uneven {scheme} tau=1e-3 (one persistent launch per call)",
+                   "instances": len(probs), "dof": int(sum(p.dof for p in probs)),
+                   "box_half_widths": "N1, N2 ~ U{16..512} (odd slice lengths 33..1025)", "scheme": scheme,
+                   "tau": BATCH_TAU, "time_steps_per_bench_step": inner,
+                   "l2_flush": "not needed: psi (540 MB) is larger than L2 (129 MB)"}
+
+
+def oracle_batch_sample(probs, steps, scheme="strang"):
+    """The oracle (FFT backend) on the first BATCH_SAMPLE instances of the
+    batched workload: (DOF-steps/s, seconds, DOF of the sample)."""
+    import oracle as O
+    dof, t = 0, 0.0
+    for p in probs[:BATCH_SAMPLE]:
+        x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+        _, dt, _ = oracle_step_rate(p, x, steps, scheme, BATCH_TAU)
+        t += dt
+        dof += p.dof
+    return dof * steps / t, t, dof
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import oracle as O
-    p = W.config_scale_1d()
-    x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+    probs, cfg = batch_config(args.scheme, args.inner)
     for _ in range(args.warmup):
-        oracle_step_rate(p, x, 1)
-    times = []
+        oracle_batch_sample(probs, 1, args.scheme)
+    tot, dof = 0.0, 0
     for _ in range(args.steps):
-        _, dt, x = oracle_step_rate(p, x, 1)
-        times.append(dt)
-    tot = sum(times)
-    val = p.dof * args.steps / tot
+        _, dt, dof = oracle_batch_sample(probs, 1, args.scheme)
+        tot += dt
+    val = dof * args.steps / tot
+    sample = (f"one {args.scheme} step of tau=1e-3 of the first {BATCH_SAMPLE} instances of the batched workload "
+              f"({dof} DOF) per bench step, FP64 NumPy oracle with its FFT transform backend")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "DOF-steps/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": "bilayer1d-2049x2049 strang tau=5e-4", "box": [2049, 2049],
-                   "scheme": "strang", "tau": TAU, "l2_flush": "n/a (host)"},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": val, "unit": "DOF-steps/s", "cores": cpu_threads(), "kind": "oracle",
-                         "sample": f"{args.steps} full Strang steps of the 2049x2049 box, FP64 NumPy "
-                                   "oracle with its FFT transform backend"},
+                         "sample": sample},
         "e2e": {"value": val, "unit": "DOF-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -205,6 +230,7 @@ def profile_case(args):
             2049 use the same convolution-form pass as the bench workload;
     2d    : the 64^4 twisted bilayer (134 MB), dedicated pass for 64 x 64 slices;
     batch : 64 uneven instances of the batched workload, one persistent launch;
+    batch256: the whole 256-instance batched workload (the headline);
     bench : the 2049 x 2049 bench workload itself (33.8 MB, L2-resident like
             the timed bench), one ls_step call of --steps steps."""
     import torch
@@ -212,14 +238,14 @@ def profile_case(args):
     G.build()
     import paper_2103_14897_gb300 as P
     kind = args.profile_case
-    if kind == "batch":
-        probs = W.batch_1d(count=64, seed=4)
+    if kind in ("batch", "batch256"):
+        probs = W.batch_1d(count=64 if kind == "batch" else 256, seed=4)
         b = P.Batch(probs, "c64")
         psi = b.empty()
         b.init_gaussian(psi, [0.0], 2.0, [1.0])
         b.step(psi, args.steps, 1e-3, args.scheme)
         torch.cuda.synchronize()
-        print(json.dumps({"workload": "batch1d-64", "steps": args.steps,
+        print(json.dumps({"workload": f"batch1d-{len(probs)}", "steps": args.steps,
                           "norm": b.observables(psi)[0]["norm"]}))
         return
     if kind == "2d":
@@ -351,6 +377,65 @@ def run_suite(args):
     return out
 
 
+def _event_time_ms(fn, calls, st, flush=None):
+    """Sum of CUDA-event durations (ms) of calls fn(k), k < calls, recorded on
+    stream st; flush (optional) is called before each, outside the events."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(calls)]
+    for k in range(calls):
+        if flush is not None:
+            flush(k)
+        ev[k][0].record(st)
+        fn(k)
+        ev[k][1].record(st)
+    torch.cuda.synchronize()
+    return float(sum(a.elapsed_time(b) for a, b in ev))
+
+
+def _hbm_roofline(bytes_per_launch, ms_per_launch, hbm, src, traffic, note):
+    achieved = bytes_per_launch / (ms_per_launch / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)", "note": note}
+
+
+def _traffic(key):
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            return json.load(f).get(key)
+    except Exception:
+        return None
+
+
+def sub_single(P, O, name, p, dtype, scheme, tau, inner, calls, hbm, src, flush, st, x0, k0):
+    """Secondary single-context workload: DOF-steps/s, its own HBM roofline
+    (48 B per DOF-step for Strang) and a one-step accuracy check."""
+    ctx = P.Context(p, dtype)
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, x0, 2.0, k0)
+    x = ctx.to_dense(psi)
+    chk = ctx.from_dense(x)
+    ctx.step(chk, 1, tau, scheme)
+    O.use_fft(True)
+    try:
+        ref = O.step(p, x, tau, scheme, 1)
+    finally:
+        O.use_fft(False)
+    err = float(np.linalg.norm(ctx.to_dense(chk) - ref) / np.linalg.norm(ref))
+    for k in range(3):
+        ctx.step(psi, inner, tau, scheme, step0=k * inner)
+    t = _event_time_ms(lambda k: ctx.step(psi, inner, tau, scheme, step0=k * inner), calls, st, flush)
+    npass = {"lie": 2, "strang_kp": 2}.get(scheme, 3)
+    esz = 8 if dtype == "c64" else 16
+    out = {"workload": name, "dof": p.dof, "dtype": dtype, "scheme": scheme, "tau": tau,
+           "value": p.dof * inner * calls / (t / 1e3), "unit": "DOF-steps/s", "ms_per_time_step": t / calls / inner,
+           "rel_l2_1step_vs_oracle": err, "norm_minus_1": ctx.observables(psi)["norm"] - 1.0}
+    out["roofline"] = _hbm_roofline(2 * esz * npass * p.dof * inner, t / calls, hbm, src, None,
+                                    f"{npass} slice passes of {2 * esz} B per DOF per time step; one ls_step "
+                                    f"call of {inner} steps is one graph launch")
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -365,132 +450,108 @@ def run_ours(args):
     import oracle as O
     import paper_2103_14897_gb300 as P
 
-    p = W.config_scale_1d()
-    scheme = args.scheme
-    ctx = P.Context(p, "c64")
-    psi = ctx.empty()
-    ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    scheme, NI = args.scheme, args.inner
+    probs, cfg = batch_config(scheme, NI)
+    dof = cfg["dof"]
+    cfg["parallelism"] = "replicas" if world > 1 else "single"
     st = torch.cuda.current_stream()
+    hbm, src = peaks()
 
-    # accuracy gate: one step against the oracle (FFT backend), FP64 reference
-    x0 = O.gaussian_packet(p, [0.0], 2.0, [1.0])
-    chk = ctx.from_dense(x0)
-    ctx.step(chk, 1, TAU, scheme, seed=7)
+    b = P.Batch(probs, "c64")
+    psi = b.empty()
+    b.init_gaussian(psi, [0.0], 2.0, [1.0])
+
+    # accuracy gate: one step of the whole batch, sampled instances against the oracle
+    chk = b.empty()
+    b.init_gaussian(chk, [0.0], 2.0, [1.0])
+    b.step(chk, 1, BATCH_TAU, scheme, seed=7)
+    sample = [0, 1, 2, 3, 64, 128, 200, 255]
+    errs = []
     O.use_fft(True)
     try:
-        ref1 = O.step(p, x0, TAU, scheme, 1, seed=7)
+        for i in sample:
+            p = probs[i]
+            ref = O.step(p, O.gaussian_packet(p, [0.0], 2.0, [1.0]), BATCH_TAU, scheme, 1, seed=7 + i)
+            got = b.get_dense(chk, i)
+            errs.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
     finally:
         O.use_fft(False)
-    got1 = ctx.to_dense(chk)
-    relerr = float(np.linalg.norm(got1 - ref1) / np.linalg.norm(ref1))
+    relerr = max(errs)
     del chk
 
-    NI = args.inner
     for k in range(args.warmup):
-        ctx.step(psi, NI, TAU, scheme, seed=7, step0=k * NI)
+        b.step(psi, NI, BATCH_TAU, scheme, seed=7, step0=k * NI)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(lr) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(st)
-            ctx.step(psi, NI, TAU, scheme, seed=7, step0=(args.warmup + k) * NI)
-            ev[k][1].record(st)
-        torch.cuda.synchronize()
+        t_ms = _event_time_ms(lambda k: b.step(psi, NI, BATCH_TAU, scheme, seed=7, step0=(args.warmup + k) * NI),
+                              args.steps, st)
     if world > 1:
         dist.barrier()
-    per = [a.elapsed_time(b) for a, b in ev]
-    t_ms = reduce_job_time(float(sum(per)), world, "cuda")
-    # one-time-step calls (no cross-step fusion), for reference
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t1 = 0.0
-    for k in range(20):
-        flush.fill_(float(k))
-        e0.record(st)
-        ctx.step(psi, 1, TAU, scheme, seed=7, step0=k)
-        e1.record(st)
-        torch.cuda.synchronize()
-        t1 += e0.elapsed_time(e1)
-    single_call = p.dof * 20 / (t1 / 1e3)
-    obs = ctx.observables(psi)
-    value = job_value(p.dof, args.steps * NI, world, t_ms)
+    t_ms = reduce_job_time(t_ms, world, "cuda")
+    value = job_value(dof, args.steps * NI, world, t_ms)
+    obs = b.observables(psi)
+    norm_err = max(abs(o["norm"] - 1.0) for o in obs)
 
-    # plain FP64 GPU form (same kernels in complex128)
-    ctx64 = P.Context(p, "c128")
-    psi64 = ctx64.empty()
-    ctx64.init_gaussian(psi64, [0.0], 2.0, [1.0])
-    for _ in range(2):
-        ctx64.step(psi64, NI, TAU, scheme)
-    n64 = 3
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t64 = 0.0
-    for k in range(n64):
-        flush.fill_(float(k))
-        e0.record(st)
-        ctx64.step(psi64, NI, TAU, scheme)
-        e1.record(st)
-        torch.cuda.synchronize()
-        t64 += e0.elapsed_time(e1)
-    fp64_value = p.dof * NI * n64 / (t64 / 1e3)
-    del psi64, ctx64
+    # the persistent batched kernel is the only kernel of a deterministic call
+    # (one graph launch: a counter reset and the kernel)
+    npass = {"lie": 2, "strang_kp": 2}.get(scheme.replace("_stoch", ""), 3)
+    roof = _hbm_roofline(16 * npass * dof * NI, t_ms / args.steps, hbm, src, _traffic(f"batch_kernel:{scheme}"),
+                         f"batch_kernel: {npass} slice passes of 16 B per DOF per time step over {dof} DOF, "
+                         f"{NI} time steps per launch; duration from CUDA events around each launch")
+
+    # plain FP64 GPU form of the same batch
+    b64 = P.Batch(probs, "c128")
+    psi64 = b64.empty()
+    b64.init_gaussian(psi64, [0.0], 2.0, [1.0])
+    b64.step(psi64, NI, BATCH_TAU, scheme, seed=7)
+    t64 = _event_time_ms(lambda k: b64.step(psi64, NI, BATCH_TAU, scheme, seed=7, step0=(k + 1) * NI), 2, st)
+    fp64_value = dof * NI * 2 / (t64 / 1e3)
+    del psi64, b64
 
     # end to end through the C ABI with host buffers (pinned)
-    host = torch.empty((ctx.rows, ctx.pitch), dtype=torch.complex64, pin_memory=True)
+    host = torch.empty(psi.numel(), dtype=psi.dtype, pin_memory=True)
     host.copy_(psi)
     nbytes = host.numel() * host.element_size()
-    dev = ctx.empty()
-    ne = max(3, args.steps // 2)
-    ctx.step(dev, NI, TAU, scheme, seed=7, step0=0)  # graph for this buffer
+    dev = b.empty()
+    b.step_host(host, dev, NI, BATCH_TAU, scheme, seed=7, step0=0)
+    ne = max(3, args.steps // 4)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(ne):
-        dev.copy_(host, non_blocking=True)
-        ctx.step(dev, NI, TAU, scheme, seed=7, step0=k * NI)
-        host.copy_(dev, non_blocking=True)
-    torch.cuda.synchronize()
+        b.step_host(host, dev, NI, BATCH_TAU, scheme, seed=7, step0=(k + 1) * NI)
     te = time.perf_counter() - t0
-    e2e = world * p.dof * NI * ne / te
-
-    # roofline of the pass kernel: every launch in a step is a pass (3 for
-    # Strang, 2 for Lie / kinetic-potential Strang).  The pass is FFT work on
-    # an L2-resident array, bound by FP32 issue, so the roofline is "alu":
-    # algorithmic flops per launch = slices x (10 N log2 N + 6 N + 12 q) for the
-    # convolution form (two complex FFTs of N at 5 N log2 N each, the kernel
-    # product, and the kinetic phase / correction arithmetic of q elements),
-    # against the FP32 FMA peak 152 SMs x 128 lanes x 2 flop x SM clock.
-    # every launch is a pass kernel; a fused launch applies two layer factors.
-    # Layer factors per call: 3 n (Strang) or 2 n (Lie, kinetic/potential Strang).
-    nfac = (3 if scheme in ("strang", "strang_stoch") else 2) * NI
-    nlaunch = (2 * NI + 1) if scheme == "strang" else nfac
-    hbm, src = peaks()
-    ms_factor = t_ms / args.steps / nfac
-    q = p.q1[0]
-    nfft = 1 << (2 * q - 3).bit_length() if q & (q - 1) else q
-    flops = p.M2 * (10 * nfft * math.log2(nfft) + 6 * nfft + 12 * q)
-    clk_peak = sm_max_mhz()
-    alu_peak = 152 * 128 * 2 * clk_peak * 1e6 / 1e12
-    achieved = flops / (ms_factor / 1e3) / 1e12
-    algo_bytes = BYTES_PER_DOF_PASS * p.dof
-    hbm_achieved = algo_bytes / (ms_factor / 1e3) / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            traffic = json.load(f).get(f"pass_fast_kernel:{scheme}")
-    except Exception:
-        pass
+    e2e = world * dof * NI * ne / te
+    del dev, host
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        xs = O.gaussian_packet(p, [0.0], 2.0, [1.0])
-        rate, dt, _ = oracle_step_rate(p, xs, args.cpu_steps, scheme)
+        rate, dt, sdof = oracle_batch_sample(probs, args.cpu_steps, scheme)
         cpu = {"value": rate, "unit": "DOF-steps/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{args.cpu_steps} full {scheme} steps of the 2049x2049 box ({dt:.1f} s), "
-                         "FP64 NumPy oracle, FFT transform backend"}
+               "sample": f"{args.cpu_steps} {scheme} steps of the first {BATCH_SAMPLE} instances ({sdof} DOF, "
+                         f"{dt:.1f} s), FP64 NumPy oracle with its FFT transform backend"}
+
+    subs = {}
+    if not args.no_sub:
+        flush_buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        fl = lambda k: flush_buf.fill_(float(k))  # noqa: E731
+        subs["bilayer1d-2049x2049"] = sub_single(
+            P, O, "bilayer1d-2049x2049 strang tau=5e-4 (33.8 MB, L2-resident; 512 MB L2 flush between calls)",
+            W.config_scale_1d(), "c64", "strang", TAU, 20, 10, hbm, src, fl, st, [0.0], [1.0])
+        subs["twisted2d-64^4"] = sub_single(
+            P, O, "twisted2d-64^4 strang tau=1e-3 (134 MB)", W.twisted_2d(q=64), "c64", "strang", 1e-3, 5, 10,
+            hbm, src, None, st, [0.0, 0.0], [1.0, 0.0])
+        del flush_buf
+        bs = P.Batch(probs, "c64")
+        ps = bs.empty()
+        bs.init_gaussian(ps, [0.0], 2.0, [1.0])
+        bs.step(ps, NI, BATCH_TAU, "strang_stoch", seed=3)
+        ts = _event_time_ms(lambda k: bs.step(ps, NI, BATCH_TAU, "strang_stoch", seed=3, step0=(k + 1) * NI), 5, st)
+        subs["batch1d-256-strang_stoch"] = {"value": dof * NI * 5 / (ts / 1e3), "unit": "DOF-steps/s",
+                                            "note": "1/8 of the slices per sub-step (Algorithm 4), lazy kinetic phases"}
+        del ps, bs
 
     if rank == 0:
         line = {
@@ -498,31 +559,17 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "ms_per_time_step": t_ms / args.steps / NI,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
-            "data": "synthetic",
-            "config": {"workload": f"bilayer1d-2049x2049 {scheme} tau=5e-4", "box": [2049, 2049],
-                       "dof": p.dof, "scheme": scheme, "tau": TAU, "time_steps_per_bench_step": NI,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2_flush": "512 MB buffer written between timed steps"},
-            "accuracy": {"rel_l2_1step_vs_oracle": relerr, "norm_minus_1": obs["norm"] - 1.0,
-                         "gate_rel_l2": 1e-5, "pass": relerr <= 1e-5},
+            "data": "synthetic", "config": cfg,
+            "accuracy": {"rel_l2_1step_vs_oracle_max": relerr, "instances_checked": sample,
+                         "norm_minus_1_max": norm_err, "gate_rel_l2": 1e-5, "pass": relerr <= 1e-5},
+            "roofline": roof,
             "fp64_gpu": {"value": fp64_value, "unit": "DOF-steps/s", "dtype": "c128",
                          "speedup_fp32_over_fp64": value / world / fp64_value},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": traffic,
-                         "note": f"the 1D pass kernels (fused layer-1 pass_fast_kernel, two-column layer-2 "
-                                 f"pass_fast_pair_kernel; convolution form, N={nfft}): {flops:.3e} algorithmic "
-                                 f"flops per layer factor, {ms_factor * 1e3:.1f} us per factor averaged over the "
-                                 f"{nlaunch} launches of a {NI}-step call (a fused launch applies two factors); "
-                                 f"FP32 peak derived from 152 SMs x 128 lanes x 2 x {clk_peak:.0f} MHz"},
-            "hbm_roofline": {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s", "frac": hbm_achieved / hbm,
-                             "algorithmic_bytes_per_launch": algo_bytes, "peak_source": f"{src} (MEASURED_PEAKS.json)",
-                             "note": "psi (33.8 MB) is L2-resident between passes"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e, "unit": "DOF-steps/s", "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes},
-            "gpu_launches": nlaunch * args.steps,
-            "single_step_calls": {"value": single_call, "unit": "DOF-steps/s",
-                                  "note": "ls_step(n=1) per call: no cross-step pass fusion"},
+            "e2e": {"value": e2e, "unit": "DOF-steps/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "note": "ls_batch_step_host: pinned host buffer in, steps, host buffer out, per bench step"},
+            "gpu_launches": args.steps,
+            "sub_workloads": subs,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
@@ -533,16 +580,17 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50,
-                    help="timed bench steps; each is one ls_step call of --inner time steps")
-    ap.add_argument("--inner", type=int, default=20, help="time steps per ls_step call")
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed bench steps; each is one ls_batch_step call of --inner time steps")
+    ap.add_argument("--inner", type=int, default=10, help="time steps per call")
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scheme", default="strang")
-    ap.add_argument("--cpu-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--suite", action="store_true", help="throughput lines of the secondary workloads")
-    ap.add_argument("--profile-case", choices=["1d", "2d", "batch", "bench"], default=None,
+    ap.add_argument("--profile-case", choices=["1d", "2d", "batch", "batch256", "bench"], default=None,
                     help="run an ncu target (array larger than L2) instead of the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:

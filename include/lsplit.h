@@ -100,6 +100,13 @@ enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_
  *   nv2, v2_h, v2_c  same for v_2
  *   dtype         LS_C64 (complex float, FP64 phase arithmetic) or LS_C128
  *   frac_den      stochastic sampling denominator (p = max(1, S/frac_den)), >= 1
+ *   mask_mode     LS_MASK_INIT_ONLY (0): the joint cutoff shapes the initial
+ *                 state and the ls_index_set query only, and the whole box is
+ *                 evolved; LS_MASK_PROJECT_EACH_STEP (1): ls_step also zeroes
+ *                 every coefficient outside the joint cutoff after each full
+ *                 time step (the truncated index set of Sec. 3 enforced during
+ *                 the evolution).  The projection is not unitary: ls_adjoint
+ *                 and the batched runner return LS_ERR_INVALID for it.
  * Supported slice shapes: 1D any length (powers of two use a direct radix FFT,
  * others a Bluestein transform of power-of-two length >= 2q-2, at most 8192
  * for LS_C64 and 4096 for LS_C128; ls_create returns LS_ERR_INVALID beyond);
@@ -119,7 +126,10 @@ typedef struct ls_problem {
   const double* v2_c;
   int32_t dtype;
   int32_t frac_den;
+  int32_t mask_mode;
 } ls_problem;
+
+enum { LS_MASK_INIT_ONLY = 0, LS_MASK_PROJECT_EACH_STEP = 1 };
 
 /* Observables (Eq. (2.4)-(2.5) in the lifted basis, Eq. (3.2) orthonormality),
  * all accumulated in FP64:
@@ -169,9 +179,19 @@ int ls_init_gaussian(ls_ctx* ctx, void* psi_dev, const double* x0_host, double w
  * factors_per_step + factor index).  Adjacent kinetic factors are merged; each
  * layer factor is one fused pass over the array.  Stochastic schemes apply
  * kinetic factors lazily and finish with a settle pass, so psi_dev is complete
- * on return.  Enqueued on stream (replays a cached CUDA graph). */
+ * on return.  With LS_MASK_PROJECT_EACH_STEP every step ends with the
+ * projection onto the joint cutoff.  Enqueued on stream (replays a cached CUDA
+ * graph, one per (psi_dev, scheme, tau, nsteps); the graphs keep the tables
+ * they use alive, and the table caches are bounded). */
 int ls_step(ls_ctx* ctx, void* psi_dev, int64_t nsteps, double tau, int32_t scheme,
             uint64_t seed, uint64_t step0, void* stream);
+
+/* End to end from host memory: copy psi_host (ls_layout()'s bytes; pinned
+ * host memory makes the copies asynchronous DMA) into the caller's device
+ * buffer psi_dev, run ls_step on it, copy the result back into psi_host and
+ * synchronise the stream.  Same arguments and errors as ls_step. */
+int ls_step_host(ls_ctx* ctx, void* psi_host, void* psi_dev, int64_t nsteps, double tau, int32_t scheme,
+                 uint64_t seed, uint64_t step0, void* stream);
 
 /* Observables of psi_dev (and overlap with chi_dev if not NULL).  Synchronises
  * the stream and writes *out (host). */
@@ -183,9 +203,10 @@ int ls_observables(ls_ctx* ctx, const void* psi_dev, const void* chi_dev, ls_obs
  *   psi(x_j) = sum_{m,n} phi[n][m] exp(i (B1 m + B2 n) . x_j),  j < nx.
  * x_host: nx points of d doubles each; out_host: 2 nx doubles (re, im per
  * point).  The phases are exact (64-bit fixed-point turns); the sum over m
- * runs in the context's precision, the sum over n in FP64.  Allocates
- * temporary device buffers of about nx (M1 + 2 M2) complex elements and
- * synchronises the stream.  LS_ERR_INVALID for nx beyond 2^22. */
+ * runs in the context's precision, the sum over n in FP64.  The points are
+ * processed in chunks whose temporary device buffers (chunk * (M1 + 2 M2)
+ * complex elements) stay below 512 MB; synchronises the stream.
+ * LS_ERR_INVALID for nx beyond 2^22. */
 int ls_density(ls_ctx* ctx, const void* psi_dev, const double* x_host, int64_t nx, double* out_host,
                void* stream);
 
@@ -206,11 +227,16 @@ int ls_samples(ls_ctx* ctx, int32_t layer, uint64_t seed, uint64_t g0, int32_t c
  * gradients; grad_c1_host / grad_c2_host (2*nv doubles, may be NULL) receive
  * (dL/dRe vhat_h, dL/dIm vhat_h) for every coefficient.  On return psi_dev
  * holds the rebuilt phi_0 and lam_dev the gradient with respect to
- * conj(phi_0).  Schemes LS_LIE, LS_STRANG, LS_STRANG_KP and LS_YOSHIDA4
- * (otherwise LS_ERR_INVALID).  Synchronises the stream. */
+ * conj(phi_0).  Schemes LS_LIE, LS_STRANG, LS_STRANG_KP, LS_YOSHIDA4 and the
+ * stochastic LS_LIE_STOCH and LS_STRANG_STOCH (Algorithm 4): seed and step0
+ * must be those of the forward ls_step call, which fix the sampled slices;
+ * a sampled factor of duration s acts with duration s*S/p and contributes
+ * 2 (s*S/p) Im(conj(mu_p) psi_p) over its sampled slices.  seed and step0 are
+ * ignored by the deterministic schemes.  Other schemes, and contexts with
+ * LS_MASK_PROJECT_EACH_STEP, return LS_ERR_INVALID.  Synchronises the stream. */
 int ls_adjoint(ls_ctx* ctx, void* psi_dev, void* lam_dev, int64_t nsteps, double tau,
-               int32_t scheme, double* grad_v1_host, double* grad_v2_host,
-               double* grad_c1_host, double* grad_c2_host, void* stream);
+               int32_t scheme, uint64_t seed, uint64_t step0, double* grad_v1_host,
+               double* grad_v2_host, double* grad_c1_host, double* grad_c2_host, void* stream);
 
 /* ---- batched uneven instances (one persistent launch per call) ----
  * A batch is a set of independent problems (same dtype, any boxes) whose wave
@@ -239,6 +265,11 @@ int ls_batch_init_gaussian(ls_batch* batch, void* psi_dev, const double* x0_host
  * expired (psi is then incomplete; the batch stays usable). */
 int ls_batch_step(ls_batch* batch, void* psi_dev, int64_t nsteps, double tau, int32_t scheme,
                   uint64_t seed, uint64_t step0, void* stream);
+/* ls_batch_step from host memory: psi_host (offsets[count] elements, the
+ * ls_batch_layout() layout) is copied into the caller's device buffer
+ * psi_dev, advanced, and copied back; synchronises.  Errors as ls_batch_step. */
+int ls_batch_step_host(ls_batch* batch, void* psi_host, void* psi_dev, int64_t nsteps, double tau,
+                       int32_t scheme, uint64_t seed, uint64_t step0, void* stream);
 /* ls_observables for every instance; out: count ls_obs (host).  Synchronises. */
 int ls_batch_observables(ls_batch* batch, const void* psi_dev, ls_obs* out_host, void* stream);
 /* Wait budget of one dependency wait (seconds, default 1) and a test hook that
@@ -247,10 +278,10 @@ int ls_batch_observables(ls_batch* batch, const void* psi_dev, ls_obs* out_host,
 int ls_batch_debug(ls_batch* batch, int32_t unmet_dependency, double timeout_seconds);
 
 /* Mass N = sum |phi|^2 (FP64) of a wave-function array, computed WITHOUT
- * allocating memory: for callers that cannot call cudaMalloc (work issued while
- * a stream is captured into a CUDA graph, hosts that own all device memory
- * through their own pool, loops that must not touch the allocator).  The paper
- * has no counterpart; the same quantity is ls_observables()->norm.
+ * allocating memory: for callers that cannot call cudaMalloc (hosts that hand
+ * out all device memory from their own pool and forbid other allocations, and
+ * loops that must not pay for or wait on the allocator).  The paper has no
+ * counterpart; the same quantity is ls_observables()->norm.
  *   psi_dev   device array, rows x cols used elements, row pitch `pitch`
  *             elements (the ls_layout() layout: rows = M2, cols = M1)
  *   dtype     LS_C64 or LS_C128

@@ -19,14 +19,16 @@ LIB_PATH = os.path.join(HERE, "_lib", "liblsplit.so")
 
 LS_OK, LS_ERR_INVALID, LS_ERR_NOMEM, LS_ERR_CUDA, LS_ERR_TIMEOUT, LS_ERR_STATE = 0, -1, -2, -3, -4, -5
 LS_C64, LS_C128 = 0, 1
+MASK_MODES = {"init_only": 0, "project": 1}
 SCHEMES = {"lie": 0, "strang": 1, "strang_kp": 2, "lie_stoch": 3, "strang_stoch": 4, "yoshida4": 5, "cn_strang": 6,
            "semi_implicit": 7, "random_batch": 8}
 
 # Every entry point declared in include/lsplit.h.
 EXPORTS = ["ls_last_error", "ls_create", "ls_destroy", "ls_layout", "ls_index_set",
-           "ls_init_gaussian", "ls_step", "ls_observables", "ls_density", "ls_samples", "ls_adjoint",
-           "ls_mass_noalloc", "ls_batch_create", "ls_batch_destroy", "ls_batch_layout",
-           "ls_batch_init_gaussian", "ls_batch_step", "ls_batch_observables", "ls_batch_debug"]
+           "ls_init_gaussian", "ls_step", "ls_step_host", "ls_observables", "ls_density", "ls_samples",
+           "ls_adjoint", "ls_mass_noalloc", "ls_batch_create", "ls_batch_destroy", "ls_batch_layout",
+           "ls_batch_init_gaussian", "ls_batch_step", "ls_batch_step_host", "ls_batch_observables",
+           "ls_batch_debug"]
 
 
 class LsProblem(C.Structure):
@@ -41,6 +43,7 @@ class LsProblem(C.Structure):
         ("nv2", C.c_int32), ("v2_h", C.POINTER(C.c_int32)), ("v2_c", C.POINTER(C.c_double)),
         ("dtype", C.c_int32),
         ("frac_den", C.c_int32),
+        ("mask_mode", C.c_int32),
     ]
 
 
@@ -78,9 +81,11 @@ def load_library(path: str = LIB_PATH):
     lib.ls_density.argtypes = [vp, vp, C.POINTER(C.c_double), i64, C.POINTER(C.c_double), vp]
     lib.ls_init_gaussian.argtypes = [vp, vp, C.POINTER(dbl), dbl, C.POINTER(dbl), vp]
     lib.ls_step.argtypes = [vp, vp, i64, dbl, i32, u64, u64, vp]
+    lib.ls_step_host.argtypes = [vp, vp, vp, i64, dbl, i32, u64, u64, vp]
+    lib.ls_batch_step_host.argtypes = [vp, vp, vp, i64, dbl, i32, u64, u64, vp]
     lib.ls_observables.argtypes = [vp, vp, vp, C.POINTER(LsObs), vp]
     lib.ls_samples.argtypes = [vp, i32, u64, u64, i32, C.POINTER(i32), C.POINTER(i32), vp]
-    lib.ls_adjoint.argtypes = [vp, vp, vp, i64, dbl, i32, C.POINTER(dbl), C.POINTER(dbl),
+    lib.ls_adjoint.argtypes = [vp, vp, vp, i64, dbl, i32, u64, u64, C.POINTER(dbl), C.POINTER(dbl),
                                C.POINTER(dbl), C.POINTER(dbl), vp]
     lib.ls_mass_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp]
     lib.ls_batch_create.argtypes = [C.POINTER(LsProblem), i32, C.POINTER(vp)]
@@ -121,7 +126,7 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
-def make_problem_struct(prob, dtype: str = "c64", frac_den: int = 8):
+def make_problem_struct(prob, dtype: str = "c64", frac_den: int = 8, mask_mode: str = "init_only"):
     """Convert a workloads.Problem-like object to the C struct (and keep the
     coefficient arrays alive by returning them too)."""
     s = LsProblem()
@@ -150,18 +155,21 @@ def make_problem_struct(prob, dtype: str = "c64", frac_den: int = 8):
             s.nv2, s.v2_h, s.v2_c = len(cc), hp, cp
     s.dtype = LS_C64 if dtype == "c64" else LS_C128
     s.frac_den = int(frac_den)
+    s.mask_mode = MASK_MODES[mask_mode]
     return s, keep
 
 
 class Context:
-    """One lifted problem on the current CUDA device (ls_create / ls_destroy)."""
+    """One lifted problem on the current CUDA device (ls_create / ls_destroy).
+    mask_mode: "init_only" (the joint cutoff shapes the initial state only) or
+    "project" (every step ends with the projection onto the cutoff)."""
 
-    def __init__(self, prob, dtype: str = "c64", frac_den: int = 8):
+    def __init__(self, prob, dtype: str = "c64", frac_den: int = 8, mask_mode: str = "init_only"):
         lib = load_library()
         self.prob = prob
         self.dtype = dtype
         self.frac_den = frac_den
-        st, keep = make_problem_struct(prob, dtype, frac_den)
+        st, keep = make_problem_struct(prob, dtype, frac_den, mask_mode)
         h = C.c_void_p()
         _check(lib.ls_create(C.byref(st), C.byref(h)))
         self._h = h
@@ -217,6 +225,15 @@ class Context:
         _check(_lib.ls_step(self._h, _ptr(psi), int(nsteps), float(tau), SCHEMES[scheme],
                             int(seed) & (2 ** 64 - 1), int(step0), _stream_handle(stream)))
 
+    def step_host(self, host, dev, nsteps: int, tau: float, scheme: str = "strang", seed: int = 0,
+                  step0: int = 0, stream=None):
+        """ls_step_host: host -> dev, step, dev -> host (host: a CPU tensor of the
+        context layout, ideally pinned; dev: a device tensor of the same shape)."""
+        if host.is_cuda or host.numel() != dev.numel() or host.dtype != dev.dtype:
+            raise ValueError("host must be a CPU tensor matching dev")
+        _check(_lib.ls_step_host(self._h, host.data_ptr(), _ptr(dev), int(nsteps), float(tau), SCHEMES[scheme],
+                                 int(seed) & (2 ** 64 - 1), int(step0), _stream_handle(stream)))
+
     def density(self, psi, x, stream=None) -> np.ndarray:
         """psi(x_j) at real-space points x ((npts,) for 1D boxes, (npts, 2)
         for 2D boxes), complex128 array."""
@@ -245,13 +262,15 @@ class Context:
         assert pc.value == p
         return out[:count]
 
-    def adjoint(self, psi, lam, nsteps: int, tau: float, scheme: str = "strang", stream=None):
+    def adjoint(self, psi, lam, nsteps: int, tau: float, scheme: str = "strang", seed: int = 0, step0: int = 0,
+                stream=None):
         g1 = np.zeros(self.M1)
         g2 = np.zeros(self.M2)
         c1 = np.zeros(2 * len(self.prob.v1_c))
         c2 = np.zeros(2 * len(self.prob.v2_c))
         P = C.POINTER(C.c_double)
         _check(_lib.ls_adjoint(self._h, _ptr(psi), _ptr(lam), int(nsteps), float(tau), SCHEMES[scheme],
+                               int(seed) & (2 ** 64 - 1), int(step0),
                                g1.ctypes.data_as(P), g2.ctypes.data_as(P),
                                c1.ctypes.data_as(P) if len(c1) else None,
                                c2.ctypes.data_as(P) if len(c2) else None, _stream_handle(stream)))
@@ -328,6 +347,14 @@ class Batch:
     def step(self, psi, nsteps, tau, scheme="strang", seed=0, step0=0, stream=None):
         _check(_lib.ls_batch_step(self._h, _ptr(psi), int(nsteps), float(tau), SCHEMES[scheme],
                                   int(seed) & (2 ** 64 - 1), int(step0), _stream_handle(stream)))
+
+    def step_host(self, host, dev, nsteps, tau, scheme="strang", seed=0, step0=0, stream=None):
+        """ls_batch_step_host: host -> dev, nsteps steps, dev -> host."""
+        if host.is_cuda or host.numel() != dev.numel() or host.dtype != dev.dtype:
+            raise ValueError("host must be a CPU tensor matching dev")
+        _check(_lib.ls_batch_step_host(self._h, host.data_ptr(), _ptr(dev), int(nsteps), float(tau),
+                                       SCHEMES[scheme], int(seed) & (2 ** 64 - 1), int(step0),
+                                       _stream_handle(stream)))
 
     def observables(self, psi, stream=None):
         out = (LsObs * len(self.probs))()

@@ -137,6 +137,18 @@ struct ConvTab {
   double fix_re = 0, fix_im = 0;
 };
 
+// A cached device table with its last-use tick (least recently used entries
+// are evicted beyond kTableCacheCap per cache; graphs and calls in flight keep
+// their own references, so eviction never frees a table still in use).
+struct CachedTab {
+  std::shared_ptr<DevBuf> buf;
+  double fix_re = 0, fix_im = 0;
+  uint64_t used = 0;
+};
+constexpr size_t kTableCacheCap = 48;
+
+using TableKeep = std::vector<std::shared_ptr<DevBuf>>;
+
 struct GraphEntry {
   void* psi;
   int scheme;
@@ -144,6 +156,7 @@ struct GraphEntry {
   int64_t n;
   cudaGraphExec_t exec = nullptr;
   std::shared_ptr<DevBuf> lists;
+  TableKeep tables;  // every table the captured kernels read
   ~GraphEntry() {
     if (exec) cudaGraphExecDestroy(exec);
   }
@@ -172,9 +185,13 @@ struct ls_ctx {
   int fast_variant = 0;   // shared-buffer / register-budget variant of the fast pass
   DevBuf tw[2], twb[2], bm[2], bp[2], chirp[2], vgrid[2];
   std::vector<double> vhost[2];
-  std::map<std::pair<int, uint64_t>, std::shared_ptr<DevBuf>> ttab;  // (layer, bits(s)) -> table
-  std::map<std::pair<int, uint64_t>, ConvTab> ctab;                   // convolution-form tables
+  std::map<std::pair<int, uint64_t>, CachedTab> ttab;  // (layer, bits(s)) -> (T - 1)/M table
+  std::map<std::pair<int, uint64_t>, CachedTab> ctab;  // convolution-form tables
+  uint64_t tab_clock = 0;
+  TableKeep* keep = nullptr;  // set while a graph or call is built: receives every table it uses
   bool conv_form[2] = {false, false};
+  int mask_mode = LS_MASK_INIT_ONLY;
+  DevBuf maskbuf;   // joint-cutoff mask (M2 x M1 bytes), built on the first projecting step
   DevBuf partials, result, touch_row, touch_col, seedbuf, grad[2];
   DevBuf scratch;   // second state array of the out-of-place semi-implicit step (allocated on first use)
   int nblk_elem = 0;
@@ -256,12 +273,27 @@ std::vector<cd> bluestein_kernel(int q, int np, double sign) {
   return b;
 }
 
+// Least recently used entry of a table cache beyond its capacity is dropped
+// (its buffer lives on while a graph or a call still holds a reference).
+void evict_tables(std::map<std::pair<int, uint64_t>, CachedTab>& m) {
+  while (m.size() > kTableCacheCap) {
+    auto old = m.begin();
+    for (auto it = m.begin(); it != m.end(); ++it)
+      if (it->second.used < old->second.used) old = it;
+    m.erase(old);
+  }
+}
+
 const void* phase_table(ls_ctx* c, int layer, double s) {
   uint64_t bits;
   std::memcpy(&bits, &s, 8);
   auto key = std::make_pair(layer, bits);
   auto it = c->ttab.find(key);
-  if (it != c->ttab.end()) return it->second->p;
+  if (it != c->ttab.end()) {
+    it->second.used = ++c->tab_clock;
+    if (c->keep) c->keep->push_back(it->second.buf);
+    return it->second.buf->p;
+  }
   const std::vector<double>& v = c->vhost[layer - 1];
   const double M = (double)v.size();
   // (exp(-i s v) - 1) / M = -2 i sin(s v / 2) exp(-i s v / 2) / M (no cancellation)
@@ -272,7 +304,12 @@ const void* phase_table(ls_ctx* c, int layer, double s) {
   }
   auto buf = std::make_shared<DevBuf>();
   upload_c(c, *buf, T);
-  c->ttab[key] = buf;
+  CachedTab e;
+  e.buf = buf;
+  e.used = ++c->tab_clock;
+  c->ttab[key] = e;
+  if (c->keep) c->keep->push_back(buf);
+  evict_tables(c->ttab);
   return buf->p;
 }
 
@@ -281,14 +318,20 @@ const void* phase_table(ls_ctx* c, int layer, double s) {
 // (FP64, exact integer-reduced angles), wrapped into N entries (d >= 0 at d,
 // d < 0 at N + d; with N = 2q - 2 index q - 1 keeps c'_{q-1}), then
 // Khat = FFT_N / N.
-const ConvTab& conv_table(ls_ctx* c, int layer, double s);
-
-const ConvTab& conv_table(ls_ctx* c, int layer, double s) {
+ConvTab conv_table(ls_ctx* c, int layer, double s) {
   uint64_t bits;
   std::memcpy(&bits, &s, 8);
   auto key = std::make_pair(layer, bits);
   auto it = c->ctab.find(key);
-  if (it != c->ctab.end()) return it->second;
+  if (it != c->ctab.end()) {
+    it->second.used = ++c->tab_clock;
+    if (c->keep) c->keep->push_back(it->second.buf);
+    ConvTab t;
+    t.khat = it->second.buf;
+    t.fix_re = it->second.fix_re;
+    t.fix_im = it->second.fix_im;
+    return t;
+  }
   const std::vector<double>& v = c->vhost[layer - 1];
   const int q = (int)v.size();
   const int N = c->geom[layer - 1].np;
@@ -321,7 +364,15 @@ const ConvTab& conv_table(ls_ctx* c, int layer, double s) {
   for (auto& x : K) x /= (double)N;
   t.khat = std::make_shared<DevBuf>();
   upload_c(c, *t.khat, K);
-  return c->ctab[key] = t;
+  CachedTab e;
+  e.buf = t.khat;
+  e.fix_re = t.fix_re;
+  e.fix_im = t.fix_im;
+  e.used = ++c->tab_clock;
+  c->ctab[key] = e;
+  if (c->keep) c->keep->push_back(t.khat);
+  evict_tables(c->ctab);
+  return t;
 }
 
 // Kinetic fixed-point coefficients for one unit of duration u: phase in turns
@@ -362,6 +413,8 @@ int validate(const ls_problem* p) {
   if (p->d != 1 && p->d != 2) return fail(LS_ERR_INVALID, "d must be 1 or 2");
   if (p->dtype != LS_C64 && p->dtype != LS_C128) return fail(LS_ERR_INVALID, "dtype must be LS_C64 or LS_C128");
   if (p->frac_den < 1) return fail(LS_ERR_INVALID, "frac_den must be >= 1");
+  if (p->mask_mode != LS_MASK_INIT_ONLY && p->mask_mode != LS_MASK_PROJECT_EACH_STEP)
+    return fail(LS_ERR_INVALID, "mask_mode must be LS_MASK_INIT_ONLY or LS_MASK_PROJECT_EACH_STEP");
   for (int i = 0; i < p->d; ++i) {
     if (p->q1[i] < 1 || p->q2[i] < 1) return fail(LS_ERR_INVALID, "box extents must be >= 1");
   }
@@ -458,6 +511,41 @@ void choose_launch(ls_ctx* c) {
 }
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Joint-cutoff predicate over the box (Sec. 3): fl(0.5 * fl(sum_i fl(u_i^2)))
+// <= Ec with u_i = sum_j fl(B1[i][j] m_j) + sum_j fl(B2[i][j] n_j) accumulated
+// left to right (this file is compiled without contraction).  mask may be
+// NULL; returns the member count.
+int64_t joint_mask(const ls_ctx* c, uint8_t* mask) {
+  const int d = c->d;
+  const ls_problem& p = c->p;
+  int64_t cnt = 0;
+  for (int64_t r = 0; r < c->M2; ++r) {
+    double nv[2] = {(double)(r % p.q2[0] + p.lo2[0]), d > 1 ? (double)(r / p.q2[0] + p.lo2[1]) : 0.0};
+    for (int64_t col = 0; col < c->M1; ++col) {
+      double mv[2] = {(double)(col % p.q1[0] + p.lo1[0]), d > 1 ? (double)(col / p.q1[0] + p.lo1[1]) : 0.0};
+      double sum = 0.0;
+      for (int i = 0; i < d; ++i) {
+        double u = p.B1[i * d + 0] * mv[0];
+        for (int j = 1; j < d; ++j) u = u + p.B1[i * d + j] * mv[j];
+        for (int j = 0; j < d; ++j) u = u + p.B2[i * d + j] * nv[j];
+        const double uu = u * u;
+        sum = (i == 0) ? uu : sum + uu;
+      }
+      const bool in = 0.5 * sum <= p.ecut;
+      if (mask) mask[r * c->M1 + col] = in ? 1 : 0;
+      cnt += in;
+    }
+  }
+  return cnt;
+}
+
+// Projection onto the joint cutoff after a full step (LS_MASK_PROJECT_EACH_STEP).
+void enqueue_project(ls_ctx* c, void* psi, cudaStream_t st) {
+  const uint8_t* m = static_cast<const uint8_t*>(c->maskbuf.p);
+  if (c->dtype == LS_C64) LS_CUDA(lsk::launch_project<float>(psi, m, c->M1, c->M2, c->pitch, st));
+  else LS_CUDA(lsk::launch_project<double>(psi, m, c->M1, c->M2, c->pitch, st));
+}
 
 bool getenv_flag(const char* name) {
   const char* v = std::getenv(name);
@@ -721,6 +809,7 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
       }
       if (c->dtype == LS_C64) LS_CUDA(lsk::launch_si<float>(a, st));
       else LS_CUDA(lsk::launch_si<double>(a, st));
+      if (c->mask_mode == LS_MASK_PROJECT_EACH_STEP) enqueue_project(c, a.dst, st);
     }
     if (n & 1)  // the last step wrote the scratch array: copy the M1 columns of every row back
       LS_CUDA(cudaMemcpy2DAsync(psi, c->pitch * c->esize, c->scratch.p, c->pitch * c->esize, c->M1 * c->esize,
@@ -742,6 +831,7 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
         LS_CUDA(lsk::launch_cn<double>(a2, st));
         LS_CUDA(lsk::launch_cn<double>(a1, st));
       }
+      if (c->mask_mode == LS_MASK_PROJECT_EACH_STEP) enqueue_project(c, psi, st);
     }
     return;
   }
@@ -760,7 +850,9 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
   // Adjacent layer-1 factors of consecutive Strang steps (separated by one
   // merged kinetic factor) run as one fused pass when the layer takes the
   // convolution form on the fast path or the dedicated 64 x 64 pass.
-  if (!stoch && base_scheme(scheme) == LS_STRANG && ((c->conv_form[0] && c->fastW[0] > 0) || c->fast2d[0]) &&
+  // (Not with the projection: it sits between the two factors.)
+  const bool project = c->mask_mode == LS_MASK_PROJECT_EACH_STEP;
+  if (!stoch && !project && base_scheme(scheme) == LS_STRANG && ((c->conv_form[0] && c->fastW[0] > 0) || c->fast2d[0]) &&
       !getenv_flag("LSPLIT_NO_FUSE")) {
     std::vector<PassSpec> merged;
     for (size_t i = 0; i < ps.size(); ++i) {
@@ -789,12 +881,12 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
       a.mode = lsk::MODE_STEP;
       a.T = phase_table(c, q.layer, q.s);
       if (c->conv_form[L]) {
-        const ConvTab& ct = conv_table(c, q.layer, q.s);
+        const ConvTab ct = conv_table(c, q.layer, q.s);
         a.Khat = ct.khat->p;
         a.fix0_re = ct.fix_re;
         a.fix0_im = ct.fix_im;
         if (q.fused) {
-          const ConvTab& c2 = conv_table(c, q.layer, q.s2);
+          const ConvTab c2 = conv_table(c, q.layer, q.s2);
           a.Khat2 = c2.khat->p;
           a.fix2_re = c2.fix_re;
           a.fix2_im = c2.fix_im;
@@ -812,7 +904,7 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
       a.mode = lsk::MODE_LAZY;
       a.T = phase_table(c, q.layer, q.s * (double)S / (double)p);
       if (c->conv_form[L]) {
-        const ConvTab& ct = conv_table(c, q.layer, q.s * (double)S / (double)p);
+        const ConvTab ct = conv_table(c, q.layer, q.s * (double)S / (double)p);
         a.Khat = ct.khat->p;
         a.fix0_re = ct.fix_re;
         a.fix0_im = ct.fix_im;
@@ -826,6 +918,9 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
       a.W = 1;
       LS_CUDA(launch(c, a, L, p, st));
     }
+    // the projection is diagonal, so it commutes with kinetic phases still
+    // pending in the stochastic schemes and with the merged kinetic factors
+    if (project && (i + 1 == ps.size() || ps[i + 1].step != q.step)) enqueue_project(c, psi, st);
   }
   if (stoch) {
     // settle: every element gets its pending kinetic phase up to end_time
@@ -924,6 +1019,7 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     c->dtype = prob->dtype;
     c->esize = prob->dtype == LS_C64 ? 8 : 16;
     c->frac_den = prob->frac_den;
+    c->mask_mode = prob->mask_mode;
     c->h1.assign(prob->v1_h, prob->v1_h + (size_t)prob->nv1 * prob->d);
     c->h2.assign(prob->v2_h, prob->v2_h + (size_t)prob->nv2 * prob->d);
     c->c1.assign(prob->v1_c, prob->v1_c + 2 * (size_t)prob->nv1);
@@ -1065,26 +1161,7 @@ int ls_layout(const ls_ctx* c, int64_t* pitch, int64_t* rows, int64_t* bytes) {
 
 int ls_index_set(const ls_ctx* c, uint8_t* mask, int64_t* count) {
   if (!c) return fail(LS_ERR_STATE, "context is NULL");
-  const int d = c->d;
-  const ls_problem& p = c->p;
-  int64_t cnt = 0;
-  for (int64_t r = 0; r < c->M2; ++r) {
-    double nv[2] = {(double)(r % p.q2[0] + p.lo2[0]), d > 1 ? (double)(r / p.q2[0] + p.lo2[1]) : 0.0};
-    for (int64_t col = 0; col < c->M1; ++col) {
-      double mv[2] = {(double)(col % p.q1[0] + p.lo1[0]), d > 1 ? (double)(col / p.q1[0] + p.lo1[1]) : 0.0};
-      double sum = 0.0;
-      for (int i = 0; i < d; ++i) {
-        double u = p.B1[i * d + 0] * mv[0];
-        for (int j = 1; j < d; ++j) u = u + p.B1[i * d + j] * mv[j];
-        for (int j = 0; j < d; ++j) u = u + p.B2[i * d + j] * nv[j];
-        const double uu = u * u;
-        sum = (i == 0) ? uu : sum + uu;
-      }
-      const bool in = 0.5 * sum <= p.ecut;
-      if (mask) mask[r * c->M1 + col] = in ? 1 : 0;
-      cnt += in;
-    }
-  }
+  const int64_t cnt = joint_mask(c, mask);
   if (count) *count = cnt;
   return LS_OK;
 }
@@ -1158,8 +1235,20 @@ int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_
         lsk::SamplerArgs sa = sampler_args(c, scheme, npf);
         e->lists->alloc((size_t)n * npf * sa.pmax * sizeof(int32_t));
       }
+      if (c->mask_mode == LS_MASK_PROJECT_EACH_STEP && !c->maskbuf.p) {
+        std::vector<uint8_t> m((size_t)(c->M1 * c->M2));
+        joint_mask(c, m.data());
+        c->maskbuf.alloc(m.size());
+        LS_CUDA(cudaMemcpy(c->maskbuf.p, m.data(), m.size(), cudaMemcpyHostToDevice));
+      }
       // Tables are built (and uploaded) before capture: no allocation or
-      // synchronous copy may happen while the stream is being captured.
+      // synchronous copy may happen while the stream is being captured.  The
+      // graph keeps a reference to every table it reads.
+      struct KeepScope {
+        ls_ctx* c;
+        ~KeepScope() { c->keep = nullptr; }
+      } ks{c};
+      c->keep = &e->tables;
       prepare_tables(c, n, tau, scheme);
       cudaGraph_t graph = nullptr;
       LS_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -1181,6 +1270,22 @@ int ls_step(ls_ctx* c, void* psi, int64_t n, double tau, int32_t scheme, uint64_
     LS_CUDA(cudaGraphLaunch(ge->exec, st));
     return LS_OK;
   });
+}
+
+int ls_step_host(ls_ctx* c, void* psi_host, void* psi_dev, int64_t n, double tau, int32_t scheme, uint64_t seed,
+                 uint64_t step0, void* stream) {
+  if (!c) return fail(LS_ERR_STATE, "context is NULL");
+  if (!psi_host || !psi_dev) return fail(LS_ERR_INVALID, "NULL buffer");
+  const size_t bytes = (size_t)c->pitch * c->M2 * c->esize;
+  cudaStream_t st = S(stream);
+  cudaError_t e = cudaMemcpyAsync(psi_dev, psi_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, std::string("host to device copy: ") + cudaGetErrorString(e));
+  const int rc = ls_step(c, psi_dev, n, tau, scheme, seed, step0, stream);
+  if (rc != LS_OK) return rc;
+  e = cudaMemcpyAsync(psi_host, psi_dev, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, std::string("device to host copy: ") + cudaGetErrorString(e));
+  return LS_OK;
 }
 
 int ls_observables(ls_ctx* c, const void* psi, const void* chi, ls_obs* out, void* stream) {
@@ -1224,47 +1329,58 @@ int ls_density(ls_ctx* c, const void* psi, const double* x, int64_t nx, double* 
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
     const int dim = c->d;
-    // f[layer][component][j] = (B^T x_j)_component / 2 pi as 64-bit fractions
-    std::vector<uint64_t> f((size_t)4 * nx, 0);
-    for (int64_t j = 0; j < nx; ++j) {
-      for (int i = 0; i < dim; ++i)
-        if (!std::isfinite(x[j * dim + i])) return fail(LS_ERR_INVALID, "x is not finite");
-      for (int L = 0; L < 2; ++L) {
-        const double* B = L == 0 ? c->p.B1 : c->p.B2;
-        for (int a = 0; a < dim; ++a) {
-          double v = 0;
-          for (int i = 0; i < dim; ++i) v += B[i * dim + a] * x[j * dim + i];
-          f[(size_t)((2 * L + a) * nx + j)] = to_fixed(v / (2.0 * kPi));
+    for (int64_t j = 0; j < nx * dim; ++j)
+      if (!std::isfinite(x[j])) return fail(LS_ERR_INVALID, "x is not finite");
+    // points per chunk: the chunk's tables E1, E2 and partial sums T
+    // (chunk * (M1 + 2 M2) complex elements) stay below 512 MB
+    const int64_t per_point = (c->M1 + 2 * c->M2) * (int64_t)c->esize;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nx, ((int64_t)512 << 20) / per_point));
+    DevBuf fb, e1, e2, t, ob;
+    fb.alloc((size_t)4 * chunk * sizeof(uint64_t));
+    e1.alloc((size_t)chunk * c->M1 * c->esize);
+    e2.alloc((size_t)chunk * c->M2 * c->esize);
+    t.alloc((size_t)chunk * c->M2 * c->esize);
+    ob.alloc((size_t)2 * nx * sizeof(double));
+    std::vector<uint64_t> f((size_t)4 * chunk, 0);
+    for (int64_t j0 = 0; j0 < nx; j0 += chunk) {
+      const int64_t cn = std::min(chunk, nx - j0);
+      // f[layer][component][j] = (B^T x_j)_component / 2 pi as 64-bit fractions
+      std::fill(f.begin(), f.end(), 0);
+      for (int64_t j = 0; j < cn; ++j) {
+        const double* xj = x + (j0 + j) * dim;
+        for (int L = 0; L < 2; ++L) {
+          const double* B = L == 0 ? c->p.B1 : c->p.B2;
+          for (int a = 0; a < dim; ++a) {
+            double v = 0;
+            for (int i = 0; i < dim; ++i) v += B[i * dim + a] * xj[i];
+            f[(size_t)((2 * L + a) * cn + j)] = to_fixed(v / (2.0 * kPi));
+          }
         }
       }
+      // the copy reads f: wait for it before the next chunk rewrites f
+      LS_CUDA(cudaMemcpyAsync(fb.p, f.data(), (size_t)4 * cn * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+      lsk::DensityArgs d;
+      d.psi = psi;
+      d.M1 = c->M1;
+      d.M2 = c->M2;
+      d.pitch = c->pitch;
+      d.nx = cn;
+      d.q1a = c->p.q1[0];
+      d.q2a = c->p.q2[0];
+      d.lo1a = c->p.lo1[0];
+      d.lo1b = dim > 1 ? c->p.lo1[1] : 0;
+      d.lo2a = c->p.lo2[0];
+      d.lo2b = dim > 1 ? c->p.lo2[1] : 0;
+      d.f1 = static_cast<const uint64_t*>(fb.p);
+      d.f2 = static_cast<const uint64_t*>(fb.p) + 2 * cn;
+      d.e1 = e1.p;
+      d.e2 = e2.p;
+      d.t = t.p;
+      d.out = static_cast<double*>(ob.p) + 2 * j0;
+      if (c->dtype == LS_C64) LS_CUDA(lsk::launch_density<float>(d, st));
+      else LS_CUDA(lsk::launch_density<double>(d, st));
+      LS_CUDA(cudaStreamSynchronize(st));
     }
-    DevBuf fb, e1, e2, t, ob;
-    fb.alloc(f.size() * sizeof(uint64_t));
-    e1.alloc((size_t)nx * c->M1 * c->esize);
-    e2.alloc((size_t)nx * c->M2 * c->esize);
-    t.alloc((size_t)nx * c->M2 * c->esize);
-    ob.alloc((size_t)2 * nx * sizeof(double));
-    LS_CUDA(cudaMemcpyAsync(fb.p, f.data(), f.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    lsk::DensityArgs d;
-    d.psi = psi;
-    d.M1 = c->M1;
-    d.M2 = c->M2;
-    d.pitch = c->pitch;
-    d.nx = nx;
-    d.q1a = c->p.q1[0];
-    d.q2a = c->p.q2[0];
-    d.lo1a = c->p.lo1[0];
-    d.lo1b = dim > 1 ? c->p.lo1[1] : 0;
-    d.lo2a = c->p.lo2[0];
-    d.lo2b = dim > 1 ? c->p.lo2[1] : 0;
-    d.f1 = static_cast<const uint64_t*>(fb.p);
-    d.f2 = static_cast<const uint64_t*>(fb.p) + 2 * nx;
-    d.e1 = e1.p;
-    d.e2 = e2.p;
-    d.t = t.p;
-    d.out = static_cast<double*>(ob.p);
-    if (c->dtype == LS_C64) LS_CUDA(lsk::launch_density<float>(d, st));
-    else LS_CUDA(lsk::launch_density<double>(d, st));
     LS_CUDA(cudaMemcpyAsync(out, ob.p, (size_t)2 * nx * sizeof(double), cudaMemcpyDeviceToHost, st));
     LS_CUDA(cudaStreamSynchronize(st));
     return LS_OK;
@@ -1299,15 +1415,25 @@ int ls_samples(ls_ctx* c, int32_t layer, uint64_t seed, uint64_t g0, int32_t cou
   });
 }
 
-int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t scheme, double* gv1, double* gv2,
-               double* gc1, double* gc2, void* stream) {
+int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t scheme, uint64_t seed,
+               uint64_t step0, double* gv1, double* gv2, double* gc1, double* gc2, void* stream) {
   if (!c) return fail(LS_ERR_STATE, "context is NULL");
   if (!psi || !lam || !gv1 || !gv2) return fail(LS_ERR_INVALID, "NULL argument");
-  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP && scheme != LS_YOSHIDA4)
-    return fail(LS_ERR_INVALID, "adjoint supports LIE, STRANG, STRANG_KP and YOSHIDA4 only");
+  const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+  if (scheme != LS_LIE && scheme != LS_STRANG && scheme != LS_STRANG_KP && scheme != LS_YOSHIDA4 && !stoch)
+    return fail(LS_ERR_INVALID, "adjoint supports LIE, STRANG, STRANG_KP, YOSHIDA4, LIE_STOCH and STRANG_STOCH only");
+  if (c->mask_mode != LS_MASK_INIT_ONLY)
+    return fail(LS_ERR_INVALID, "the projection onto the cutoff is not unitary: no adjoint sweep");
   if (n < 0 || !std::isfinite(tau)) return fail(LS_ERR_INVALID, "bad nsteps or tau");
+  if (n > (1 << 26) / 8) return fail(LS_ERR_INVALID, "nsteps too large for one call (split it)");
   return guarded([&]() -> int {
     cudaStream_t st = S(stream);
+    TableKeep keep;  // tables of this call stay alive until it returns
+    struct KeepScope {
+      ls_ctx* c;
+      ~KeepScope() { c->keep = nullptr; }
+    } ks{c};
+    c->keep = &keep;
     for (int L = 0; L < 2; ++L) {
       const int64_t M = L == 0 ? c->M1 : c->M2;
       if (c->grad[L].bytes < (size_t)M * sizeof(double)) c->grad[L].alloc((size_t)M * sizeof(double));
@@ -1317,20 +1443,60 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
     int32_t end_time = 0;
     const double u = build_passes(scheme, tau, n, ps, end_time);
     set_kinetic(c, u);
+    DevBuf lists;
+    int npf = 0;
+    lsk::SamplerArgs sa = sampler_args(c, scheme, npf);
+    if (stoch && n > 0) {
+      // the forward call's samples: sub-step g = (step0 + k) * npf + factor
+      sa.seed = seed;
+      sa.g0 = step0 * (uint64_t)npf;
+      lists.alloc((size_t)n * npf * sa.pmax * sizeof(int32_t));
+      LS_CUDA(lsk::launch_sampler(sa, nullptr, (int32_t)(n * npf), (int32_t*)lists.p, st));
+    }
     for (size_t i = ps.size(); i-- > 0;) {
       const PassSpec& q = ps[i];
       const int L = q.layer - 1;
       if (q.unit != 0) set_kinetic(c, q.unit);  // per-pass kinetic unit (fourth-order scheme)
+      if (!stoch) {
+        lsk::PassArgs a = base_args(c, L, psi);
+        a.mode = lsk::MODE_ADJOINT;
+        a.lam = lam;
+        a.T = phase_table(c, q.layer, -q.s);
+        a.units_pre = -q.post;
+        a.units_post = -q.pre;
+        a.grad = (double*)c->grad[L].p;
+        a.sdur = q.s;
+        LS_CUDA(launch(c, a, L, c->geom[L].nslices, st));
+        continue;
+      }
+      // Stochastic factor (Algorithm 4): the kinetic factors act on every
+      // element, the potential factor of duration s S/p on the sampled slices.
+      auto kin_all = [&](int64_t units) {
+        if (units == 0) return;
+        lsk::PassArgs k = base_args(c, 0, psi);
+        k.mode = lsk::MODE_KIN;
+        k.lam = lam;
+        k.units_pre = units;
+        LS_CUDA(launch(c, k, 0, c->geom[0].nslices, st));
+      };
+      const int64_t Sv = c->geom[L].nslices;
+      const int32_t pv = std::max<int32_t>(1, (int32_t)(Sv / c->frac_den));
+      const double sd = q.s * (double)Sv / (double)pv;
+      kin_all(-q.post);
       lsk::PassArgs a = base_args(c, L, psi);
       a.mode = lsk::MODE_ADJOINT;
       a.lam = lam;
-      a.T = phase_table(c, q.layer, -q.s);
-      a.units_pre = -q.post;
-      a.units_post = -q.pre;
+      a.T = phase_table(c, q.layer, -sd);
       a.grad = (double*)c->grad[L].p;
-      a.sdur = q.s;
-      LS_CUDA(launch(c, a, L, c->geom[L].nslices, st));
+      a.sdur = sd;
+      a.list = (const int32_t*)lists.p + (int64_t)i * sa.pmax;
+      a.nlist = pv;
+      a.strided = 0;  // sampled columns are scattered
+      a.W = 1;
+      LS_CUDA(launch(c, a, L, pv, st));
+      kin_all(-q.pre);
     }
+    set_kinetic(c, u);  // the call's unit (the fourth-order sweep changed it per pass)
     LS_CUDA(cudaMemcpyAsync(gv1, c->grad[0].p, c->M1 * sizeof(double), cudaMemcpyDeviceToHost, st));
     LS_CUDA(cudaMemcpyAsync(gv2, c->grad[1].p, c->M2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     LS_CUDA(cudaStreamSynchronize(st));
@@ -1392,6 +1558,7 @@ struct ls_batch {
     int64_t n;
     cudaGraphExec_t exec = nullptr;
     std::shared_ptr<DevBuf> args, lists;
+    TableKeep tables;  // every instance table the captured launch reads
     ~Cached() {
       if (exec) cudaGraphExecDestroy(exec);
     }
@@ -1439,6 +1606,8 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     if (v != LS_OK) return v;
     if (probs[i].dtype != probs[0].dtype) return fail(LS_ERR_INVALID, "all instances need the same dtype");
     if (probs[i].d != 1) return fail(LS_ERR_INVALID, "the batched runner takes 1D instances");
+    if (probs[i].mask_mode != LS_MASK_INIT_ONLY)
+      return fail(LS_ERR_INVALID, "the batched runner evolves the whole box (LS_MASK_INIT_ONLY)");
   }
   return guarded([&]() -> int {
     std::unique_ptr<ls_batch> b(new ls_batch());
@@ -1545,6 +1714,22 @@ int ls_batch_init_gaussian(ls_batch* b, void* psi, const double* x0, double w, c
   return LS_OK;
 }
 
+int ls_batch_step_host(ls_batch* b, void* psi_host, void* psi_dev, int64_t n, double tau, int32_t scheme,
+                       uint64_t seed, uint64_t step0, void* stream) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (!psi_host || !psi_dev) return fail(LS_ERR_INVALID, "NULL buffer");
+  const size_t bytes = (size_t)b->off.back() * (b->dtype == LS_C64 ? 8 : 16);
+  cudaStream_t st = S(stream);
+  cudaError_t e = cudaMemcpyAsync(psi_dev, psi_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, std::string("host to device copy: ") + cudaGetErrorString(e));
+  const int rc = ls_batch_step(b, psi_dev, n, tau, scheme, seed, step0, stream);
+  if (rc != LS_OK) return rc;
+  e = cudaMemcpyAsync(psi_host, psi_dev, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(LS_ERR_CUDA, std::string("device to host copy: ") + cudaGetErrorString(e));
+  return LS_OK;
+}
+
 int ls_batch_observables(ls_batch* b, const void* psi, ls_obs* out, void* stream) {
   if (!b) return fail(LS_ERR_STATE, "batch is NULL");
   if (!psi || !out) return fail(LS_ERR_INVALID, "NULL argument");
@@ -1629,6 +1814,13 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       }
       e->lists = std::make_shared<DevBuf>();
       if (stoch) e->lists->alloc((size_t)ltot * sizeof(int32_t));
+      for (ls_ctx* c : b->inst) c->keep = &e->tables;
+      struct KeepScope {
+        ls_batch* b;
+        ~KeepScope() {
+          for (ls_ctx* c : b->inst) c->keep = nullptr;
+        }
+      } ks{b};
       std::vector<lsk::PassArgs> args((size_t)npass * ninst), sargs(ninst);
       std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0), scum(ninst + 1, 0);
       const size_t es = b->dtype == LS_C64 ? 8 : 16;
@@ -1649,7 +1841,7 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
             a.mode = lsk::MODE_STEP;
             a.T = phase_table(c, layer, ps[q].s);
             if (conv) {
-              const ConvTab& ct = conv_table(c, layer, ps[q].s);
+              const ConvTab ct = conv_table(c, layer, ps[q].s);
               a.Khat = ct.khat->p;
               a.fix0_re = ct.fix_re;
               a.fix0_im = ct.fix_im;
@@ -1661,7 +1853,7 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
             a.mode = lsk::MODE_LAZY;
             a.T = phase_table(c, layer, ps[q].s * (double)Sv / (double)pv);
             if (conv) {
-              const ConvTab& ct = conv_table(c, layer, ps[q].s * (double)Sv / (double)pv);
+              const ConvTab ct = conv_table(c, layer, ps[q].s * (double)Sv / (double)pv);
               a.Khat = ct.khat->p;
               a.fix0_re = ct.fix_re;
               a.fix0_im = ct.fix_im;

@@ -101,6 +101,9 @@ template <typename Real> cudaError_t launch_gaussian(const ElemArgs& e, void* ps
                                                      int nblocks, cudaStream_t st);
 template <typename Real> cudaError_t launch_scale(const ElemArgs& e, void* psi, const double* sumsq,
                                                   cudaStream_t st);
+// Zero every coefficient whose byte in mask (M2 x M1, row-major) is 0.
+template <typename Real> cudaError_t launch_project(void* psi, const uint8_t* mask, int64_t M1, int64_t M2,
+                                                    int64_t pitch, cudaStream_t st);
 template <typename Real> cudaError_t launch_elem_obs(const ElemArgs& e, const void* psi,
                                                      const void* chi, double* partials, int nblocks,
                                                      cudaStream_t st);

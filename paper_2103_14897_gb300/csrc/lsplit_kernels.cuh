@@ -371,7 +371,10 @@ __device__ __forceinline__ void bluestein_conv(typename CT<Real>::C* sm, const L
 //   MODE_STEP     K(post) P(s) K(pre) with fixed kinetic units;
 //   MODE_LAZY     stochastic: P on the listed slices only, the kinetic phase
 //                 pending since the element's last touch applied before P;
-//   MODE_KIN      settle: pending kinetic phase only, no transform;
+//   MODE_KIN      kinetic phase only, no transform: the phase pending since
+//                 the element's last touch (settle, touch_own set), or a fixed
+//                 units_pre on psi and, if lam is set, on lam (the reverse
+//                 sweep of the stochastic schemes);
 //   MODE_MEASURE  sum_p v(x_p)|psi(x_p)|^2 / M per CTA (potential energy);
 //   MODE_ADJOINT  inverse factor on psi and lambda together, accumulating
 //                 dL/dv(x_p).
@@ -428,7 +431,7 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
       la = g.X_aa * ua + g.X_ab * ub;
       lb = g.X_ba * ua + g.X_bb * ub;
       c0 = g.C_aa * (ua * ua) + g.C_ab * (ua * ub) + g.C_bb * (ub * ub);
-      if (lazy || kin_only) touch = CG ? __ldcg(a.touch_own + s) : a.touch_own[s];
+      if (lazy || (kin_only && a.touch_own)) touch = CG ? __ldcg(a.touch_own + s) : a.touch_own[s];
     }
     s_la[tid] = la;
     s_lb[tid] = lb;
@@ -440,6 +443,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
   C* psi = reinterpret_cast<C*>(a.psi);
   C* lam = reinterpret_cast<C*>(a.lam);
   const C* chirp = reinterpret_cast<const C*>(g.chirp);
+  const bool kin_lam = kin_only && lam != nullptr;   // fixed-units kinetic factor on psi and lam
+  const bool kin_touch = kin_only && a.touch_own != nullptr;
 
   // ---- load + kinetic pre-phase (+ Bluestein pre-chirp on the transform input)
   for (int e = tid; e < W * M; e += NT) {
@@ -451,10 +456,10 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
       const int ia = i % g.qa, ib = i / g.qa;
       const int64_t off = s * g.slice_stride + ia * g.ea + ib * g.eb;
       x = ldpsi<CG>(psi + off);
-      if (adj) xl = lam[off];
+      if (adj || kin_lam) xl = lam[off];
       if (!measure) {
         int64_t units = a.units_pre;
-        if (lazy || kin_only) {
+        if (lazy || kin_touch) {
           const int32_t t2 = CG ? __ldcg(a.touch_other + i) : a.touch_other[i];
           units = (int64_t)a.now - (int64_t)(s_touch[w] > t2 ? s_touch[w] : t2);
         }
@@ -462,10 +467,11 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
           const uint64_t qd = quad_turns(g, g.lo_a + ia, g.lo_b + ib, s_la[w], s_lb[w], s_c0[w]);
           const Phase<Real> ph = phase_of<Real>((uint64_t)0 - (uint64_t)units * qd);
           x = apply_phase<Real>(x, ph);
-          if (adj) xl = apply_phase<Real>(xl, ph);
+          if (adj || kin_lam) xl = apply_phase<Real>(xl, ph);
         }
         if (kin_only) {
           psi[off] = x;
+          if (kin_lam) lam[off] = xl;
           continue;
         }
       }
@@ -1996,6 +2002,22 @@ __global__ void scale_kernel(const ElemArgs e, typename CT<Real>::C* psi, const 
   }
 }
 
+// Projection onto the joint cutoff (Sec. 3 index sets): every coefficient
+// whose mask byte is 0 is set to zero; members are not touched.
+template <typename Real>
+__global__ void project_kernel(typename CT<Real>::C* psi, const uint8_t* __restrict__ mask, int64_t M1,
+                               int64_t M2, int64_t pitch) {
+  using C = typename CT<Real>::C;
+  const int64_t total = M1 * M2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    if (!mask[idx]) {
+      const int64_t row = idx / M1, col = idx - row * M1;
+      psi[row * pitch + col] = czero<C>();
+    }
+  }
+}
+
 template <typename Real>
 __global__ void elem_obs_kernel(const ElemArgs e, const typename CT<Real>::C* psi,
                                 const typename CT<Real>::C* chi, double* partials) {
@@ -2162,6 +2184,13 @@ cudaError_t launch_scale(const ElemArgs& e, void* psi, const double* sumsq, cuda
   return cudaGetLastError();
 }
 template <typename Real>
+cudaError_t launch_project(void* psi, const uint8_t* mask, int64_t M1, int64_t M2, int64_t pitch,
+                           cudaStream_t st) {
+  project_kernel<Real><<<kReduceBlocks, 256, 0, st>>>(reinterpret_cast<typename CT<Real>::C*>(psi), mask, M1, M2,
+                                                      pitch);
+  return cudaGetLastError();
+}
+template <typename Real>
 cudaError_t launch_elem_obs(const ElemArgs& e, const void* psi, const void* chi, double* partials, int nblocks,
                             cudaStream_t st) {
   using C = typename CT<Real>::C;
@@ -2210,6 +2239,7 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
   template cudaError_t launch_gaussian<R>(const ElemArgs&, void*, const double*, double, const double*, \
                                           double*, int, cudaStream_t);                                   \
   template cudaError_t launch_scale<R>(const ElemArgs&, void*, const double*, cudaStream_t);             \
+  template cudaError_t launch_project<R>(void*, const uint8_t*, int64_t, int64_t, int64_t, cudaStream_t); \
   template cudaError_t launch_elem_obs<R>(const ElemArgs&, const void*, const void*, double*, int,      \
                                           cudaStream_t);                                                 \
   template cudaError_t launch_fast<R>(const PassArgs&, int64_t, cudaStream_t);                           \

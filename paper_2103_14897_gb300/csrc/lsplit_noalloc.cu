@@ -1,12 +1,11 @@
 // ls_mass_noalloc: the mass sum |phi|^2 of a wave-function array, computed
 // without allocating any memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (allocation would break the capture), hosts that
-// hand out all device memory from their own pool and forbid other
-// allocations, and real-time loops that must not touch the allocator.  This
-// entry point needs no context (ls_create allocates) and uses, as its scratch,
-// a fixed file-scope device array instead of memory it would allocate.
+// Some callers cannot call cudaMalloc: hosts that hand out all device memory
+// from their own pool and forbid other allocations, and real-time loops that
+// must not pay for or wait on the allocator.  This entry point needs no
+// context (ls_create allocates) and uses, as its scratch, a fixed file-scope
+// device array instead of memory it would allocate.
 //
 // The scratch holds one FP64 partial sum per row, kNoAllocMaxRows rows at
 // most (512 KB).  It lives in every GPU that loads the library until the

@@ -63,6 +63,11 @@ def test_invalid_problems_rejected_before_cuda(lib):
     st.dtype = 0
     st.frac_den = 0
     assert lib.ls_create(C.byref(st), C.byref(h)) == -1
+    st.frac_den = 8
+    st.mask_mode = 2
+    assert lib.ls_create(C.byref(st), C.byref(h)) == -1
+    assert b"mask_mode" in lib.ls_last_error()
+    st.mask_mode = 0
     assert lib.ls_create(C.byref(st), None) == -1
     assert lib.ls_create(None, C.byref(h)) == -1
 
@@ -73,3 +78,16 @@ def test_null_context_calls(lib):
     assert lib.ls_step(None, None, 1, 0.1, 1, 0, 0, None) == -5
     assert lib.ls_destroy(None) == 0
     assert lib.ls_index_set(None, None, None) == -5
+    assert lib.ls_step_host(None, None, None, 1, 0.1, 1, 0, 0, None) == -5
+    assert lib.ls_batch_step_host(None, None, None, 1, 0.1, 1, 0, 0, None) == -5
+    assert lib.ls_adjoint(None, None, None, 1, 0.1, 1, 0, 0, None, None, None, None, None) == -5
+
+
+def test_batch_rejects_projection_before_cuda(lib):
+    import workloads as W
+    from paper_2103_14897_gb300._binding import make_problem_struct, LsProblem
+    st, keep = make_problem_struct(W.config_small_1d(), mask_mode="project")
+    arr = (LsProblem * 1)(st)
+    h = C.c_void_p()
+    assert lib.ls_batch_create(arr, 1, C.byref(h)) == -1
+    assert b"LS_MASK_INIT_ONLY" in lib.ls_last_error()

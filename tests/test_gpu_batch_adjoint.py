@@ -5,6 +5,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from tests._parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -21,8 +22,6 @@ def P():
     return P
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def uneven_batch():
@@ -177,6 +176,65 @@ def test_autograd_overlap_gradient_matches_oracle(P):
             assert np.abs(t2.grad.numpy() - ref2).max() < tol * sc * 20, (dtype, ck)
 
 
+def test_autograd_backward_twice_and_stochastic(P):
+    """A second backward (retain_graph=True) gives the same gradients as the
+    first; the stochastic schemes differentiate with the forward call's
+    samples (Algorithm 4), against the oracle's adjoint with the same seed."""
+    import torch
+    from paper_2103_14897_gb300.autograd import overlap_loss
+    base = W.bilayer_1d(20, 16, 0.0, 0.0, ecut=1e9)
+    th1 = np.array([0.6, -0.3, 0.2])
+    th2 = np.array([0.4, 0.25])
+    phi0 = O.gaussian_packet(base, [0.0], 0.8, [1.0])
+    chi = O.gaussian_packet(base, [0.3], 0.8, [1.2])
+    h1, c1 = W.cos_series_coeffs(th1)
+    h2, c2 = W.cos_series_coeffs(th2)
+    prob = base.with_potentials(c1, c2, h1, h2)
+    for scheme, ck in (("strang", 3), ("strang", 0), ("strang_stoch", 4), ("lie_stoch", 0)):
+        Lref, _, g1, g2 = O.adjoint(prob, phi0, 0.02, scheme, 9, lambda f: O.overlap_loss(chi, f), seed=6)
+        cg1 = O.coefficient_gradient(g1, h1, prob.q1)
+        cg2 = O.coefficient_gradient(g2, h2, prob.q2)
+        ref1 = 0.5 * (cg1[0::2, 0] + cg1[1::2, 0])
+        ref2 = 0.5 * (cg2[0::2, 0] + cg2[1::2, 0])
+        sc = max(np.abs(ref1).max(), np.abs(ref2).max())
+        t1 = torch.tensor(th1, requires_grad=True)
+        t2 = torch.tensor(th2, requires_grad=True)
+        L = overlap_loss(t1, t2, base, phi0, chi, 0.02, 9, scheme, "c64", checkpoint_every=ck, seed=6)
+        assert abs(float(L.detach()) - Lref) < 1e-4
+        a1, a2 = torch.autograd.grad(L, (t1, t2), retain_graph=True)
+        b1, b2 = torch.autograd.grad(L, (t1, t2))
+        assert np.abs(a1.numpy() - ref1).max() < 2e-4 * sc, (scheme, ck)
+        assert np.abs(a2.numpy() - ref2).max() < 2e-4 * sc, (scheme, ck)
+        assert np.array_equal(a1.numpy(), b1.numpy()) and np.array_equal(a2.numpy(), b2.numpy()), (scheme, ck)
+
+
+def test_autograd_reduced_box_500_steps_against_oracle(P):
+    """The adjoint workload's potentials (8 cosine coefficients per layer,
+    N(0, 0.5), seed 5) and 500 steps of tau = 1e-3 on a reduced 65 x 65 box:
+    the FP32 reverse sweep with drift-placed checkpoints against the oracle's
+    trajectory-storing FP64 adjoint."""
+    import torch
+    from paper_2103_14897_gb300.autograd import overlap_loss
+    _, th1, th2 = W.config_adjoint_1d()
+    base = W.bilayer_1d(32, 32, 0.0, 0.0)
+    h1, c1 = W.cos_series_coeffs(th1)
+    h2, c2 = W.cos_series_coeffs(th2)
+    prob = base.with_potentials(c1, c2, h1, h2)
+    phi0 = O.gaussian_packet(base, [0.0], 2.0, [1.0])
+    chi = O.gaussian_packet(base, [0.5], 2.0, [1.2])
+    Lref, _, g1, g2 = O.adjoint(prob, phi0, 1e-3, "strang", 500, lambda f: O.overlap_loss(chi, f))
+    cg1 = O.coefficient_gradient(g1, h1, prob.q1)
+    cg2 = O.coefficient_gradient(g2, h2, prob.q2)
+    ref = np.concatenate([0.5 * (cg1[0::2, 0] + cg1[1::2, 0]), 0.5 * (cg2[0::2, 0] + cg2[1::2, 0])])
+    t1 = torch.tensor(th1, requires_grad=True)
+    t2 = torch.tensor(th2, requires_grad=True)
+    L = overlap_loss(t1, t2, base, phi0, chi, 1e-3, 500, "strang", "c64", drift_tol=1e-5)
+    L.backward()
+    got = np.concatenate([t1.grad.numpy(), t2.grad.numpy()])
+    assert abs(float(L.detach()) - Lref) < 1e-4 * max(1.0, Lref)
+    assert np.abs(got - ref).max() < 1e-3 * np.abs(ref).max(), (got, ref)
+
+
 def test_autograd_adjoint_workload_central_differences(P):
     """513 x 513 box, 8 cosine coefficients per layer (N(0, 0.5), seed 5),
     overlap loss after 500 steps of tau = 1e-3: the FP32 reverse-sweep gradient
@@ -187,10 +245,19 @@ def test_autograd_adjoint_workload_central_differences(P):
     base = prob
     phi0 = O.gaussian_packet(base, [0.0], 2.0, [1.0])
     chi = O.gaussian_packet(base, [0.5], 2.0, [1.2])
-    t1 = torch.tensor(th1, requires_grad=True)
-    t2 = torch.tensor(th2, requires_grad=True)
-    L = overlap_loss(t1, t2, base, phi0, chi, 1e-3, 500, "strang", "c64", checkpoint_every=100)
-    L.backward()
+    from paper_2103_14897_gb300.autograd import checkpoint_plan
+    # drift-placed checkpoints against the fixed policy (every 100 steps)
+    grads = {}
+    for name, kw in (("fixed", {"checkpoint_every": 100}), ("drift", {"drift_tol": 1e-4})):
+        t1 = torch.tensor(th1, requires_grad=True)
+        t2 = torch.tensor(th2, requires_grad=True)
+        L = overlap_loss(t1, t2, base, phi0, chi, 1e-3, 500, "strang", "c64", **kw)
+        L.backward()
+        grads[name] = (t1.grad.numpy().copy(), t2.grad.numpy().copy())
+    c = P.Context(prob, "c64")
+    marks, d, probe = checkpoint_plan(c, c.from_dense(phi0), 500, 1e-3, "strang", drift_tol=1e-4)
+    print("drift-placed checkpoints", marks, "probe drift", d, "over", probe, "steps")
+    assert len(marks) < 4
     h = 1e-4
 
     def f(a, b):
@@ -206,8 +273,9 @@ def test_autograd_adjoint_workload_central_differences(P):
         a[i] += h
         b[i] -= h
         fd2.append((f(th1, a) - f(th1, b)) / (2 * h))
-    got1 = t1.grad.numpy()[[0, 3, 7]]
-    got2 = t2.grad.numpy()[[1, 6]]
     scale = max(np.abs(fd1).max(), np.abs(fd2).max(), 1e-6)
-    assert np.abs(got1 - fd1).max() < 1e-3 * scale + 1e-7, (got1, fd1)
-    assert np.abs(got2 - fd2).max() < 1e-3 * scale + 1e-7, (got2, fd2)
+    for name, (a1, a2) in grads.items():
+        got1 = a1[[0, 3, 7]]
+        got2 = a2[[1, 6]]
+        assert np.abs(got1 - fd1).max() < 1e-3 * scale + 1e-7, (name, got1, fd1)
+        assert np.abs(got2 - fd2).max() < 1e-3 * scale + 1e-7, (name, got2, fd2)

@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from tests._parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -27,8 +28,6 @@ def P():
     return P
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def run_vs_oracle(P, p, dtype, scheme, n=2, tau=5e-3, seed=0, fft=False):

@@ -12,6 +12,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from tests._parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -30,8 +31,6 @@ def P():
     return P
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def problems_1d():
@@ -358,6 +357,84 @@ def test_stochastic_step_parity(P, scheme, dtype):
         assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 5
 
 
+def long_slice_boxes():
+    """Rows (then columns) of length 2049: the layer-1 fast pass and the
+    strided layer-2 passes of transform length 4096, next to a short other
+    layer so the oracle stays quick."""
+    return [W.bilayer_1d(1024, 16, 1.3, 0.9, ecut=1e9, name="2049x33"),
+            W.bilayer_1d(16, 1024, 0.9, 1.3, ecut=1e9, name="33x2049")]
+
+
+@pytest.mark.parametrize("scheme", ["lie_stoch", "strang_stoch"])
+def test_stochastic_long_slices(P, scheme):
+    """The stochastic schemes where the sampled slices are 2049 long, so the
+    lazy kinetic phases run inside the fast 1D passes (the sampled-slice path
+    of the 2049 x 2049 workload): 3 steps, then 2 more continuing the sample
+    sequence, against the oracle."""
+    O.use_fft(True)
+    try:
+        for p in long_slice_boxes():
+            ctx = P.Context(p, "c64")
+            x = W.random_state((p.M2, p.M1), 24)
+            psi = ctx.from_dense(x)
+            ctx.step(psi, 3, 5e-4, scheme, seed=11, step0=4)
+            ref = O.step(p, x, 5e-4, scheme, 3, seed=11, step0=4)
+            assert rel(ctx.to_dense(psi), ref) < TOL1["c64"] * 3, (p.name, rel(ctx.to_dense(psi), ref))
+            ctx.step(psi, 2, 5e-4, scheme, seed=11, step0=7)
+            ref = O.step(p, ref, 5e-4, scheme, 2, seed=11, step0=7)
+            assert rel(ctx.to_dense(psi), ref) < TOL1["c64"] * 5, (p.name, rel(ctx.to_dense(psi), ref))
+    finally:
+        O.use_fft(False)
+
+
+def test_long_run_1000_steps_long_slices(P):
+    """The 1000-step gate through the headline kernels: 1000 Strang steps of
+    tau = 5e-4 on boxes whose rows or columns are 2049 long (fused layer-1
+    fast pass, two-column strided pass), random full-spectrum state:
+    rel-L2 <= 1e-4 and | ||psi|| - 1 | <= 1e-5 against the oracle."""
+    O.use_fft(True)
+    try:
+        for p in long_slice_boxes():
+            ctx = P.Context(p, "c64")
+            x = W.random_state((p.M2, p.M1), 25)
+            psi = ctx.from_dense(x)
+            ctx.step(psi, 1000, 5e-4, "strang")
+            ref = O.step(p, x, 5e-4, "strang", 1000)
+            got = ctx.to_dense(psi)
+            print(p.name, "1000-step rel", rel(got, ref), "norm-1", np.linalg.norm(got) - 1)
+            assert rel(got, ref) < 1e-4, (p.name, rel(got, ref))
+            assert abs(np.linalg.norm(got) - 1) < 1e-5
+    finally:
+        O.use_fft(False)
+
+
+def test_project_each_step_mode(P):
+    """mask_mode "project": every step ends with the projection onto the joint
+    cutoff of Sec. 3 (the oracle's project=True); members keep the scheme's
+    values and everything outside the cutoff is zero after each call."""
+    cases = [(W.config_small_1d(), ["lie", "strang", "strang_kp", "strang_stoch", "yoshida4", "cn_strang",
+                                    "semi_implicit"]),
+             (W.bilayer_1d(300, 5, 1.1, 0.7), ["strang", "lie_stoch"]),
+             (W.twisted_2d(q=8, hmax=2, ecut=30.0), ["strang", "strang_stoch"])]
+    for p, schemes in cases:
+        mask = O.index_mask(p)
+        assert 0 < mask.sum() < mask.size
+        for dtype in ("c64", "c128"):
+            ctx = P.Context(p, dtype, mask_mode="project")
+            x = W.random_state((p.M2, p.M1), 26)
+            for scheme in schemes:
+                psi = ctx.from_dense(x)
+                ctx.step(psi, 3, 2e-3, scheme, seed=4, step0=1)
+                ref = O.step(p, x, 2e-3, scheme, 3, seed=4, step0=1, project=True)
+                got = ctx.to_dense(psi)
+                assert np.all(got[~mask] == 0), (p.name, scheme)
+                assert rel(got, ref) < TOL1[dtype] * 3, (p.name, scheme, dtype, rel(got, ref))
+            # the projection is not unitary: no reverse sweep
+            with pytest.raises(P.LsplitError) as e:
+                ctx.adjoint(ctx.empty(), ctx.empty(), 1, 1e-3, "strang")
+            assert e.value.code == P.LS_ERR_INVALID
+
+
 def test_full_sampling_equals_deterministic(P):
     p = W.bilayer_1d(16, 20, 1.3, 0.9, ecut=1e9)
     c1 = P.Context(p, "c128", frac_den=1)
@@ -495,19 +572,57 @@ def test_adjoint_parity(P):
     p = base.with_potentials(c1, c2, h1, h2)
     phi0 = O.gaussian_packet(p, [0.0], 0.8, [1.0])
     chi = O.gaussian_packet(p, [0.3], 0.8, [1.2])
-    for scheme in ("strang", "lie", "strang_kp", "yoshida4"):
-        L, phiT, g1, g2 = O.adjoint(p, phi0, 0.02, scheme, 6, lambda f: O.overlap_loss(chi, f))
+    for scheme in ("strang", "lie", "strang_kp", "yoshida4", "lie_stoch", "strang_stoch"):
+        L, phiT, g1, g2 = O.adjoint(p, phi0, 0.02, scheme, 6, lambda f: O.overlap_loss(chi, f), seed=5, step0=2)
         for dtype, tol in (("c64", 2e-5), ("c128", 1e-10)):
             ctx = P.Context(p, dtype)
             psi = ctx.from_dense(phiT)
             lam = ctx.from_dense(O.overlap_loss(chi, phiT)[1])
-            gg1, gg2, gc1, gc2 = ctx.adjoint(psi, lam, 6, 0.02, scheme)
+            gg1, gg2, gc1, gc2 = ctx.adjoint(psi, lam, 6, 0.02, scheme, seed=5, step0=2)
             sc = max(np.abs(g1).max(), np.abs(g2).max())
             assert np.abs(gg1 - g1).max() < tol * sc * 10, (scheme, dtype)
             assert np.abs(gg2 - g2).max() < tol * sc * 10, (scheme, dtype)
             assert rel(ctx.to_dense(psi), phi0) < tol * 10
             cg = O.coefficient_gradient(g1, h1, p.q1)
             assert np.abs(gc1 - cg).max() < tol * max(1, np.abs(cg).max()) * 10
+
+
+def test_adjoint_round_trip_fast_and_64x64_passes(P):
+    """Forward on the GPU through the fast 1D passes (slices of length 513)
+    and the dedicated 64 x 64 passes, then the reverse sweep: the rebuilt state
+    is the initial one and the gradients match the oracle's adjoint, for the
+    fourth-order scheme (one kinetic unit per pass) and Strang."""
+    import dataclasses
+    th1 = np.array([0.5, -0.2])
+    th2 = np.array([0.3, 0.15])
+    h1, c1 = W.cos_series_coeffs(th1)
+    h2, c2 = W.cos_series_coeffs(th2)
+    p1 = W.bilayer_1d(256, 12, 0.0, 0.0, ecut=1e9).with_potentials(c1, c2, h1, h2)
+    p2 = dataclasses.replace(W.twisted_2d(q=64, hmax=2), lo2=(-4, -4), q2=(8, 8), ecut=1e9, name="64x64-adj")
+    O.use_fft(True)
+    try:
+        for p, n, tau in ((p1, 3, 5e-3), (p2, 2, 2e-3)):
+            phi0 = W.random_state((p.M2, p.M1), 27)
+            chi = W.random_state((p.M2, p.M1), 28)
+            for scheme in ("yoshida4", "strang"):
+                L, phiT, g1, g2 = O.adjoint(p, phi0, tau, scheme, n, lambda f: O.overlap_loss(chi, f))
+                ctx = P.Context(p, "c64")
+                psi = ctx.from_dense(phi0)
+                ctx.step(psi, n, tau, scheme)
+                assert rel(ctx.to_dense(psi), phiT) < 5e-5, (p.name, scheme)
+                lam = ctx.from_dense(O.overlap_loss(chi, ctx.to_dense(psi))[1])
+                gg1, gg2, _, _ = ctx.adjoint(psi, lam, n, tau, scheme)
+                assert rel(ctx.to_dense(psi), phi0) < 1e-4, (p.name, scheme)
+                sc = max(np.abs(g1).max(), np.abs(g2).max())
+                assert np.abs(gg1 - g1).max() < 1e-3 * sc, (p.name, scheme)
+                assert np.abs(gg2 - g2).max() < 1e-3 * sc, (p.name, scheme)
+                # a later call on the context uses the call's own kinetic unit
+                x = W.random_state((p.M2, p.M1), 29)
+                y = ctx.from_dense(x)
+                ctx.step(y, 1, tau, "strang_kp")
+                assert rel(ctx.to_dense(y), O.step(p, x, tau, "strang_kp", 1)) < 1e-5
+    finally:
+        O.use_fft(False)
 
 
 def test_error_codes(P):
@@ -520,4 +635,6 @@ def test_error_codes(P):
     with pytest.raises(P.LsplitError):
         ctx.step(psi, 1, float("nan"), "strang")
     with pytest.raises(P.LsplitError):
-        ctx.adjoint(psi, psi, 1, 1e-3, "strang_stoch")
+        ctx.adjoint(psi, psi, 1, 1e-3, "cn_strang")
+    with pytest.raises(P.LsplitError):
+        ctx.adjoint(psi, psi, 1, 1e-3, "semi_implicit")

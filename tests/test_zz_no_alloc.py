@@ -1,7 +1,8 @@
 """ls_mass_noalloc: the mass without any allocation inside the library.
 
-Callers that cannot allocate device memory (stream capture, externally managed
-pools) use this entry point; its scratch is a fixed device array.  Checked
+Callers that cannot allocate device memory (hosts whose device memory all
+comes from their own pool, loops that must not touch the allocator) use this
+entry point; its scratch is a fixed device array.  Checked
 against the context-based ls_observables() on two calls in a row, within the
 observables tolerance of the parity tests.  Collected last on purpose.
 """
