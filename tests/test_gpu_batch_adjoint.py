@@ -170,7 +170,7 @@ def test_autograd_overlap_gradient_matches_oracle(P):
             t2 = torch.tensor(th2, requires_grad=True)
             L = overlap_loss(t1, t2, base, phi0, chi, 0.02, 8, "strang", dtype, checkpoint_every=ck)
             L.backward()
-            assert abs(float(L) - Lref) < tol * 10
+            assert abs(float(L.detach()) - Lref) < tol * 10
             sc = max(np.abs(ref1).max(), np.abs(ref2).max())
             assert np.abs(t1.grad.numpy() - ref1).max() < tol * sc * 20, (dtype, ck)
             assert np.abs(t2.grad.numpy() - ref2).max() < tol * sc * 20, (dtype, ck)
@@ -205,7 +205,10 @@ def test_autograd_backward_twice_and_stochastic(P):
         b1, b2 = torch.autograd.grad(L, (t1, t2))
         assert np.abs(a1.numpy() - ref1).max() < 2e-4 * sc, (scheme, ck)
         assert np.abs(a2.numpy() - ref2).max() < 2e-4 * sc, (scheme, ck)
-        assert np.array_equal(a1.numpy(), b1.numpy()) and np.array_equal(a2.numpy(), b2.numpy()), (scheme, ck)
+        # same sweep from phi_T again (the gradient's atomic accumulation
+        # order is not fixed, so agreement is to rounding, not bitwise)
+        np.testing.assert_allclose(b1.numpy(), a1.numpy(), rtol=1e-9, atol=1e-12 * sc)
+        np.testing.assert_allclose(b2.numpy(), a2.numpy(), rtol=1e-9, atol=1e-12 * sc)
 
 
 def test_autograd_reduced_box_500_steps_against_oracle(P):

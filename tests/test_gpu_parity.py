@@ -280,7 +280,10 @@ def test_density_on_line_parity(P, dtype, tol):
         phi = W.random_state((p.M2, p.M1), 18)
         got = ctx.density(ctx.from_dense(phi), x)
         ref = O.density_on_line(p, phi, x)
-        assert rel(got, ref) < tol, (p.name, rel(got, ref))
+        # the FP64 oracle forms k.x in floating point: its own phase error
+        # grows with max |k| |x| (the library's phases are exact fixed point)
+        th = float(np.abs(O.wavevectors(p)).max() * np.abs(x).max())
+        assert rel(got, ref) < tol + (4e-16 * th if dtype == "c128" else 0.0), (p.name, rel(got, ref))
     p = W.config_scale_1d()
     ctx = P.Context(p, dtype)
     psi = ctx.empty()
