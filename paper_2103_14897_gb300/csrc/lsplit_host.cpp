@@ -143,6 +143,7 @@ struct ConvTab {
 struct CachedTab {
   std::shared_ptr<DevBuf> buf;
   double fix_re = 0, fix_im = 0;
+  int B = 0;          // compact-kernel tables: half-width of the kept taps (0: not applicable)
   uint64_t used = 0;
 };
 constexpr size_t kTableCacheCap = 48;
@@ -187,7 +188,9 @@ struct ls_ctx {
   std::vector<double> vhost[2];
   std::map<std::pair<int, uint64_t>, CachedTab> ttab;  // (layer, bits(s)) -> (T - 1)/M table
   std::map<std::pair<int, uint64_t>, CachedTab> ctab;  // convolution-form tables
+  std::map<std::pair<int, uint64_t>, CachedTab> stab;  // compact-kernel taps
   uint64_t tab_clock = 0;
+  int stW[2] = {0, 0};  // slices per tile of the compact-kernel pass (0: no such pass)
   TableKeep* keep = nullptr;  // set while a graph or call is built: receives every table it uses
   bool conv_form[2] = {false, false};
   int mask_mode = LS_MASK_INIT_ONLY;
@@ -318,6 +321,74 @@ const void* phase_table(ls_ctx* c, int layer, double s) {
 // (FP64, exact integer-reduced angles), wrapped into N entries (d >= 0 at d,
 // d < 0 at N + d; with N = 2q - 2 index q - 1 keeps c'_{q-1}), then
 // Khat = FFT_N / N.
+// c'_j = (1/q) sum_p (exp(-i s v_p) - 1) exp(-2 pi i j p / q), j < q: the
+// first column of the circulant P_j(s) - I on a 1D slice (FP64, exact
+// integer-reduced angles, direct sum).
+std::vector<cd> conv_kernel(const ls_ctx* c, int layer, double s) {
+  const std::vector<double>& v = c->vhost[layer - 1];
+  const int q = (int)v.size();
+  std::vector<cd> tm1(q), roots(q), cp(q);
+  for (int p2 = 0; p2 < q; ++p2) {
+    const double h = -0.5 * s * v[p2];
+    tm1[p2] = cd(0.0, 2.0 * std::sin(h)) * cd(std::cos(h), std::sin(h));
+    const double ang = -2.0 * kPi * (double)p2 / (double)q;
+    roots[p2] = cd(std::cos(ang), std::sin(ang));
+  }
+  for (int j = 0; j < q; ++j) {
+    cd acc(0, 0);
+    for (int p2 = 0; p2 < q; ++p2) acc += tm1[p2] * roots[(int)(((int64_t)j * p2) % q)];
+    cp[j] = acc / (double)q;
+  }
+  return cp;
+}
+
+// Compact-kernel taps of P_j(s) - I on a 1D layer: c'_d for |d| <= B with B
+// the smallest of 2, 3, 5, 8 whose dropped l1 tail sum_{|d| > B} |c'_d| (a
+// bound on the operator-norm error of the truncation) is at most 2^-30 for
+// complex64 (64 times below one FP32 rounding of the result; 1000 steps of
+// three factors stay below 1e-6 even if the truncation adds up coherently) or
+// 2^-48 for complex128 (near the FP64 noise floor of the computed kernel), and
+// 2B + 1 <= q.  Returns a table with B = 0 when no class qualifies.
+CachedTab stencil_table(ls_ctx* c, int layer, double s) {
+  uint64_t bits;
+  std::memcpy(&bits, &s, 8);
+  auto key = std::make_pair(layer, bits);
+  auto it = c->stab.find(key);
+  if (it != c->stab.end()) {
+    it->second.used = ++c->tab_clock;
+    if (c->keep && it->second.buf) c->keep->push_back(it->second.buf);
+    return it->second;
+  }
+  CachedTab e;
+  e.used = ++c->tab_clock;
+  const int L = layer - 1;
+  const int q = c->geom[L].qa;
+  if (c->d == 1 && c->stW[L] > 0) {
+    const std::vector<cd> cp = conv_kernel(c, layer, s);
+    const double eps = c->dtype == LS_C64 ? std::ldexp(1.0, -30) : std::ldexp(1.0, -48);
+    for (int B : {2, 3, 5, 8}) {
+      if (2 * B + 1 > q) break;
+      double tail = 0.0;
+      for (int j = 0; j < q; ++j) {
+        const int d = j <= q / 2 ? j : j - q;
+        if (d > B || d < -B) tail += std::abs(cp[j]);
+      }
+      if (tail <= eps) {
+        std::vector<cd> taps(2 * B + 1);
+        for (int k = 0; k <= 2 * B; ++k) taps[k] = cp[((k - B) % q + q) % q];
+        e.buf = std::make_shared<DevBuf>();
+        upload_c(c, *e.buf, taps);
+        e.B = B;
+        break;
+      }
+    }
+  }
+  c->stab[key] = e;
+  if (c->keep && e.buf) c->keep->push_back(e.buf);
+  evict_tables(c->stab);
+  return e;
+}
+
 ConvTab conv_table(ls_ctx* c, int layer, double s) {
   uint64_t bits;
   std::memcpy(&bits, &s, 8);
@@ -332,21 +403,9 @@ ConvTab conv_table(ls_ctx* c, int layer, double s) {
     t.fix_im = it->second.fix_im;
     return t;
   }
-  const std::vector<double>& v = c->vhost[layer - 1];
-  const int q = (int)v.size();
+  const int q = (int)c->vhost[layer - 1].size();
   const int N = c->geom[layer - 1].np;
-  std::vector<cd> tm1(q), roots(q), cp(q);
-  for (int p2 = 0; p2 < q; ++p2) {
-    const double h = -0.5 * s * v[p2];
-    tm1[p2] = cd(0.0, 2.0 * std::sin(h)) * cd(std::cos(h), std::sin(h));
-    const double ang = -2.0 * kPi * (double)p2 / (double)q;
-    roots[p2] = cd(std::cos(ang), std::sin(ang));
-  }
-  for (int j = 0; j < q; ++j) {
-    cd acc(0, 0);
-    for (int p2 = 0; p2 < q; ++p2) acc += tm1[p2] * roots[(int)(((int64_t)j * p2) % q)];
-    cp[j] = acc / (double)q;
-  }
+  const std::vector<cd> cp = conv_kernel(c, layer, s);
   std::vector<cd> K(N, cd(0, 0));
   for (int d = -(q - 1); d <= q - 1; ++d) {
     const int idx = d >= 0 ? d : N + d;
@@ -512,6 +571,35 @@ void choose_launch(ls_ctx* c) {
 
 cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+bool getenv_flag(const char* name) {
+  const char* v = std::getenv(name);
+  return v && v[0] && v[0] != '0';
+}
+
+// Slices per tile of the compact-kernel pass of a 1D layer: the tile (W
+// slices of length q with wrap halos for up to kStencilMaxB taps, rows padded
+// as the kernel lays them out) fits `budget` bytes of shared memory (68 KB:
+// three CTAs per SM next to the kernels' static shared memory; 48 KB: four).
+// Strided tiles take a power of two in [2, 16], so that their 16-byte copies
+// stay inside the row pitch (a multiple of 16 elements).
+// 0: the layer has no compact-kernel pass (2D slices, or LSPLIT_NO_STENCIL).
+constexpr size_t kStencilTileBytes = 68 * 1024;
+constexpr size_t kStencilTileBytes4 = 48 * 1024;
+int stencil_width(const lsk::LayerGeom& g, size_t esize, bool strided, size_t budget = kStencilTileBytes) {
+  if (g.d != 1 || g.qa < 7 || getenv_flag("LSPLIT_NO_STENCIL")) return 0;
+  const int64_t row = ((int64_t)g.qa + 2 * lsk::kStencilMaxB + 1) & ~(int64_t)1;
+  int64_t W = (int64_t)(budget / ((size_t)row * esize));
+  W = std::min<int64_t>(W, strided ? 16 : lsk::kMaxTileSlices);
+  if (strided) {
+    if (W < 2) return 0;
+    int p = 2;
+    while (p * 2 <= W) p *= 2;
+    return p;
+  }
+  if (W < 1) return 0;
+  return (int)std::min<int64_t>(W, std::max<int64_t>(1, g.nslices));
+}
+
 // Joint-cutoff predicate over the box (Sec. 3): fl(0.5 * fl(sum_i fl(u_i^2)))
 // <= Ec with u_i = sum_j fl(B1[i][j] m_j) + sum_j fl(B2[i][j] n_j) accumulated
 // left to right (this file is compiled without contraction).  mask may be
@@ -547,10 +635,6 @@ void enqueue_project(ls_ctx* c, void* psi, cudaStream_t st) {
   else LS_CUDA(lsk::launch_project<double>(psi, m, c->M1, c->M2, c->pitch, st));
 }
 
-bool getenv_flag(const char* name) {
-  const char* v = std::getenv(name);
-  return v && v[0] && v[0] != '0';
-}
 
 lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
   lsk::PassArgs a;
@@ -564,6 +648,14 @@ lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
 }
 
 cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a0, int L, int64_t nitems, cudaStream_t st) {
+  if (a0.sB > 0 && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
+    lsk::PassArgs a = a0;
+    a.W = c->stW[L];
+    a.strided = (L == 1) ? 1 : 0;
+    const int64_t ntiles = (nitems + a.W - 1) / a.W;
+    if (c->dtype == LS_C64) return lsk::launch_stencil<float>(a, ntiles, st);
+    return lsk::launch_stencil<double>(a, ntiles, st);
+  }
   if (c->fast2d[L] && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
     if (c->dtype == LS_C64) return lsk::launch_fast2d<float>(a0, nitems, st);
     return lsk::launch_fast2d<double>(a0, nitems, st);
@@ -850,10 +942,19 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
   // Adjacent layer-1 factors of consecutive Strang steps (separated by one
   // merged kinetic factor) run as one fused pass when the layer takes the
   // convolution form on the fast path or the dedicated 64 x 64 pass.
-  // (Not with the projection: it sits between the two factors.)
+  // (Not with the projection: it sits between the two factors; not when
+  // layer 1 takes the compact-kernel form, which has no fused pass.)
   const bool project = c->mask_mode == LS_MASK_PROJECT_EACH_STEP;
-  if (!stoch && !project && base_scheme(scheme) == LS_STRANG && ((c->conv_form[0] && c->fastW[0] > 0) || c->fast2d[0]) &&
-      !getenv_flag("LSPLIT_NO_FUSE")) {
+  bool st1 = false;
+  for (const PassSpec& q : ps)
+    if (q.layer == 1) {
+      const int64_t S = c->geom[0].nslices;
+      const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
+      st1 = stencil_table(c, 1, stoch ? q.s * (double)S / (double)p : q.s).B > 0;
+      break;
+    }
+  if (!stoch && !project && !st1 && base_scheme(scheme) == LS_STRANG &&
+      ((c->conv_form[0] && c->fastW[0] > 0) || c->fast2d[0]) && !getenv_flag("LSPLIT_NO_FUSE")) {
     std::vector<PassSpec> merged;
     for (size_t i = 0; i < ps.size(); ++i) {
       if (ps[i].layer == 1 && i + 1 < ps.size() && ps[i + 1].layer == 1) {
@@ -880,7 +981,11 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     if (!stoch) {
       a.mode = lsk::MODE_STEP;
       a.T = phase_table(c, q.layer, q.s);
-      if (c->conv_form[L]) {
+      const CachedTab stt = q.fused ? CachedTab() : stencil_table(c, q.layer, q.s);
+      if (stt.B > 0) {
+        a.taps = stt.buf->p;
+        a.sB = stt.B;
+      } else if (c->conv_form[L]) {
         const ConvTab ct = conv_table(c, q.layer, q.s);
         a.Khat = ct.khat->p;
         a.fix0_re = ct.fix_re;
@@ -903,7 +1008,11 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     } else {
       a.mode = lsk::MODE_LAZY;
       a.T = phase_table(c, q.layer, q.s * (double)S / (double)p);
-      if (c->conv_form[L]) {
+      const CachedTab stt = stencil_table(c, q.layer, q.s * (double)S / (double)p);
+      if (stt.B > 0) {
+        a.taps = stt.buf->p;
+        a.sB = stt.B;
+      } else if (c->conv_form[L]) {
         const ConvTab ct = conv_table(c, q.layer, q.s * (double)S / (double)p);
         a.Khat = ct.khat->p;
         a.fix0_re = ct.fix_re;
@@ -952,7 +1061,7 @@ void prepare_tables(ls_ctx* c, int64_t n, double tau, int scheme) {
     const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
     const double sd = stoch ? q.s * (double)S / (double)p : q.s;
     phase_table(c, q.layer, sd);
-    if (c->conv_form[q.layer - 1]) conv_table(c, q.layer, sd);
+    if (stencil_table(c, q.layer, sd).B == 0 && c->conv_form[q.layer - 1]) conv_table(c, q.layer, sd);
   }
 }
 
@@ -1089,6 +1198,9 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     else LS_CUDA(lsk::cn_prepare<double>(block_max));
     if (c->dtype == LS_C64) LS_CUDA(lsk::fast2d_prepare<float>(block_max));
     else LS_CUDA(lsk::fast2d_prepare<double>(block_max));
+    if (c->dtype == LS_C64) LS_CUDA(lsk::stencil_prepare<float>(block_max));
+    else LS_CUDA(lsk::stencil_prepare<double>(block_max));
+    for (int L = 0; L < 2; ++L) c->stW[L] = stencil_width(c->geom[L], c->esize, L == 1);
     for (int L = 0; L < 2; ++L) {
       const lsk::LayerGeom& g = c->geom[L];
       const size_t sm = c->dtype == LS_C64 ? lsk::fast2d_smem_bytes<float>(g) : lsk::fast2d_smem_bytes<double>(g);
@@ -1544,6 +1656,11 @@ struct ls_batch {
   std::vector<int> Wi[2];     // per instance and layer: slices per tile
   std::vector<int> Wg;        // per instance: slices per general layer-1 tile (settle phase)
   std::vector<int> Fi[2];     // per instance and layer: log2 of the fast tile's length (0: general tile)
+  std::vector<int> Si[2];     // per instance and layer: slices per compact-kernel tile (0: none)
+  std::vector<int> Si1[2];    // the same for the compact-only kernel (KIND 1)
+  int minb1 = 4;              // CTAs per SM of the compact-only kernel (3 or 4)
+  size_t smem1 = 0;           // its dynamic shared memory
+  int blocks1 = 0;            // its persistent grid
   DevBuf args, cum, tsteps, counters, status, touch, seedbuf;
   std::vector<int64_t> touch_off;  // per instance: rows at touch_off[i], columns after them
   double timeout_s = 1.0;
@@ -1612,6 +1729,10 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
   return guarded([&]() -> int {
     std::unique_ptr<ls_batch> b(new ls_batch());
     b->dtype = probs[0].dtype;
+    {
+      const char* mb = std::getenv("LSPLIT_STENCIL_MINB");
+      b->minb1 = (mb && std::atoi(mb) == 3) ? 3 : 4;
+    }
     LS_CUDA(cudaGetDevice(&b->device));
     int64_t total = 0;
     for (int32_t i = 0; i < count; ++i) {
@@ -1648,22 +1769,43 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
         }
         b->Wi[L][i] = W;
         smem = std::max(smem, sm);
+        // compact-kernel tiles (used when the taps of a call qualify)
+        const size_t es = b->dtype == LS_C64 ? 8 : 16;
+        const int sw = stencil_width(g, es, L == 1);
+        b->Si[L].push_back(sw);
+        if (sw > 0) {
+          const size_t ss = b->dtype == LS_C64 ? lsk::stencil_smem_bytes<float>(g, sw, lsk::kStencilMaxB)
+                                               : lsk::stencil_smem_bytes<double>(g, sw, lsk::kStencilMaxB);
+          smem = std::max(smem, ss);
+        }
+        const int sw1 = stencil_width(g, es, L == 1, b->minb1 == 4 ? kStencilTileBytes4 : kStencilTileBytes);
+        b->Si1[L].push_back(sw1);
+        if (sw1 > 0) {
+          const size_t ss = b->dtype == LS_C64 ? lsk::stencil_smem_bytes<float>(g, sw1, lsk::kStencilMaxB)
+                                               : lsk::stencil_smem_bytes<double>(g, sw1, lsk::kStencilMaxB);
+          b->smem1 = std::max(b->smem1, ss);
+        }
       }
     }
     int dev_max = 0;
     LS_CUDA(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
     if (smem + 4096 > (size_t)dev_max) throw CudaError{cudaErrorInvalidValue, "batched tile exceeds shared memory"};
     b->smem = smem;
-    int per_sm = 0;
-    {
-      const char* mb = std::getenv("LSPLIT_BATCH_MINB");
-      b->minb = (mb && std::atoi(mb) == 2) ? 2 : 3;
+    int per_sm = 0, per_sm1 = 0;
+    b->minb = 3;
+    if (b->dtype == LS_C64) {
+      LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, 0, b->minb, &per_sm));
+      LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, std::max<size_t>(b->smem1, 16), 1, b->minb1,
+                                        &per_sm1));
+    } else {
+      LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, 0, b->minb, &per_sm));
+      LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, std::max<size_t>(b->smem1, 16), 1, b->minb1,
+                                         &per_sm1));
     }
-    if (b->dtype == LS_C64) LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, b->minb, &per_sm));
-    else LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, b->minb, &per_sm));
     int sms = 0;
     LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
     b->blocks = std::max(1, per_sm) * sms;
+    b->blocks1 = std::max(1, per_sm1) * sms;
     int64_t tt = 0;
     int32_t smax = 1;
     for (int32_t i = 0; i < count; ++i) {
@@ -1824,6 +1966,18 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       std::vector<lsk::PassArgs> args((size_t)npass * ninst), sargs(ninst);
       std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0), scum(ninst + 1, 0);
       const size_t es = b->dtype == LS_C64 ? 8 : 16;
+      // every factor of every instance in the compact-kernel form: the
+      // compact-only kernel (KIND 1) with its own tile widths
+      bool all_compact = !getenv_flag("LSPLIT_BATCH_GENERIC");
+      for (int q = 0; q < npass && all_compact; ++q)
+        for (int i = 0; i < ninst && all_compact; ++i) {
+          ls_ctx* c = b->inst[i];
+          const int L = ps[q].layer - 1;
+          const double sdur = stoch ? ps[q].s * (double)c->geom[L].nslices / (double)sP[(size_t)i * npass + q]
+                                    : ps[q].s;
+          all_compact = b->Si1[L][i] > 0 && stencil_table(c, ps[q].layer, sdur).B > 0;
+        }
+      const int kind = all_compact ? 1 : 0;
       int32_t* touch = static_cast<int32_t*>(b->touch.p);
       for (int q = 0; q < npass; ++q) {
         const int layer = ps[q].layer, L = layer - 1;
@@ -1837,10 +1991,23 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
           a.variant = 1;
           const bool conv = a.fast_logn && c->conv_form[L];
           int64_t tiles;
+          // compact-kernel form when the taps of this duration qualify
+          const double sdur = stoch ? ps[q].s * (double)c->geom[L].nslices /
+                                          (double)sP[(size_t)i * npass + q]
+                                    : ps[q].s;
+          const int sw = kind == 1 ? b->Si1[L][i] : b->Si[L][i];
+          const CachedTab stt = sw > 0 ? stencil_table(c, layer, sdur) : CachedTab();
+          if (stt.B > 0) {
+            a.sB = stt.B;
+            a.taps = stt.buf->p;
+            a.W = sw;
+            a.strided = L == 1 ? 1 : 0;
+            a.fast_logn = 0;
+          }
           if (!stoch) {
             a.mode = lsk::MODE_STEP;
             a.T = phase_table(c, layer, ps[q].s);
-            if (conv) {
+            if (conv && stt.B == 0) {
               const ConvTab ct = conv_table(c, layer, ps[q].s);
               a.Khat = ct.khat->p;
               a.fix0_re = ct.fix_re;
@@ -1852,7 +2019,7 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
             const int32_t pv = sP[(size_t)i * npass + q];
             a.mode = lsk::MODE_LAZY;
             a.T = phase_table(c, layer, ps[q].s * (double)Sv / (double)pv);
-            if (conv) {
+            if (conv && stt.B == 0) {
               const ConvTab ct = conv_table(c, layer, ps[q].s * (double)Sv / (double)pv);
               a.Khat = ct.khat->p;
               a.fix0_re = ct.fix_re;
@@ -1966,7 +2133,8 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       LS_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device));
       ba.timeout_cycles = (long long)(b->timeout_s * (double)std::max(clk_khz, 1000000) * 1e3);
       ba.unmet = b->unmet;
-      ba.minb = b->minb;
+      ba.minb = kind == 1 ? b->minb1 : b->minb;
+      ba.kind = kind;
       cudaGraph_t graph = nullptr;
       LS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
       cudaError_t ce = cudaMemsetAsync(b->counters.p, 0, (size_t)(ninst + 1) * sizeof(unsigned long long), b->cap);
@@ -1975,8 +2143,11 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
         ce = lsk::launch_batch_sampler(sa, static_cast<const uint64_t*>(b->seedbuf.p), (int64_t)ninst * n * npass,
                                        static_cast<int32_t*>(e->lists->p), b->cap);
       if (ce == cudaSuccess)
-        ce = b->dtype == LS_C64 ? lsk::launch_batch<float>(ba, b->nthreads, b->blocks, b->smem, b->cap)
-                                : lsk::launch_batch<double>(ba, b->nthreads, b->blocks, b->smem, b->cap);
+        ce = b->dtype == LS_C64
+                 ? lsk::launch_batch<float>(ba, b->nthreads, kind == 1 ? b->blocks1 : b->blocks,
+                                            kind == 1 ? b->smem1 : b->smem, b->cap)
+                 : lsk::launch_batch<double>(ba, b->nthreads, kind == 1 ? b->blocks1 : b->blocks,
+                                             kind == 1 ? b->smem1 : b->smem, b->cap);
       cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
       if (ce != cudaSuccess || ee != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

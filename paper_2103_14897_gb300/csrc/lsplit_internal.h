@@ -77,7 +77,16 @@ struct PassArgs {
   int32_t variant;         // fast pass: 0 two shared buffers (2 CTAs/SM), 1 one buffer (3 CTAs/SM)
   int32_t fast_logn;       // batched runner: tile on the fast pass of length 2^fast_logn (0: general tile)
   const void* T2;          // fused 2D pass: (T - 1)/M table of the second factor
+  // Compact-kernel form of a potential factor on 1D slices (sB > 0):
+  // (P - I) x = sum_{|d| <= sB} c'_d x_{(i - d) mod q}, the taps c'_d of the
+  // circulant kernel c' = DFT_q(T - 1)/q whose l1 tail beyond sB is below the
+  // working precision; taps holds 2 sB + 1 complex Real values, d = -sB..sB.
+  const void* taps;
+  int32_t sB;
 };
+
+constexpr int kStencilMaxB = 8;       // widest compact kernel (17 taps)
+constexpr int kStencilThreads = 256;
 
 struct ElemArgs {          // elementwise kernels over the whole lifted box
   int d;
@@ -131,6 +140,12 @@ template <typename Real> int fast_max_threads();
 template <typename Real> cudaError_t launch_fast2d(const PassArgs& a, int64_t ntiles, cudaStream_t st);
 template <typename Real> size_t fast2d_smem_bytes(const LayerGeom& g);
 template <typename Real> cudaError_t fast2d_prepare(size_t max_smem);
+// Compact-kernel pass (MODE_STEP / MODE_LAZY) over W slices per CTA of
+// kStencilThreads threads; the tile (W slices with their wrap halos) sits in
+// shared memory.  W must be a power of two for strided slices.
+template <typename Real> cudaError_t launch_stencil(const PassArgs& a, int64_t ntiles, cudaStream_t st);
+template <typename Real> size_t stencil_smem_bytes(const LayerGeom& g, int W, int B);
+template <typename Real> cudaError_t stencil_prepare(size_t max_smem);
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
 cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
 
@@ -159,7 +174,8 @@ struct BatchArgs {
   const PassArgs* settle_args;  // [ninst]
   const int64_t* settle_cum;    // [ninst + 1]
   int64_t settle_items;
-  int32_t minb;                 // register budget variant (2 or 3 CTAs per SM)
+  int32_t minb;                 // CTAs per SM the registers are budgeted for (3, or 4 for KIND 1)
+  int32_t kind;                 // 0: any tile kind; 1: compact-kernel tiles only
   // deterministic Strang with fused layer-1 factors (fused != 0): passes of a
   // call are [first L1] then per step [L2, fused L1 (plain L1 in the last
   // step)]; args kinds [5][ninst]: 0 first L1, 1 L2, 2 fused L1 (fused tile
@@ -186,7 +202,7 @@ cudaError_t launch_batch_sampler(const BatchSamplerArgs& sa, const uint64_t* see
 cudaError_t batch_sampler_prepare(size_t max_block);
 template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
                                                   cudaStream_t st);
-template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int minb,
+template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int kind, int minb,
                                                    int* blocks_per_sm);
 
 // Crank-Nicolson layer factor (Sec. 4.2.1, Eq. (tsCN)) over every slice of

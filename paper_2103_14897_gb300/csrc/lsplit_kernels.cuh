@@ -49,6 +49,19 @@ template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
 
+// Per-slice metadata of the tile a CTA works on (slice index, kinetic
+// quadratic-form coefficients, lazy touch time) and a reduction scratch.  One
+// file-scope block shared by every tile body, so a kernel that can run
+// several tile kinds (the persistent batched runner) holds it once.
+struct TileMeta {
+  int64_t slice[kMaxTileSlices];
+  uint64_t la[kMaxTileSlices], lb[kMaxTileSlices], c0[kMaxTileSlices];
+  int32_t touch[kMaxTileSlices];
+  double2 fix1[kMaxTileSlices];
+  double red[32];
+};
+static __shared__ TileMeta g_tm;
+
 // Shared-memory padding: one spare element after every 16 breaks the
 // power-of-two strides of the first Stockham stages across banks.
 __device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
@@ -105,13 +118,13 @@ template <> __device__ __forceinline__ Phase<float> phase_of<float>(uint64_t t) 
   const float c2h = __fmul_rn(c1, c1), c2l = fmaf(c1, c1, -c2h);
   const float s2h = __fmul_rn(s1, s1), s2l = fmaf(s1, s1, -s2h);
   const float e = __fadd_rn(__fadd_rn(__fadd_rn(c2h, -1.0f), s2h), __fadd_rn(c2l, s2l));
+  // rotate by q quarter turns without branches: odd q swaps (c, s) -> (-s, c),
+  // q & 2 negates both
+  const bool odd = (q & 1) != 0;
+  const uint32_t neg = (q & 2) << 30;
+  const float vx = odd ? -s1 : c1, vy = odd ? c1 : s1;
   Phase<float> p;
-  switch (q & 3) {
-    case 0: p.v = make_float2(c1, s1); break;
-    case 1: p.v = make_float2(-s1, c1); break;
-    case 2: p.v = make_float2(-c1, -s1); break;
-    default: p.v = make_float2(s1, -c1); break;
-  }
+  p.v = make_float2(__uint_as_float(__float_as_uint(vx) ^ neg), __uint_as_float(__float_as_uint(vy) ^ neg));
   p.half_e = 0.5f * e;
   return p;
 }
@@ -404,10 +417,10 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
   C* sml = sm + (size_t)W * g.sb;                         // adjoint: lambda tile
   C* sx = sm + (size_t)W * g.sb * (adj ? 2 : 1);          // saved x (pre-phased)
   C* sxl = sx + (size_t)W * M;                            // adjoint: saved lambda
-  __shared__ int64_t s_slice[kMaxTileSlices];
-  __shared__ uint64_t s_la[kMaxTileSlices], s_lb[kMaxTileSlices], s_c0[kMaxTileSlices];
-  __shared__ int32_t s_touch[kMaxTileSlices];
-  __shared__ double s_red[32];
+  int64_t* s_slice = g_tm.slice;
+  uint64_t *s_la = g_tm.la, *s_lb = g_tm.lb, *s_c0 = g_tm.c0;
+  int32_t* s_touch = g_tm.touch;
+  double* s_red = g_tm.red;
 
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
@@ -842,9 +855,9 @@ __device__ __forceinline__ void fast_tile(const PassArgs& a, int64_t tile, unsig
   const int j = a.strided ? t / W : t % TPS;
   C* bufA = reinterpret_cast<C*>(smraw) + (size_t)w * NBUF * g.sb;
   C* bufB = SINGLE ? bufA : bufA + g.sb;
-  __shared__ int64_t s_slice[kMaxTileSlices];
-  __shared__ uint64_t s_la[kMaxTileSlices], s_c0[kMaxTileSlices];
-  __shared__ int32_t s_touch[kMaxTileSlices];
+  int64_t* s_slice = g_tm.slice;
+  uint64_t *s_la = g_tm.la, *s_c0 = g_tm.c0;
+  int32_t* s_touch = g_tm.touch;
   if (t < W) {
     int64_t s = -1;
     if (a.list) {
@@ -919,7 +932,7 @@ __device__ __forceinline__ void fast_tile(const PassArgs& a, int64_t tile, unsig
     fast_fft<Real, LOGN, true, SINGLE>(v, bufA, bufB, flip, tw, j);
     if constexpr (FUSED) {
       // x1 = K(mid) (x + c1): through shared memory, then the second factor
-      __shared__ C s_fix1[kMaxTileSlices];
+      C* s_fix1 = reinterpret_cast<C*>(g_tm.fix1);
       if (t < W && s_slice[t] >= 0) {
         C f;
         f.x = (Real)a.fix0_re;
@@ -1632,6 +1645,269 @@ template <typename Real> cudaError_t fast_prepare(size_t max_smem) {
 }
 template <typename Real> int fast_max_threads() { return 256; }
 
+// ---------------------------------------------------------------- compact-kernel pass
+// P_j(s) - I is the circulant of c' = DFT_q(T - 1)/q on a 1D slice of length q
+// (the kernel the convolution form transforms).  For band-limited potentials
+// and short durations c' decays fast (for v = a cos, c'_d is the Bessel
+// coefficient J_d(s a) up to a unit phase, minus the identity at d = 0), and
+// the host keeps the taps |d| <= BV when the l1 norm of the dropped ones, a
+// bound on the operator-norm error, is below working precision.  A tile holds
+// W whole slices in shared memory, each with a wrap halo on both sides, so
+// x_{(i - d) mod q} is a plain offset:
+//   16-byte asynchronous copies global -> shared (through L2) -> kinetic
+//   pre-phase in shared memory -> halos -> y_i = x_i + sum_d c'_d x_{i-d}
+//   (the identity plus the small correction, as in the transform forms) ->
+//   kinetic post-phase -> store.
+// Shared-memory layout, H = the halo width rounded up to even, so that element
+// pairs (and complex128 elements) are 16-byte aligned:
+//   contiguous slices (rows): slice w at w * Ls, Ls = q + 2H rounded up to
+//   even, element i at + H + i;
+//   strided slices (adjacent columns, W a power of two >= 2): element (w, i)
+//   at (i + H) W + w.
+// Consecutive threads touch consecutive words in every phase.
+__host__ __device__ constexpr int stencil_halo(int bv) { return (bv + 1) & ~1; }
+__host__ __device__ inline int stencil_row_len(int q, int bv) {
+  const int l = q + 2 * stencil_halo(bv);
+  return (l + 1) & ~1;
+}
+
+// Kinetic phase turns q(m) = A m^2 + la m + c0 (64-bit fixed point) along a
+// thread's elements m, m + st, m + 2 st, ... by exact second differences
+// modulo 2^64; scale(u) walks u q instead.
+struct KinWalk {
+  uint64_t q, d, dd;
+  __device__ __forceinline__ void init(uint64_t A, uint64_t la, uint64_t c0, int64_t m, int64_t st) {
+    const uint64_t um = (uint64_t)m, us = (uint64_t)st;
+    q = A * (um * um) + la * um + c0;
+    d = A * (2 * um * us + us * us) + la * us;
+    dd = 2 * A * (us * us);
+  }
+  __device__ __forceinline__ void scale(uint64_t u) {
+    q *= u;
+    d *= u;
+    dd *= u;
+  }
+  __device__ __forceinline__ void next() {
+    q += d;
+    d += dd;
+  }
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <typename Real, int MODE, bool CG, int BV>
+__device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  using C = typename CT<Real>::C;
+  constexpr bool lazy = (MODE == MODE_LAZY);
+  constexpr int NTAP = 2 * BV + 1;
+  constexpr int H = stencil_halo(BV);
+  constexpr int PAIR = sizeof(C) == 8 ? 2 : 1;   // elements per 16-byte copy
+  const LayerGeom& g = a.g;
+  const int W = a.W, q = g.qa;
+  const bool strided = a.strided != 0;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = NT >> 5;
+  C* sm = reinterpret_cast<C*>(smraw);
+  int64_t* s_slice = g_tm.slice;
+  uint64_t *s_la = g_tm.la, *s_c0 = g_tm.c0;
+  int32_t* s_touch = g_tm.touch;
+  if (tid < W) {
+    int64_t sl = -1;
+    if (a.list) {
+      const int64_t li = tile * W + tid;
+      if (li < a.nlist) sl = a.list[li];
+    } else {
+      sl = tile * W + tid;
+      if (sl >= g.nslices) sl = -1;
+    }
+    s_slice[tid] = sl;
+    uint64_t la = 0, c0 = 0;
+    int32_t touch = 0;
+    if (sl >= 0) {
+      const uint64_t ua = (uint64_t)(sl + g.olo_a);
+      la = g.X_aa * ua;
+      c0 = g.C_aa * (ua * ua);
+      if (lazy) touch = CG ? __ldcg(a.touch_own + sl) : a.touch_own[sl];
+    }
+    s_la[tid] = la;
+    s_c0[tid] = c0;
+    s_touch[tid] = touch;
+  }
+  C t[NTAP];
+  {
+    const C* tp = reinterpret_cast<const C*>(a.taps);
+#pragma unroll
+    for (int k = 0; k < NTAP; ++k) t[k] = tp[k];
+  }
+  __syncthreads();
+  C* psi = reinterpret_cast<C*>(a.psi);
+  const int Ls = stencil_row_len(q, BV);
+  // ---- load: 16-byte copies global -> shared through L2
+  if (!strided) {
+    // rows, one warp per row (a row starts 128-byte aligned and its pitch
+    // padding covers the pair past an odd end)
+    const int np2 = (q + PAIR - 1) / PAIR;
+    for (int w = warp; w < W; w += nwarp) {
+      const int64_t sl = s_slice[w];
+      if (sl < 0) continue;
+      const C* src = psi + sl * g.slice_stride;
+      C* dst = sm + w * Ls + H;
+      for (int j = lane; j < np2; j += 32) cp_async16(dst + PAIR * j, src + (int64_t)PAIR * j);
+    }
+    cp_async_wait_all();
+  } else if (!a.list) {
+    // adjacent columns: one copy moves PAIR columns of a row; tiles start at a
+    // multiple of W columns and never read past the row pitch
+    const int wp = W / PAIR;
+    const int wsh = 31 - __clz(wp);
+    const int64_t s0 = tile * (int64_t)W;
+    for (int e = tid; e < q * wp; e += NT) {
+      const int i = e >> wsh, k = e & (wp - 1);
+      cp_async16(sm + (i + H) * W + PAIR * k, psi + s0 + (int64_t)i * g.ea + PAIR * k);
+    }
+    cp_async_wait_all();
+  } else {
+    // sampled (scattered) columns: plain loads, the column fixed per thread
+    const int wsh = 31 - __clz(W);
+    const int w = tid & (W - 1), di = NT >> wsh;
+    const int64_t sl = s_slice[w];
+#pragma unroll 4
+    for (int i = tid >> wsh; i < q; i += di) {
+      C x = czero<C>();
+      if (sl >= 0) x = ldpsi<CG>(psi + sl + (int64_t)i * g.ea);
+      sm[(i + H) * W + w] = x;
+    }
+  }
+  __syncthreads();
+  // Element ownership in the phase and stencil sweeps: contiguous tiles: one
+  // warp per slice, lane i, i + 32, ...; strided tiles: the column w = tid mod W
+  // fixed per thread, rows i = tid / W + k NT / W.  Every thread walks its
+  // kinetic phase turns by second differences along its elements.
+  const int wsh = 31 - __clz(W);
+  const int sw0 = strided ? (tid & (W - 1)) : warp;             // first slice of this thread
+  const int swd = strided ? W : nwarp;                          // slice step (strided: one slice only)
+  const int ei0 = strided ? (tid >> wsh) : lane;                // first element
+  const int eid = strided ? (NT >> wsh) : 32;                   // element step
+  const int sstep = strided ? W : 1;                            // shared-memory step between neighbours
+  // ---- kinetic pre-phase (first pass of a call) or the pending lazy phase
+  if (lazy || a.units_pre != 0) {
+    for (int w = sw0; w < W; w += swd) {
+      const int64_t sl = s_slice[w];
+      if (sl >= 0) {
+        KinWalk kw;
+        kw.init(g.A_aa, s_la[w], s_c0[w], g.lo_a + ei0, eid);
+        if (!lazy) kw.scale((uint64_t)0 - (uint64_t)a.units_pre);
+        const int32_t tw = s_touch[w];
+        C* p = sm + (strided ? (ei0 + H) * W + w : w * Ls + H + ei0);
+        for (int i = ei0; i < q; i += eid) {
+          if (lazy) {
+            const int32_t t2 = CG ? __ldcg(a.touch_other + i) : a.touch_other[i];
+            const int64_t units = (int64_t)a.now - (int64_t)(tw > t2 ? tw : t2);
+            if (units != 0) *p = apply_phase<Real>(*p, phase_of<Real>((uint64_t)0 - (uint64_t)units * kw.q));
+          } else {
+            *p = apply_phase<Real>(*p, phase_of<Real>(kw.q));
+          }
+          p += eid * sstep;
+          kw.next();
+        }
+      }
+      if (strided) break;
+    }
+    __syncthreads();
+  }
+  // ---- wrap halos: i in [-BV, 0) takes x_{i + q}, i in [q, q + BV) takes x_{i - q}
+  for (int e = tid; e < W * 2 * BV; e += NT) {
+    const int w = e / (2 * BV), k = e - w * (2 * BV);
+    const int dst = k < BV ? k - BV : q + (k - BV);
+    const int src = k < BV ? q - BV + k : k - BV;
+    if (strided) sm[(dst + H) * W + w] = sm[(src + H) * W + w];
+    else sm[w * Ls + H + dst] = sm[w * Ls + H + src];
+  }
+  __syncthreads();
+  // ---- y = x + sum_d c'_d x_{i-d}, post-phase, store
+  {
+    const bool post = !lazy && a.units_post != 0;
+    for (int w = sw0; w < W; w += swd) {
+      const int64_t sl = s_slice[w];
+      if (sl >= 0) {
+        KinWalk kw;
+        kw.init(g.A_aa, s_la[w], s_c0[w], g.lo_a + ei0, eid);
+        kw.scale((uint64_t)0 - (uint64_t)a.units_post);
+        const C* sp = sm + (strided ? (ei0 + H) * W + w : w * Ls + H + ei0);
+        C* gp = psi + sl * g.slice_stride + (int64_t)ei0 * g.ea;
+        const int64_t gstep = (int64_t)eid * g.ea;
+        for (int i = ei0; i < q; i += eid) {
+          C acc = czero<C>();
+#pragma unroll
+          for (int k = 0; k < NTAP; ++k) {
+            // tap k is d = k - BV: x_{i - d} sits (BV - k) steps from x_i
+            const C v = sp[(BV - k) * sstep];
+            acc.x = fma(t[k].x, v.x, fma(-t[k].y, v.y, acc.x));
+            acc.y = fma(t[k].x, v.y, fma(t[k].y, v.x, acc.y));
+          }
+          C y = cadd(sp[0], acc);
+          if (post) y = apply_phase<Real>(y, phase_of<Real>(kw.q));
+          *gp = y;
+          sp += eid * sstep;
+          gp += gstep;
+          kw.next();
+        }
+      }
+      if (strided) break;
+    }
+  }
+  if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
+}
+
+template <typename Real, int MODE, int BV>
+__global__ void __launch_bounds__(kStencilThreads, sizeof(Real) == 4 ? 3 : 2)
+pass_stencil_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  stencil_tile<Real, MODE, false, BV>(a, (int64_t)blockIdx.x, smraw);
+}
+
+template <typename Real> size_t stencil_smem_bytes(const LayerGeom& g, int W, int B) {
+  using C = typename CT<Real>::C;
+  return (size_t)W * stencil_row_len(g.qa, B) * sizeof(C);
+}
+
+template <typename Real, int BV>
+static cudaError_t launch_stencil_b(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
+  const size_t smem = stencil_smem_bytes<Real>(a.g, a.W, BV);
+  if (a.mode == MODE_LAZY) pass_stencil_kernel<Real, MODE_LAZY, BV><<<(unsigned)ntiles, kStencilThreads, smem, st>>>(a);
+  else pass_stencil_kernel<Real, MODE_STEP, BV><<<(unsigned)ntiles, kStencilThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Real> cudaError_t launch_stencil(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (a.g.d != 1 || a.W < 1 || a.W > kMaxTileSlices || (a.strided && (a.W < 2 || (a.W & (a.W - 1)))) ||
+      2 * a.sB + 1 > a.g.qa || (reinterpret_cast<uintptr_t>(a.psi) & 15) != 0 ||
+      (a.strided ? (a.g.ea & 1) : (a.g.slice_stride & 1)) != 0)
+    return cudaErrorInvalidValue;
+  switch (a.sB) {
+    case 2: return launch_stencil_b<Real, 2>(a, ntiles, st);
+    case 3: return launch_stencil_b<Real, 3>(a, ntiles, st);
+    case 5: return launch_stencil_b<Real, 5>(a, ntiles, st);
+    case 8: return launch_stencil_b<Real, 8>(a, ntiles, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename Real> cudaError_t stencil_prepare(size_t max_smem) {
+  cudaError_t e = cudaSuccess;
+#define LS_SPREP(BV)                                                                                   \
+  if (e == cudaSuccess) e = allow_smem(pass_stencil_kernel<Real, MODE_STEP, BV>, max_smem);           \
+  if (e == cudaSuccess) e = allow_smem(pass_stencil_kernel<Real, MODE_LAZY, BV>, max_smem);
+  LS_SPREP(2) LS_SPREP(3) LS_SPREP(5) LS_SPREP(8)
+#undef LS_SPREP
+  return e;
+}
+
 // ---------------------------------------------------------------- batched runner
 // 256-thread CTAs (the block size the host uses for every tile shape); 1D
 // slices only; STOCH selects the stochastic (lazy + settle) or deterministic
@@ -1646,6 +1922,23 @@ __device__ __noinline__ void batch_fast_tile_n(const PassArgs& a, int64_t tile, 
 template <typename Real, int BPT, int MODE>
 __device__ __noinline__ void batch_general_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   pass_tile<Real, BPT, MODE, true, true>(a, tile, smraw);
+}
+
+template <typename Real, int MODE, int BV>
+__device__ __noinline__ void batch_stencil_tile_n(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  stencil_tile<Real, MODE, true, BV>(a, tile, smraw);
+}
+
+// Compact-kernel tile of a batched work item (sB > 0); false: not this form.
+template <typename Real, int MODE>
+__device__ __forceinline__ bool batch_stencil_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  switch (a.sB) {
+    case 2: batch_stencil_tile_n<Real, MODE, 2>(a, tile, smraw); return true;
+    case 3: batch_stencil_tile_n<Real, MODE, 3>(a, tile, smraw); return true;
+    case 5: batch_stencil_tile_n<Real, MODE, 5>(a, tile, smraw); return true;
+    case 8: batch_stencil_tile_n<Real, MODE, 8>(a, tile, smraw); return true;
+    default: return false;
+  }
 }
 
 // Fast tile of a batched work item (complex64, transform length 2^9..2^11,
@@ -1672,7 +1965,26 @@ __device__ __forceinline__ bool batch_fast_tile(const PassArgs& a, int64_t tile,
   return false;
 }
 
-template <typename Real, int BPT, bool STOCH, int MINB>
+// One work item's tile.  KIND 0: any tile kind (compact-kernel, fast and
+// general transform tiles as calls with the kernel's whole register budget);
+// KIND 1: compact-kernel tiles only, inlined (a batch whose every factor takes
+// that form: no transform code, lighter registers, more CTAs per SM).
+template <typename Real, int BPT, int MODE, int KIND>
+__device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  if constexpr (KIND == 1) {
+    switch (a.sB) {
+      case 2: stencil_tile<Real, MODE, true, 2>(a, tile, smraw); break;
+      case 3: stencil_tile<Real, MODE, true, 3>(a, tile, smraw); break;
+      case 5: stencil_tile<Real, MODE, true, 5>(a, tile, smraw); break;
+      default: stencil_tile<Real, MODE, true, 8>(a, tile, smraw); break;
+    }
+  } else {
+    if (!batch_stencil_tile<Real, MODE>(a, tile, smraw) && !batch_fast_tile<Real, MODE>(a, tile, smraw))
+      batch_general_tile<Real, BPT, MODE>(a, tile, smraw);
+  }
+}
+
+template <typename Real, int BPT, bool STOCH, int MINB, int KIND>
 __global__ void __launch_bounds__(256, MINB)
 batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1829,11 +2141,9 @@ batch_kernel(const BatchArgs b) {
     }
     if constexpr (STOCH) {
       if (s_settle) batch_general_tile<Real, BPT, MODE_KIN>(s_args, s_tile, smraw);
-      else if (!batch_fast_tile<Real, MODE_LAZY>(s_args, s_tile, smraw))
-        batch_general_tile<Real, BPT, MODE_LAZY>(s_args, s_tile, smraw);
+      else batch_tile<Real, BPT, MODE_LAZY, KIND>(s_args, s_tile, smraw);
     } else {
-      if (!batch_fast_tile<Real, MODE_STEP>(s_args, s_tile, smraw))
-        batch_general_tile<Real, BPT, MODE_STEP>(s_args, s_tile, smraw);
+      batch_tile<Real, BPT, MODE_STEP, KIND>(s_args, s_tile, smraw);
       if (b.fused && s_pass == 2 && s_args.Khat2 == nullptr) {
         // fused item without a fused tile body: the second factor on the same
         // slices, after the first is complete in this CTA
@@ -1843,8 +2153,7 @@ batch_kernel(const BatchArgs b) {
         int* dst = reinterpret_cast<int*>(&s_args);
         for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / 4); w += blockDim.x) dst[w] = src[w];
         __syncthreads();
-        if (!batch_fast_tile<Real, MODE_STEP>(s_args, s_tile, smraw))
-          batch_general_tile<Real, BPT, MODE_STEP>(s_args, s_tile, smraw);
+        batch_tile<Real, BPT, MODE_STEP, KIND>(s_args, s_tile, smraw);
       }
     }
     __threadfence();
@@ -1853,35 +2162,43 @@ batch_kernel(const BatchArgs b) {
   }
 }
 
-template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
-                                                  cudaStream_t st) {
-  if (b.minb == 3) {
-    if (b.stoch) batch_kernel<Real, 2, true, 3><<<nblocks, nthreads, smem, st>>>(b);
-    else batch_kernel<Real, 2, false, 3><<<nblocks, nthreads, smem, st>>>(b);
-  } else {
-    if (b.stoch) batch_kernel<Real, 2, true, 2><<<nblocks, nthreads, smem, st>>>(b);
-    else batch_kernel<Real, 2, false, 2><<<nblocks, nthreads, smem, st>>>(b);
-  }
+// Variants: (KIND 0, 3 CTAs per SM), (KIND 1, 3 or 4 CTAs per SM).
+template <typename Real, int KIND, int MINB>
+static cudaError_t launch_batch_v(const BatchArgs& b, int nthreads, int nblocks, size_t smem, cudaStream_t st) {
+  if (b.stoch) batch_kernel<Real, 2, true, MINB, KIND><<<nblocks, nthreads, smem, st>>>(b);
+  else batch_kernel<Real, 2, false, MINB, KIND><<<nblocks, nthreads, smem, st>>>(b);
   return cudaGetLastError();
 }
 
-template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int minb,
-                                                   int* blocks_per_sm) {
-  cudaError_t e = cudaSuccess;
-  int a = 0, c = 0;
-  if (minb == 3) {
-    e = allow_smem(batch_kernel<Real, 2, false, 3>, max_smem);
-    if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 3>, max_smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, 3>, nthreads, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, 3>, nthreads, smem);
-  } else {
-    e = allow_smem(batch_kernel<Real, 2, false, 2>, max_smem);
-    if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, 2>, max_smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, 2>, nthreads, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, 2>, nthreads, smem);
+template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
+                                                  cudaStream_t st) {
+  if (b.kind == 1) {
+    if (b.minb == 4) return launch_batch_v<Real, 1, 4>(b, nthreads, nblocks, smem, st);
+    return launch_batch_v<Real, 1, 3>(b, nthreads, nblocks, smem, st);
   }
+  return launch_batch_v<Real, 0, 3>(b, nthreads, nblocks, smem, st);
+}
+
+template <typename Real, int KIND, int MINB>
+static cudaError_t batch_prepare_v(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm) {
+  int a = 0, c = 0;
+  cudaError_t e = allow_smem(batch_kernel<Real, 2, false, MINB, KIND>, max_smem);
+  if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, MINB, KIND>, max_smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, MINB, KIND>, nthreads, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, MINB, KIND>, nthreads, smem);
   *blocks_per_sm = a < c ? a : c;
   return e;
+}
+
+template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int kind, int minb,
+                                                   int* blocks_per_sm) {
+  if (kind == 1) {
+    if (minb == 4) return batch_prepare_v<Real, 1, 4>(max_smem, nthreads, smem, blocks_per_sm);
+    return batch_prepare_v<Real, 1, 3>(max_smem, nthreads, smem, blocks_per_sm);
+  }
+  return batch_prepare_v<Real, 0, 3>(max_smem, nthreads, smem, blocks_per_sm);
 }
 
 #define LS_FOR_MODES(X, R, B) \
@@ -2246,6 +2563,9 @@ cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st) {
   template size_t fast_smem_bytes<R>(const LayerGeom&, int, int);                                        \
   template cudaError_t fast_prepare<R>(size_t);                                                          \
   template int fast_max_threads<R>();                                                                    \
+  template cudaError_t launch_stencil<R>(const PassArgs&, int64_t, cudaStream_t);                        \
+  template size_t stencil_smem_bytes<R>(const LayerGeom&, int, int);                                     \
+  template cudaError_t stencil_prepare<R>(size_t);                                                       \
   template cudaError_t launch_fast2d<R>(const PassArgs&, int64_t, cudaStream_t);                         \
   template size_t fast2d_smem_bytes<R>(const LayerGeom&);                                                \
   template cudaError_t fast2d_prepare<R>(size_t);
@@ -2254,9 +2574,9 @@ LS_INST(LS_INST_REAL)
 #endif
 #ifdef LS_INST_BATCH
 template cudaError_t launch_batch<float>(const BatchArgs&, int, int, size_t, cudaStream_t);
-template cudaError_t batch_prepare<float>(size_t, int, size_t, int, int*);
+template cudaError_t batch_prepare<float>(size_t, int, size_t, int, int, int*);
 template cudaError_t launch_batch<double>(const BatchArgs&, int, int, size_t, cudaStream_t);
-template cudaError_t batch_prepare<double>(size_t, int, size_t, int, int*);
+template cudaError_t batch_prepare<double>(size_t, int, size_t, int, int, int*);
 #endif
 
 }  // namespace lsk

@@ -30,9 +30,12 @@ def uneven_batch():
     return W.batch_1d(count=7, seed=4, nmin=3, nmax=40) + [W.bilayer_1d(64, 3, 1.0, 0.7, ecut=1e9)]
 
 
+@pytest.mark.parametrize("form", ["compact", "fft"])
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
 @pytest.mark.parametrize("scheme", ["strang", "lie", "strang_kp"])
-def test_batched_runner_parity(P, dtype, tol, scheme):
+def test_batched_runner_parity(P, dtype, tol, scheme, form, monkeypatch):
+    if form == "fft":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     probs = uneven_batch()
     b = P.Batch(probs, dtype)
     psi = b.empty()
@@ -50,9 +53,12 @@ def test_batched_runner_parity(P, dtype, tol, scheme):
         assert rel(b.get_dense(psi, i), ref) < tol * 4
 
 
+@pytest.mark.parametrize("form", ["compact", "fft"])
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
 @pytest.mark.parametrize("scheme", ["strang_stoch", "lie_stoch"])
-def test_batched_runner_stochastic_parity(P, dtype, tol, scheme):
+def test_batched_runner_stochastic_parity(P, dtype, tol, scheme, form, monkeypatch):
+    if form == "fft":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     """Stochastic schemes inside the persistent launch: instance i samples with
     seed + i; lists drawn on the device; lazy kinetic phases and a settle phase."""
     probs = uneven_batch()
@@ -72,9 +78,13 @@ def test_batched_runner_stochastic_parity(P, dtype, tol, scheme):
 
 
 @pytest.mark.parametrize("scheme", ["strang", "lie", "strang_stoch"])
-def test_batched_fast_tiles_parity(P, scheme):
-    """Lengths 129..1001 (transforms of 256..2048 points): most slices run on
-    the register-resident fast tiles inside the persistent launch."""
+@pytest.mark.parametrize("form", ["compact", "fft"])
+def test_batched_fast_tiles_parity(P, scheme, form, monkeypatch):
+    """Lengths 129..1001 (transforms of 256..2048 points): every slice runs on
+    the compact-kernel tiles, or (transform form) most on the register-resident
+    fast tiles inside the persistent launch."""
+    if form == "fft":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     probs = W.batch_1d(count=5, seed=8, nmin=64, nmax=500)
     b = P.Batch(probs, "c64")
     psi = b.empty()

@@ -75,13 +75,17 @@ def test_gaussian_initial_state(P, dtype):
         assert np.all(got[~O.index_mask(p)] == 0)
 
 
-@pytest.mark.parametrize("form", ["convolution", "bluestein"])
+@pytest.mark.parametrize("form", ["compact", "convolution", "bluestein"])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 @pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
 def test_step_parity_1d(P, dtype, scheme, form, monkeypatch):
-    """Both forms of the potential factor for odd slice lengths: the cyclic
-    convolution through one power-of-two transform pair, and the chirp-z
-    (Bluestein) transform to the real-space grid and back."""
+    """Every form of the potential factor on 1D slices: the compact kernel
+    (the taps of P - I above the working precision; the default where they
+    qualify), the cyclic convolution through one power-of-two transform pair,
+    and the chirp-z (Bluestein) transform to the real-space grid and back
+    (powers of two: the radix transforms)."""
+    if form != "compact":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     if form == "bluestein":
         monkeypatch.setenv("LSPLIT_TRANSFORM", "bluestein")
     for p in problems_1d() + [W.bilayer_1d(1024, 20, 1.1, 0.7, ecut=1e9)]:
@@ -151,7 +155,8 @@ def problems_strided_4096():
 
 
 @pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
-def test_step_parity_strided_4096(P, scheme):
+def test_step_parity_strided_4096(P, scheme, monkeypatch):
+    monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")   # the transform form of this pass
     O.use_fft(True)
     try:
         for p in problems_strided_4096():
@@ -344,9 +349,12 @@ def test_stochastic_samples_bit_exact(P):
                 assert np.array_equal(got[i], ref)
 
 
+@pytest.mark.parametrize("form", ["compact", "fft"])
 @pytest.mark.parametrize("scheme", ["lie_stoch", "strang_stoch"])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_stochastic_step_parity(P, scheme, dtype):
+def test_stochastic_step_parity(P, scheme, dtype, form, monkeypatch):
+    if form == "fft":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     for p in [W.bilayer_1d(16, 20, 1.3, 0.9, ecut=1e9), W.config_small_1d(), W.twisted_2d(q=8, hmax=2)]:
         ctx = P.Context(p, dtype)
         x = W.random_state((p.M2, p.M1), 6)
@@ -368,12 +376,16 @@ def long_slice_boxes():
             W.bilayer_1d(16, 1024, 0.9, 1.3, ecut=1e9, name="33x2049")]
 
 
+@pytest.mark.parametrize("form", ["compact", "fft"])
 @pytest.mark.parametrize("scheme", ["lie_stoch", "strang_stoch"])
-def test_stochastic_long_slices(P, scheme):
+def test_stochastic_long_slices(P, scheme, form, monkeypatch):
     """The stochastic schemes where the sampled slices are 2049 long, so the
     lazy kinetic phases run inside the fast 1D passes (the sampled-slice path
     of the 2049 x 2049 workload): 3 steps, then 2 more continuing the sample
-    sequence, against the oracle."""
+    sequence, against the oracle.  Both the compact-kernel form and the
+    transform (fast pass) form."""
+    if form == "fft":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     O.use_fft(True)
     try:
         for p in long_slice_boxes():
@@ -390,11 +402,15 @@ def test_stochastic_long_slices(P, scheme):
         O.use_fft(False)
 
 
-def test_long_run_1000_steps_long_slices(P):
+@pytest.mark.parametrize("form", ["compact", "fft"])
+def test_long_run_1000_steps_long_slices(P, form, monkeypatch):
     """The 1000-step gate through the headline kernels: 1000 Strang steps of
     tau = 5e-4 on boxes whose rows or columns are 2049 long (fused layer-1
     fast pass, two-column strided pass), random full-spectrum state:
-    rel-L2 <= 1e-4 and | ||psi|| - 1 | <= 1e-5 against the oracle."""
+    rel-L2 <= 1e-4 and | ||psi|| - 1 | <= 1e-5 against the oracle; the
+    compact-kernel form and the transform form."""
+    if form == "fft":
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     O.use_fft(True)
     try:
         for p in long_slice_boxes():
@@ -499,23 +515,32 @@ def test_long_run_1000_steps(P):
 
 
 def test_fast_and_generic_paths_agree(P, monkeypatch):
-    """The register-resident fast pass and the generic pass compute the same
-    step (both are also checked against the oracle above)."""
+    """The compact-kernel pass, the register-resident fast pass and the
+    generic pass compute the same step (each is also checked against the
+    oracle above)."""
     for p in [W.config_scale_1d(), W.bilayer_1d(128, 200, 1.1, 0.6, ecut=1e9)]:
         x = W.random_state((p.M2, p.M1), 9)
+        c = P.Context(p, "c64")
+        monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
         a = P.Context(p, "c64")
         monkeypatch.setenv("LSPLIT_NO_FAST", "1")
         b = P.Context(p, "c64")
         monkeypatch.delenv("LSPLIT_NO_FAST")
+        monkeypatch.delenv("LSPLIT_NO_STENCIL")
+        pc = c.from_dense(x)
+        c.step(pc, 3, 5e-4, "strang")
         pa, pb = a.from_dense(x), b.from_dense(x)
         a.step(pa, 3, 5e-4, "strang")
         b.step(pb, 3, 5e-4, "strang")
         assert rel(a.to_dense(pa), b.to_dense(pb)) < 3e-6
+        assert rel(c.to_dense(pc), b.to_dense(pb)) < 3e-6
 
 
 def test_fused_strang_passes_match_unfused(P, monkeypatch):
     """Adjacent layer-1 factors of consecutive Strang steps fused into one pass
-    give the same state as separate passes (and the oracle)."""
+    give the same state as separate passes (and the oracle); transform forms
+    (the compact-kernel form has no fused pass)."""
+    monkeypatch.setenv("LSPLIT_NO_STENCIL", "1")
     import dataclasses
     rect = dataclasses.replace(W.twisted_2d(q=64, hmax=3), lo2=(-4, -2), q2=(8, 4), ecut=1e9, name="64x64-fused")
     for p in [W.config_scale_1d(), W.bilayer_1d(256, 40, 1.4, 0.6, ecut=1e9), rect]:
