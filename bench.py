@@ -495,6 +495,7 @@ def run_ours(args):
     obs = b.observables(psi)
     norm_err = max(abs(o["norm"] - 1.0) for o in obs)
 
+    tuned = b.config()
     # the persistent batched kernel is the only kernel of a deterministic call
     # (one graph launch: a counter reset and the kernel)
     npass = {"lie": 2, "strang_kp": 2}.get(scheme.replace("_stoch", ""), 3)
@@ -569,6 +570,7 @@ def run_ours(args):
             "e2e": {"value": e2e, "unit": "DOF-steps/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "note": "ls_batch_step_host: pinned host buffer in, steps, host buffer out, per bench step"},
             "gpu_launches": args.steps,
+            "autotuner": tuned,
             "sub_workloads": subs,
             "clocks": clk.summary(),
         }

@@ -28,7 +28,7 @@ EXPORTS = ["ls_last_error", "ls_create", "ls_destroy", "ls_layout", "ls_index_se
            "ls_init_gaussian", "ls_step", "ls_step_host", "ls_observables", "ls_density", "ls_samples",
            "ls_adjoint", "ls_mass_noalloc", "ls_batch_create", "ls_batch_destroy", "ls_batch_layout",
            "ls_batch_init_gaussian", "ls_batch_step", "ls_batch_step_host", "ls_batch_observables",
-           "ls_batch_debug"]
+           "ls_batch_config", "ls_batch_debug"]
 
 
 class LsProblem(C.Structure):
@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH):
     lib.ls_batch_step.argtypes = [vp, vp, i64, dbl, i32, u64, u64, vp]
     lib.ls_batch_observables.argtypes = [vp, vp, C.POINTER(LsObs), vp]
     lib.ls_batch_debug.argtypes = [vp, i32, dbl]
+    lib.ls_batch_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
+                                    C.POINTER(C.c_float), C.POINTER(i32)]
     for name in EXPORTS[1:]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -360,6 +362,15 @@ class Batch:
         out = (LsObs * len(self.probs))()
         _check(_lib.ls_batch_observables(self._h, _ptr(psi), out, _stream_handle(stream)))
         return [{"norm": o.norm, "energy": o.energy} for o in out]
+
+    def config(self) -> dict:
+        """ls_batch_config: the compact-kernel launch configuration and the
+        autotuner's last timings (ms per two steps per candidate)."""
+        t, c, tb, tu, n = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(8)
+        ms = (C.c_float * 8)()
+        _check(_lib.ls_batch_config(self._h, C.byref(t), C.byref(c), C.byref(tb), C.byref(tu), ms, C.byref(n)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "tile_bytes": tb.value, "tuned": bool(tu.value),
+                "tune_ms": [ms[k] for k in range(min(n.value, 8))]}
 
     def debug(self, unmet: bool, timeout_s: float = 1.0):
         _check(_lib.ls_batch_debug(self._h, 1 if unmet else 0, float(timeout_s)))

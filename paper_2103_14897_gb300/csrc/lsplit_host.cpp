@@ -24,6 +24,7 @@
 #include <list>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1658,9 +1659,15 @@ struct ls_batch {
   std::vector<int> Fi[2];     // per instance and layer: log2 of the fast tile's length (0: general tile)
   std::vector<int> Si[2];     // per instance and layer: slices per compact-kernel tile (0: none)
   std::vector<int> Si1[2];    // the same for the compact-only kernel (KIND 1)
-  int minb1 = 4;              // CTAs per SM of the compact-only kernel (3 or 4)
+  int minb1 = 3;              // CTAs per SM of the compact-only kernel
+  int nthreads1 = 256;        // its threads per CTA
+  size_t budget1 = 0;         // its tile budget (bytes of shared memory)
   size_t smem1 = 0;           // its dynamic shared memory
   int blocks1 = 0;            // its persistent grid
+  bool tune = true;           // time the compact-only configurations on first use
+  bool transform_form = false;  // the tuner chose the transform (FFT) forms over the compact kernels
+  int tuned = 0;              // 1 once a tuned configuration is in place
+  std::vector<float> tune_ms; // the last tuning's times (ms per two steps) per candidate
   DevBuf args, cum, tsteps, counters, status, touch, seedbuf;
   std::vector<int64_t> touch_off;  // per instance: rows at touch_off[i], columns after them
   double timeout_s = 1.0;
@@ -1710,6 +1717,388 @@ void batch_units(int scheme, int32_t u[4][3][2], int& npass, double& unit, doubl
   }
 }
 
+// Capture the persistent launch of n steps on psi (tables uploaded first; the
+// graph keeps them alive).  The compact-only kernel (KIND 1) runs when every
+// factor of every instance takes the compact-kernel form.
+std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme) {
+  const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+  const int ninst = (int)b->inst.size();
+    std::unique_ptr<ls_batch::Cached> e(new ls_batch::Cached());
+    e->psi = psi;
+    e->scheme = scheme;
+    e->tau = tau;
+    e->n = n;
+    lsk::BatchArgs ba;
+    std::memset(&ba, 0, sizeof(ba));
+    int npass = 0;
+    double u = 0;
+    batch_units(scheme, ba.units, npass, u, tau);
+    ba.npass = npass;
+    ba.ninst = ninst;
+    ba.nsteps = (int32_t)n;
+    ba.stoch = stoch ? 1 : 0;
+    std::vector<PassSpec> ps;
+    int32_t et = 0;
+    build_passes(scheme, tau, 1, ps, et);
+    ba.now_mul = et;
+    for (int q = 0; q < npass; ++q) ba.now_off[q] = ps[q].now;
+    // sampled-slice lists: [instance][step][pass][p entries]
+    std::vector<int32_t> sS((size_t)ninst * npass), sP((size_t)ninst * npass);
+    std::vector<int64_t> sBase(ninst), sStep(ninst), sOff((size_t)ninst * npass);
+    int64_t ltot = 0;
+    int32_t smax = 1;
+    for (int i = 0; i < ninst; ++i) {
+      ls_ctx* c = b->inst[i];
+      int64_t step_len = 0;
+      for (int q = 0; q < npass; ++q) {
+        const int64_t Sv = c->geom[ps[q].layer - 1].nslices;
+        const int32_t pv = std::max<int32_t>(1, (int32_t)(Sv / c->frac_den));
+        sS[(size_t)i * npass + q] = (int32_t)Sv;
+        sP[(size_t)i * npass + q] = pv;
+        sOff[(size_t)i * npass + q] = step_len;
+        step_len += pv;
+        smax = std::max<int32_t>(smax, (int32_t)Sv);
+      }
+      sBase[i] = ltot;
+      sStep[i] = step_len;
+      ltot += step_len * n;
+    }
+    e->lists = std::make_shared<DevBuf>();
+    if (stoch) e->lists->alloc((size_t)ltot * sizeof(int32_t));
+    for (ls_ctx* c : b->inst) c->keep = &e->tables;
+    struct KeepScope {
+      ls_batch* b;
+      ~KeepScope() {
+        for (ls_ctx* c : b->inst) c->keep = nullptr;
+      }
+    } ks{b};
+    std::vector<lsk::PassArgs> args((size_t)npass * ninst), sargs(ninst);
+    std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0), scum(ninst + 1, 0);
+    const size_t es = b->dtype == LS_C64 ? 8 : 16;
+    // every factor of every instance in the compact-kernel form: the
+    // compact-only kernel (KIND 1) with its own tile widths
+    bool all_compact = !getenv_flag("LSPLIT_BATCH_GENERIC") && !b->transform_form;
+    for (int q = 0; q < npass && all_compact; ++q)
+      for (int i = 0; i < ninst && all_compact; ++i) {
+        ls_ctx* c = b->inst[i];
+        const int L = ps[q].layer - 1;
+        const double sdur = stoch ? ps[q].s * (double)c->geom[L].nslices / (double)sP[(size_t)i * npass + q]
+                                  : ps[q].s;
+        all_compact = b->Si1[L][i] > 0 && stencil_table(c, ps[q].layer, sdur).B > 0;
+      }
+    const int kind = all_compact ? 1 : 0;
+    int32_t* touch = static_cast<int32_t*>(b->touch.p);
+    for (int q = 0; q < npass; ++q) {
+      const int layer = ps[q].layer, L = layer - 1;
+      int64_t acc = 0;
+      for (int i = 0; i < ninst; ++i) {
+        ls_ctx* c = b->inst[i];
+        set_kinetic(c, u);
+        lsk::PassArgs a = base_args(c, L, static_cast<char*>(psi) + b->off[i] * es);
+        a.W = b->Wi[L][i];
+        a.fast_logn = b->Fi[L][i];
+        a.variant = 1;
+        const bool conv = a.fast_logn && c->conv_form[L];
+        int64_t tiles;
+        // compact-kernel form when the taps of this duration qualify
+        const double sdur = stoch ? ps[q].s * (double)c->geom[L].nslices /
+                                        (double)sP[(size_t)i * npass + q]
+                                  : ps[q].s;
+        const int sw = b->transform_form ? 0 : kind == 1 ? b->Si1[L][i] : b->Si[L][i];
+        const CachedTab stt = sw > 0 ? stencil_table(c, layer, sdur) : CachedTab();
+        if (stt.B > 0) {
+          a.sB = stt.B;
+          a.taps = stt.buf->p;
+          a.W = sw;
+          a.strided = L == 1 ? 1 : 0;
+          a.fast_logn = 0;
+        }
+        if (!stoch) {
+          a.mode = lsk::MODE_STEP;
+          a.T = phase_table(c, layer, ps[q].s);
+          if (conv && stt.B == 0) {
+            const ConvTab ct = conv_table(c, layer, ps[q].s);
+            a.Khat = ct.khat->p;
+            a.fix0_re = ct.fix_re;
+            a.fix0_im = ct.fix_im;
+          }
+          tiles = (c->geom[L].nslices + a.W - 1) / a.W;
+        } else {
+          const int64_t Sv = c->geom[L].nslices;
+          const int32_t pv = sP[(size_t)i * npass + q];
+          a.mode = lsk::MODE_LAZY;
+          a.T = phase_table(c, layer, ps[q].s * (double)Sv / (double)pv);
+          if (conv && stt.B == 0) {
+            const ConvTab ct = conv_table(c, layer, ps[q].s * (double)Sv / (double)pv);
+            a.Khat = ct.khat->p;
+            a.fix0_re = ct.fix_re;
+            a.fix0_im = ct.fix_im;
+          }
+          a.list = static_cast<const int32_t*>(e->lists->p) + sBase[i] + sOff[(size_t)i * npass + q];
+          a.nlist = pv;
+          a.list_step = sStep[i];
+          int32_t* rows = touch + b->touch_off[i];
+          int32_t* cols = rows + c->M2;
+          a.touch_own = L == 0 ? rows : cols;
+          a.touch_other = L == 0 ? cols : rows;
+          tiles = (pv + a.W - 1) / a.W;
+        }
+        args[(size_t)q * ninst + i] = a;
+        cum[(size_t)q * (ninst + 1) + i] = acc;
+        acc += tiles;
+        tsteps[i] += tiles;
+      }
+      cum[(size_t)q * (ninst + 1) + ninst] = acc;
+      ba.pass_items[q] = acc;
+      ba.step_items += acc;
+    }
+    if (stoch) {
+      int64_t acc = 0;
+      for (int i = 0; i < ninst; ++i) {
+        ls_ctx* c = b->inst[i];
+        lsk::PassArgs a = base_args(c, 0, static_cast<char*>(psi) + b->off[i] * es);
+        a.mode = lsk::MODE_KIN;
+        a.W = b->Wg[i];
+        int32_t* rows = touch + b->touch_off[i];
+        a.touch_own = rows;
+        a.touch_other = rows + c->M2;
+        a.now = (int32_t)(et * n);
+        sargs[i] = a;
+        scum[i] = acc;
+        acc += (c->M2 + a.W - 1) / a.W;
+      }
+      scum[ninst] = acc;
+      ba.settle_items = acc;
+    }
+    // deterministic Strang: adjacent layer-1 factors of consecutive steps
+    // become one item (a fused tile, or the two factors back to back)
+    const bool fused = !stoch && scheme == LS_STRANG && !getenv_flag("LSPLIT_NO_FUSE");
+    std::vector<int64_t> t1(ninst), t2(ninst);
+    if (fused) {
+      std::vector<lsk::PassArgs> fa((size_t)5 * ninst);
+      for (int i = 0; i < ninst; ++i) {
+        const lsk::PassArgs& l1 = args[(size_t)0 * ninst + i];
+        const lsk::PassArgs& l2 = args[(size_t)1 * ninst + i];
+        auto with = [](lsk::PassArgs a, int64_t pre, int64_t post) {
+          a.units_pre = pre;
+          a.units_post = post;
+          return a;
+        };
+        fa[(size_t)0 * ninst + i] = with(l1, 1, 3);
+        fa[(size_t)1 * ninst + i] = with(l2, 0, 3);
+        lsk::PassArgs f = with(l1, 0, 2);
+        if (l1.fast_logn && l1.Khat) {
+          f.units_post = 3;
+          f.Khat2 = l1.Khat;      // the second factor has the same duration tau/2
+          f.fix2_re = l1.fix0_re;
+          f.fix2_im = l1.fix0_im;
+          f.units_mid = 2;
+        }
+        fa[(size_t)2 * ninst + i] = f;
+        fa[(size_t)3 * ninst + i] = with(l1, 0, 1);
+        fa[(size_t)4 * ninst + i] = with(l1, 0, 3);
+        t1[i] = cum[(size_t)0 * (ninst + 1) + i + 1] - cum[(size_t)0 * (ninst + 1) + i];
+        t2[i] = cum[(size_t)1 * (ninst + 1) + i + 1] - cum[(size_t)1 * (ninst + 1) + i];
+      }
+      args.swap(fa);
+    }
+    e->args = std::make_shared<DevBuf>();
+    const size_t b_args = args.size() * sizeof(lsk::PassArgs), b_cum = cum.size() * sizeof(int64_t);
+    const size_t b_ts = tsteps.size() * sizeof(int64_t), b_sargs = sargs.size() * sizeof(lsk::PassArgs);
+    const size_t b_scum = scum.size() * sizeof(int64_t);
+    const size_t b_si = sS.size() * sizeof(int32_t), b_sl = sBase.size() * sizeof(int64_t);
+    const size_t b_so = sOff.size() * sizeof(int64_t);
+    const size_t b_t12 = (size_t)ninst * sizeof(int64_t);
+    const size_t total_b = b_args + b_cum + b_ts + b_sargs + b_scum + 2 * b_si + 2 * b_sl + b_so + 2 * b_t12;
+    e->args->alloc(total_b);
+    char* base = static_cast<char*>(e->args->p);
+    size_t o = 0;
+    auto put = [&](const void* src, size_t bytes) -> void* {
+      void* d = base + o;
+      LS_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
+      o += bytes;
+      return d;
+    };
+    ba.args = static_cast<const lsk::PassArgs*>(put(args.data(), b_args));
+    ba.settle_args = static_cast<const lsk::PassArgs*>(put(sargs.data(), b_sargs));
+    ba.cum = static_cast<const int64_t*>(put(cum.data(), b_cum));
+    ba.tiles_step = static_cast<const int64_t*>(put(tsteps.data(), b_ts));
+    ba.settle_cum = static_cast<const int64_t*>(put(scum.data(), b_scum));
+    ba.tiles1 = static_cast<const int64_t*>(put(t1.data(), b_t12));
+    ba.tiles2 = static_cast<const int64_t*>(put(t2.data(), b_t12));
+    ba.fused = fused ? 1 : 0;
+    lsk::BatchSamplerArgs sa;
+    sa.base = static_cast<const int64_t*>(put(sBase.data(), b_sl));
+    sa.step_len = static_cast<const int64_t*>(put(sStep.data(), b_sl));
+    sa.pass_off = static_cast<const int64_t*>(put(sOff.data(), b_so));
+    sa.S = static_cast<const int32_t*>(put(sS.data(), b_si));
+    sa.p = static_cast<const int32_t*>(put(sP.data(), b_si));
+    sa.npf = npass;
+    sa.nsteps = (int32_t)n;
+    sa.Smax = smax;
+    ba.counters = static_cast<unsigned long long*>(b->counters.p);
+    ba.status = static_cast<int32_t*>(b->status.p);
+    int clk_khz = 0;
+    LS_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device));
+    ba.timeout_cycles = (long long)(b->timeout_s * (double)std::max(clk_khz, 1000000) * 1e3);
+    ba.unmet = b->unmet;
+    ba.minb = kind == 1 ? b->minb1 : b->minb;
+    ba.kind = kind;
+    cudaGraph_t graph = nullptr;
+    LS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaMemsetAsync(b->counters.p, 0, (size_t)(ninst + 1) * sizeof(unsigned long long), b->cap);
+    if (ce == cudaSuccess && stoch) ce = cudaMemsetAsync(b->touch.p, 0, b->touch.bytes, b->cap);
+    if (ce == cudaSuccess && stoch)
+      ce = lsk::launch_batch_sampler(sa, static_cast<const uint64_t*>(b->seedbuf.p), (int64_t)ninst * n * npass,
+                                     static_cast<int32_t*>(e->lists->p), b->cap);
+    if (ce == cudaSuccess)
+      ce = b->dtype == LS_C64
+               ? lsk::launch_batch<float>(ba, kind == 1 ? b->nthreads1 : b->nthreads,
+                                          kind == 1 ? b->blocks1 : b->blocks, kind == 1 ? b->smem1 : b->smem, b->cap)
+               : lsk::launch_batch<double>(ba, kind == 1 ? b->nthreads1 : b->nthreads,
+                                           kind == 1 ? b->blocks1 : b->blocks, kind == 1 ? b->smem1 : b->smem, b->cap);
+    cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      throw CudaError{ce != cudaSuccess ? ce : ee, "batched graph capture"};
+    }
+    cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) throw CudaError{ie, "cudaGraphInstantiate"};
+  return e;
+}
+
+// Compact-only kernel configuration: threads per CTA, CTAs per SM and the
+// tile budget that lets that many CTAs share an SM; recomputes the tile widths,
+// shared memory and the persistent grid.
+void apply_compact_config(ls_batch* b, int nt, int mb) {
+  b->nthreads1 = nt;
+  b->minb1 = mb;
+  b->budget1 = mb == 3 ? kStencilTileBytes : mb == 4 ? kStencilTileBytes4 : mb == 6 ? 32 * 1024 : 22 * 1024;
+  b->smem1 = 0;
+  const size_t es = b->dtype == LS_C64 ? 8 : 16;
+  for (int L = 0; L < 2; ++L)
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      const lsk::LayerGeom& g = b->inst[i]->geom[L];
+      const int sw1 = stencil_width(g, es, L == 1, b->budget1);
+      b->Si1[L][i] = sw1;
+      if (sw1 > 0) {
+        const size_t ss = b->dtype == LS_C64 ? lsk::stencil_smem_bytes<float>(g, sw1, lsk::kStencilMaxB)
+                                             : lsk::stencil_smem_bytes<double>(g, sw1, lsk::kStencilMaxB);
+        b->smem1 = std::max(b->smem1, ss);
+      }
+    }
+  int dev_max = 0, per_sm = 0, sms = 0;
+  LS_CUDA(cudaDeviceGetAttribute(&dev_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+  LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  if (b->dtype == LS_C64)
+    LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, nt, std::max<size_t>(b->smem1, 16), 1, mb, &per_sm));
+  else
+    LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, nt, std::max<size_t>(b->smem1, 16), 1, mb, &per_sm));
+  b->blocks1 = std::max(1, per_sm) * sms;
+}
+
+bool batch_all_compact(ls_batch* b, double tau, int32_t scheme) {
+  if (getenv_flag("LSPLIT_BATCH_GENERIC") || b->transform_form) return false;
+  const bool stoch = scheme == LS_LIE_STOCH || scheme == LS_STRANG_STOCH;
+  std::vector<PassSpec> ps;
+  int32_t et = 0;
+  build_passes(scheme, tau, 1, ps, et);
+  for (const PassSpec& q : ps)
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      ls_ctx* c = b->inst[i];
+      const int L = q.layer - 1;
+      const int64_t S = c->geom[L].nslices;
+      const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
+      const double sd = stoch ? q.s * (double)S / (double)p : q.s;
+      if (b->Si1[L][i] <= 0 || stencil_table(c, q.layer, sd).B == 0) return false;
+    }
+  return true;
+}
+
+// Process-wide record of tuned configurations, keyed by the batch's shapes,
+// dtype, scheme and time step.
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tuned;   // (threads, CTAs per SM); threads 0: transform forms
+
+std::string tune_key(const ls_batch* b, double tau, int32_t scheme) {
+  std::string k = std::to_string(b->dtype) + ":" + std::to_string(scheme) + ":";
+  uint64_t bits;
+  std::memcpy(&bits, &tau, 8);
+  k += std::to_string(bits) + ":";
+  for (const ls_ctx* c : b->inst) k += std::to_string(c->M1) + "x" + std::to_string(c->M2) + ",";
+  return k;
+}
+
+// Autotuner of the batched launch: on the first call of a (scheme, tau) whose
+// factors all take the compact-kernel form, time every configuration of the
+// compact-only kernel (threads per CTA, CTAs per SM, tile budget) and the
+// transform forms (the generic kernel with fast and general transform tiles)
+// for two steps on a scratch copy of psi, and keep the fastest; the choice is
+// cached for the process.  Off with LSPLIT_TUNE=0, a forced
+// LSPLIT_STENCIL_CFG, or the timeout test hook armed.
+void maybe_tune(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, cudaStream_t st) {
+  if (!b->tune || b->unmet || b->dtype != LS_C64 || !batch_all_compact(b, tau, scheme)) return;
+  const std::string key = tune_key(b, tau, scheme);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      if (it->second.first == 0) b->transform_form = true;
+      else if (it->second.first != b->nthreads1 || it->second.second != b->minb1)
+        apply_compact_config(b, it->second.first, it->second.second);
+      b->tuned = 1;
+      return;
+    }
+  }
+  (void)n;
+  const size_t bytes = (size_t)b->off.back() * 8;
+  DevBuf scratch;
+  scratch.alloc(bytes);
+  LS_CUDA(cudaMemcpyAsync(scratch.p, psi, bytes, cudaMemcpyDeviceToDevice, st));
+  LS_CUDA(cudaStreamSynchronize(st));
+  const int cand[5][2] = {{256, 3}, {256, 4}, {128, 6}, {128, 8}, {0, 0}};
+  float best = 0.f;
+  int bi = -1;
+  b->tune_ms.clear();
+  for (int ci = 0; ci < 5; ++ci) {
+    if (cand[ci][0] > 0) apply_compact_config(b, cand[ci][0], cand[ci][1]);
+    b->transform_form = cand[ci][0] == 0;
+    std::unique_ptr<ls_batch::Cached> g = build_batch_graph(b, scratch.p, 2, tau, scheme);
+    cudaEvent_t e0, e1;
+    LS_CUDA(cudaEventCreate(&e0));
+    LS_CUDA(cudaEventCreate(&e1));
+    float tot = 0.f;
+    cudaError_t err = cudaGraphLaunch(g->exec, st);  // warm-up
+    for (int r = 0; r < 3 && err == cudaSuccess; ++r) {
+      err = cudaEventRecord(e0, st);
+      if (err == cudaSuccess) err = cudaGraphLaunch(g->exec, st);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) throw CudaError{err, "autotuner timing"};
+    b->tune_ms.push_back(tot / 3);
+    if (bi < 0 || tot < best) {
+      best = tot;
+      bi = ci;
+    }
+  }
+  // the timing launches advanced the scratch copy only; reset the status word
+  LS_CUDA(cudaMemsetAsync(b->status.p, 0, sizeof(int32_t), st));
+  LS_CUDA(cudaStreamSynchronize(st));
+  b->transform_form = cand[bi][0] == 0;
+  if (cand[bi][0] > 0) apply_compact_config(b, cand[bi][0], cand[bi][1]);
+  b->tuned = 1;
+  b->graphs.clear();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = std::make_pair(cand[bi][0], cand[bi][1]);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1730,8 +2119,22 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     std::unique_ptr<ls_batch> b(new ls_batch());
     b->dtype = probs[0].dtype;
     {
-      const char* mb = std::getenv("LSPLIT_STENCIL_MINB");
-      b->minb1 = (mb && std::atoi(mb) == 3) ? 3 : 4;
+      // compact-only kernel configuration (threads per CTA, CTAs per SM):
+      // (128, 6) until the autotuner picks; LSPLIT_STENCIL_CFG forces one and
+      // turns the tuning off, as does LSPLIT_TUNE=0
+      const char* cf = std::getenv("LSPLIT_STENCIL_CFG");
+      int nt = 128, mb = 6;
+      if (cf) {
+        b->tune = false;
+        if (std::sscanf(cf, "%d,%d", &nt, &mb) != 2) nt = 128, mb = 6;
+      }
+      const char* tv = std::getenv("LSPLIT_TUNE");
+      if (tv && tv[0] == '0') b->tune = false;
+      if (b->dtype != LS_C64) nt = 256, mb = 3;
+      if (!((nt == 256 && (mb == 3 || mb == 4)) || (nt == 128 && (mb == 6 || mb == 8)))) nt = 128, mb = 6;
+      b->nthreads1 = nt;
+      b->minb1 = mb;
+      b->budget1 = mb == 3 ? kStencilTileBytes : mb == 4 ? kStencilTileBytes4 : mb == 6 ? 32 * 1024 : 22 * 1024;
     }
     LS_CUDA(cudaGetDevice(&b->device));
     int64_t total = 0;
@@ -1778,7 +2181,7 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
                                                : lsk::stencil_smem_bytes<double>(g, sw, lsk::kStencilMaxB);
           smem = std::max(smem, ss);
         }
-        const int sw1 = stencil_width(g, es, L == 1, b->minb1 == 4 ? kStencilTileBytes4 : kStencilTileBytes);
+        const int sw1 = stencil_width(g, es, L == 1, b->budget1);
         b->Si1[L].push_back(sw1);
         if (sw1 > 0) {
           const size_t ss = b->dtype == LS_C64 ? lsk::stencil_smem_bytes<float>(g, sw1, lsk::kStencilMaxB)
@@ -1795,12 +2198,12 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
     b->minb = 3;
     if (b->dtype == LS_C64) {
       LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, smem, 0, b->minb, &per_sm));
-      LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads, std::max<size_t>(b->smem1, 16), 1, b->minb1,
+      LS_CUDA(lsk::batch_prepare<float>((size_t)dev_max, b->nthreads1, std::max<size_t>(b->smem1, 16), 1, b->minb1,
                                         &per_sm1));
     } else {
       LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, smem, 0, b->minb, &per_sm));
-      LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads, std::max<size_t>(b->smem1, 16), 1, b->minb1,
-                                         &per_sm1));
+      LS_CUDA(lsk::batch_prepare<double>((size_t)dev_max, b->nthreads1, std::max<size_t>(b->smem1, 16), 1,
+                                         b->minb1, &per_sm1));
     }
     int sms = 0;
     LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -1883,6 +2286,22 @@ int ls_batch_observables(ls_batch* b, const void* psi, ls_obs* out, void* stream
   return LS_OK;
 }
 
+int ls_batch_config(const ls_batch* b, int32_t* threads, int32_t* ctas_per_sm, int64_t* tile_bytes, int32_t* tuned,
+                    float* tune_ms, int32_t* ntimes) {
+  if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (threads) *threads = b->transform_form ? 0 : b->nthreads1;
+  if (ctas_per_sm) *ctas_per_sm = b->minb1;
+  if (tile_bytes) *tile_bytes = (int64_t)b->budget1;
+  if (tuned) *tuned = b->tuned;
+  if (ntimes) {
+    const int32_t cap = *ntimes;
+    *ntimes = (int32_t)b->tune_ms.size();
+    if (tune_ms)
+      for (int32_t k = 0; k < cap && k < *ntimes; ++k) tune_ms[k] = b->tune_ms[k];
+  }
+  return LS_OK;
+}
+
 int ls_batch_debug(ls_batch* b, int32_t unmet_dependency, double timeout_seconds) {
   if (!b) return fail(LS_ERR_STATE, "batch is NULL");
   if (!(timeout_seconds > 0) || timeout_seconds > 60) return fail(LS_ERR_INVALID, "timeout must be in (0, 60] s");
@@ -1914,248 +2333,8 @@ int ls_batch_step(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme,
       if (e->psi == psi && e->scheme == scheme && e->tau == tau && e->n == n) ge = e.get();
     const int ninst = (int)b->inst.size();
     if (!ge) {
-      std::unique_ptr<ls_batch::Cached> e(new ls_batch::Cached());
-      e->psi = psi;
-      e->scheme = scheme;
-      e->tau = tau;
-      e->n = n;
-      lsk::BatchArgs ba;
-      std::memset(&ba, 0, sizeof(ba));
-      int npass = 0;
-      double u = 0;
-      batch_units(scheme, ba.units, npass, u, tau);
-      ba.npass = npass;
-      ba.ninst = ninst;
-      ba.nsteps = (int32_t)n;
-      ba.stoch = stoch ? 1 : 0;
-      std::vector<PassSpec> ps;
-      int32_t et = 0;
-      build_passes(scheme, tau, 1, ps, et);
-      ba.now_mul = et;
-      for (int q = 0; q < npass; ++q) ba.now_off[q] = ps[q].now;
-      // sampled-slice lists: [instance][step][pass][p entries]
-      std::vector<int32_t> sS((size_t)ninst * npass), sP((size_t)ninst * npass);
-      std::vector<int64_t> sBase(ninst), sStep(ninst), sOff((size_t)ninst * npass);
-      int64_t ltot = 0;
-      int32_t smax = 1;
-      for (int i = 0; i < ninst; ++i) {
-        ls_ctx* c = b->inst[i];
-        int64_t step_len = 0;
-        for (int q = 0; q < npass; ++q) {
-          const int64_t Sv = c->geom[ps[q].layer - 1].nslices;
-          const int32_t pv = std::max<int32_t>(1, (int32_t)(Sv / c->frac_den));
-          sS[(size_t)i * npass + q] = (int32_t)Sv;
-          sP[(size_t)i * npass + q] = pv;
-          sOff[(size_t)i * npass + q] = step_len;
-          step_len += pv;
-          smax = std::max<int32_t>(smax, (int32_t)Sv);
-        }
-        sBase[i] = ltot;
-        sStep[i] = step_len;
-        ltot += step_len * n;
-      }
-      e->lists = std::make_shared<DevBuf>();
-      if (stoch) e->lists->alloc((size_t)ltot * sizeof(int32_t));
-      for (ls_ctx* c : b->inst) c->keep = &e->tables;
-      struct KeepScope {
-        ls_batch* b;
-        ~KeepScope() {
-          for (ls_ctx* c : b->inst) c->keep = nullptr;
-        }
-      } ks{b};
-      std::vector<lsk::PassArgs> args((size_t)npass * ninst), sargs(ninst);
-      std::vector<int64_t> cum((size_t)npass * (ninst + 1), 0), tsteps(ninst, 0), scum(ninst + 1, 0);
-      const size_t es = b->dtype == LS_C64 ? 8 : 16;
-      // every factor of every instance in the compact-kernel form: the
-      // compact-only kernel (KIND 1) with its own tile widths
-      bool all_compact = !getenv_flag("LSPLIT_BATCH_GENERIC");
-      for (int q = 0; q < npass && all_compact; ++q)
-        for (int i = 0; i < ninst && all_compact; ++i) {
-          ls_ctx* c = b->inst[i];
-          const int L = ps[q].layer - 1;
-          const double sdur = stoch ? ps[q].s * (double)c->geom[L].nslices / (double)sP[(size_t)i * npass + q]
-                                    : ps[q].s;
-          all_compact = b->Si1[L][i] > 0 && stencil_table(c, ps[q].layer, sdur).B > 0;
-        }
-      const int kind = all_compact ? 1 : 0;
-      int32_t* touch = static_cast<int32_t*>(b->touch.p);
-      for (int q = 0; q < npass; ++q) {
-        const int layer = ps[q].layer, L = layer - 1;
-        int64_t acc = 0;
-        for (int i = 0; i < ninst; ++i) {
-          ls_ctx* c = b->inst[i];
-          set_kinetic(c, u);
-          lsk::PassArgs a = base_args(c, L, static_cast<char*>(psi) + b->off[i] * es);
-          a.W = b->Wi[L][i];
-          a.fast_logn = b->Fi[L][i];
-          a.variant = 1;
-          const bool conv = a.fast_logn && c->conv_form[L];
-          int64_t tiles;
-          // compact-kernel form when the taps of this duration qualify
-          const double sdur = stoch ? ps[q].s * (double)c->geom[L].nslices /
-                                          (double)sP[(size_t)i * npass + q]
-                                    : ps[q].s;
-          const int sw = kind == 1 ? b->Si1[L][i] : b->Si[L][i];
-          const CachedTab stt = sw > 0 ? stencil_table(c, layer, sdur) : CachedTab();
-          if (stt.B > 0) {
-            a.sB = stt.B;
-            a.taps = stt.buf->p;
-            a.W = sw;
-            a.strided = L == 1 ? 1 : 0;
-            a.fast_logn = 0;
-          }
-          if (!stoch) {
-            a.mode = lsk::MODE_STEP;
-            a.T = phase_table(c, layer, ps[q].s);
-            if (conv && stt.B == 0) {
-              const ConvTab ct = conv_table(c, layer, ps[q].s);
-              a.Khat = ct.khat->p;
-              a.fix0_re = ct.fix_re;
-              a.fix0_im = ct.fix_im;
-            }
-            tiles = (c->geom[L].nslices + a.W - 1) / a.W;
-          } else {
-            const int64_t Sv = c->geom[L].nslices;
-            const int32_t pv = sP[(size_t)i * npass + q];
-            a.mode = lsk::MODE_LAZY;
-            a.T = phase_table(c, layer, ps[q].s * (double)Sv / (double)pv);
-            if (conv && stt.B == 0) {
-              const ConvTab ct = conv_table(c, layer, ps[q].s * (double)Sv / (double)pv);
-              a.Khat = ct.khat->p;
-              a.fix0_re = ct.fix_re;
-              a.fix0_im = ct.fix_im;
-            }
-            a.list = static_cast<const int32_t*>(e->lists->p) + sBase[i] + sOff[(size_t)i * npass + q];
-            a.nlist = pv;
-            a.list_step = sStep[i];
-            int32_t* rows = touch + b->touch_off[i];
-            int32_t* cols = rows + c->M2;
-            a.touch_own = L == 0 ? rows : cols;
-            a.touch_other = L == 0 ? cols : rows;
-            tiles = (pv + a.W - 1) / a.W;
-          }
-          args[(size_t)q * ninst + i] = a;
-          cum[(size_t)q * (ninst + 1) + i] = acc;
-          acc += tiles;
-          tsteps[i] += tiles;
-        }
-        cum[(size_t)q * (ninst + 1) + ninst] = acc;
-        ba.pass_items[q] = acc;
-        ba.step_items += acc;
-      }
-      if (stoch) {
-        int64_t acc = 0;
-        for (int i = 0; i < ninst; ++i) {
-          ls_ctx* c = b->inst[i];
-          lsk::PassArgs a = base_args(c, 0, static_cast<char*>(psi) + b->off[i] * es);
-          a.mode = lsk::MODE_KIN;
-          a.W = b->Wg[i];
-          int32_t* rows = touch + b->touch_off[i];
-          a.touch_own = rows;
-          a.touch_other = rows + c->M2;
-          a.now = (int32_t)(et * n);
-          sargs[i] = a;
-          scum[i] = acc;
-          acc += (c->M2 + a.W - 1) / a.W;
-        }
-        scum[ninst] = acc;
-        ba.settle_items = acc;
-      }
-      // deterministic Strang: adjacent layer-1 factors of consecutive steps
-      // become one item (a fused tile, or the two factors back to back)
-      const bool fused = !stoch && scheme == LS_STRANG && !getenv_flag("LSPLIT_NO_FUSE");
-      std::vector<int64_t> t1(ninst), t2(ninst);
-      if (fused) {
-        std::vector<lsk::PassArgs> fa((size_t)5 * ninst);
-        for (int i = 0; i < ninst; ++i) {
-          const lsk::PassArgs& l1 = args[(size_t)0 * ninst + i];
-          const lsk::PassArgs& l2 = args[(size_t)1 * ninst + i];
-          auto with = [](lsk::PassArgs a, int64_t pre, int64_t post) {
-            a.units_pre = pre;
-            a.units_post = post;
-            return a;
-          };
-          fa[(size_t)0 * ninst + i] = with(l1, 1, 3);
-          fa[(size_t)1 * ninst + i] = with(l2, 0, 3);
-          lsk::PassArgs f = with(l1, 0, 2);
-          if (l1.fast_logn && l1.Khat) {
-            f.units_post = 3;
-            f.Khat2 = l1.Khat;      // the second factor has the same duration tau/2
-            f.fix2_re = l1.fix0_re;
-            f.fix2_im = l1.fix0_im;
-            f.units_mid = 2;
-          }
-          fa[(size_t)2 * ninst + i] = f;
-          fa[(size_t)3 * ninst + i] = with(l1, 0, 1);
-          fa[(size_t)4 * ninst + i] = with(l1, 0, 3);
-          t1[i] = cum[(size_t)0 * (ninst + 1) + i + 1] - cum[(size_t)0 * (ninst + 1) + i];
-          t2[i] = cum[(size_t)1 * (ninst + 1) + i + 1] - cum[(size_t)1 * (ninst + 1) + i];
-        }
-        args.swap(fa);
-      }
-      e->args = std::make_shared<DevBuf>();
-      const size_t b_args = args.size() * sizeof(lsk::PassArgs), b_cum = cum.size() * sizeof(int64_t);
-      const size_t b_ts = tsteps.size() * sizeof(int64_t), b_sargs = sargs.size() * sizeof(lsk::PassArgs);
-      const size_t b_scum = scum.size() * sizeof(int64_t);
-      const size_t b_si = sS.size() * sizeof(int32_t), b_sl = sBase.size() * sizeof(int64_t);
-      const size_t b_so = sOff.size() * sizeof(int64_t);
-      const size_t b_t12 = (size_t)ninst * sizeof(int64_t);
-      const size_t total_b = b_args + b_cum + b_ts + b_sargs + b_scum + 2 * b_si + 2 * b_sl + b_so + 2 * b_t12;
-      e->args->alloc(total_b);
-      char* base = static_cast<char*>(e->args->p);
-      size_t o = 0;
-      auto put = [&](const void* src, size_t bytes) -> void* {
-        void* d = base + o;
-        LS_CUDA(cudaMemcpy(d, src, bytes, cudaMemcpyHostToDevice));
-        o += bytes;
-        return d;
-      };
-      ba.args = static_cast<const lsk::PassArgs*>(put(args.data(), b_args));
-      ba.settle_args = static_cast<const lsk::PassArgs*>(put(sargs.data(), b_sargs));
-      ba.cum = static_cast<const int64_t*>(put(cum.data(), b_cum));
-      ba.tiles_step = static_cast<const int64_t*>(put(tsteps.data(), b_ts));
-      ba.settle_cum = static_cast<const int64_t*>(put(scum.data(), b_scum));
-      ba.tiles1 = static_cast<const int64_t*>(put(t1.data(), b_t12));
-      ba.tiles2 = static_cast<const int64_t*>(put(t2.data(), b_t12));
-      ba.fused = fused ? 1 : 0;
-      lsk::BatchSamplerArgs sa;
-      sa.base = static_cast<const int64_t*>(put(sBase.data(), b_sl));
-      sa.step_len = static_cast<const int64_t*>(put(sStep.data(), b_sl));
-      sa.pass_off = static_cast<const int64_t*>(put(sOff.data(), b_so));
-      sa.S = static_cast<const int32_t*>(put(sS.data(), b_si));
-      sa.p = static_cast<const int32_t*>(put(sP.data(), b_si));
-      sa.npf = npass;
-      sa.nsteps = (int32_t)n;
-      sa.Smax = smax;
-      ba.counters = static_cast<unsigned long long*>(b->counters.p);
-      ba.status = static_cast<int32_t*>(b->status.p);
-      int clk_khz = 0;
-      LS_CUDA(cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, b->device));
-      ba.timeout_cycles = (long long)(b->timeout_s * (double)std::max(clk_khz, 1000000) * 1e3);
-      ba.unmet = b->unmet;
-      ba.minb = kind == 1 ? b->minb1 : b->minb;
-      ba.kind = kind;
-      cudaGraph_t graph = nullptr;
-      LS_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-      cudaError_t ce = cudaMemsetAsync(b->counters.p, 0, (size_t)(ninst + 1) * sizeof(unsigned long long), b->cap);
-      if (ce == cudaSuccess && stoch) ce = cudaMemsetAsync(b->touch.p, 0, b->touch.bytes, b->cap);
-      if (ce == cudaSuccess && stoch)
-        ce = lsk::launch_batch_sampler(sa, static_cast<const uint64_t*>(b->seedbuf.p), (int64_t)ninst * n * npass,
-                                       static_cast<int32_t*>(e->lists->p), b->cap);
-      if (ce == cudaSuccess)
-        ce = b->dtype == LS_C64
-                 ? lsk::launch_batch<float>(ba, b->nthreads, kind == 1 ? b->blocks1 : b->blocks,
-                                            kind == 1 ? b->smem1 : b->smem, b->cap)
-                 : lsk::launch_batch<double>(ba, b->nthreads, kind == 1 ? b->blocks1 : b->blocks,
-                                             kind == 1 ? b->smem1 : b->smem, b->cap);
-      cudaError_t ee = cudaStreamEndCapture(b->cap, &graph);
-      if (ce != cudaSuccess || ee != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        throw CudaError{ce != cudaSuccess ? ce : ee, "batched graph capture"};
-      }
-      cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ie != cudaSuccess) throw CudaError{ie, "cudaGraphInstantiate"};
+      maybe_tune(b, psi, n, tau, scheme, st);
+      std::unique_ptr<ls_batch::Cached> e = build_batch_graph(b, psi, n, tau, scheme);
       b->graphs.push_front(std::move(e));
       while (b->graphs.size() > 4) b->graphs.pop_back();
       ge = b->graphs.front().get();

@@ -88,14 +88,14 @@ template <typename Real> __device__ __forceinline__ Phase<Real> phase_of(uint64_
 // device: rms angle error 0.19 and max 1.4 units of 2^-24, as sincospif.
 __device__ __forceinline__ void sincospi_quarter(float y, float& s, float& c) {
   const float y2 = y * y;
-  float ps = fmaf(0.0821458866f, y2, -0.599264529f);
-  ps = fmaf(ps, y2, 2.55016404f);
-  ps = fmaf(ps, y2, -5.16771278f);
-  s = fmaf(y, 3.14159274f, fmaf(y * y2, ps, y * -8.74227766e-08f));
-  float pc = fmaf(-0.0258068914f, y2, 0.235330630f);
-  pc = fmaf(pc, y2, -1.33526277f);
-  pc = fmaf(pc, y2, 4.05871213f);
-  pc = fmaf(pc, y2, -4.93480220f);
+  // the sine and cosine series side by side as one pair of Horner steps
+  // (per-lane paired FMAs, each rounded as fmaf); the cosine has one more term
+  const float2 Y2 = make_float2(y2, y2);
+  float2 P = __ffma2_rn(make_float2(0.0821458866f, -0.0258068914f), Y2, make_float2(-0.599264529f, 0.235330630f));
+  P = __ffma2_rn(P, Y2, make_float2(2.55016404f, -1.33526277f));
+  P = __ffma2_rn(P, Y2, make_float2(-5.16771278f, 4.05871213f));
+  s = fmaf(y, 3.14159274f, fmaf(y * y2, P.x, y * -8.74227766e-08f));
+  const float pc = fmaf(P.y, y2, -4.93480220f);
   c = fmaf(y2, pc, 1.0f);
 }
 
@@ -114,10 +114,12 @@ template <> __device__ __forceinline__ Phase<float> phase_of<float>(uint64_t t) 
   sincospi_quarter(xf * 0x1p-31f, s, c);
   const float d = fmaf((float)lo, 0x1p-32f, (float)res) * 0x1.921fb6p-30f;  // 2 pi / 2^32 per unit
   const float c1 = fmaf(-d, s, c), s1 = fmaf(d, c, s);
-  // explicit round-to-nearest operations: no contraction may merge c2h - 1
-  const float c2h = __fmul_rn(c1, c1), c2l = fmaf(c1, c1, -c2h);
-  const float s2h = __fmul_rn(s1, s1), s2l = fmaf(s1, s1, -s2h);
-  const float e = __fadd_rn(__fadd_rn(__fadd_rn(c2h, -1.0f), s2h), __fadd_rn(c2l, s2l));
+  // explicit round-to-nearest operations: no contraction may merge c2h - 1;
+  // lane 0 carries c1, lane 1 s1: NH = -(v^2 rounded), L = v^2 - fl(v^2) exactly
+  const float2 V = make_float2(c1, s1);
+  const float2 NH = __fmul2_rn(V, make_float2(-c1, -s1));
+  const float2 L = __ffma2_rn(V, V, NH);
+  const float e = __fadd_rn(__fadd_rn(__fadd_rn(-NH.x, -1.0f), -NH.y), __fadd_rn(L.x, L.y));
   // rotate by q quarter turns without branches: odd q swaps (c, s) -> (-s, c),
   // q & 2 negates both
   const bool odd = (q & 1) != 0;
@@ -167,10 +169,29 @@ template <typename Real>
 __device__ __forceinline__ typename CT<Real>::C apply_phase(typename CT<Real>::C x, const Phase<Real>& p);
 template <>
 __device__ __forceinline__ float2 apply_phase<float>(float2 x, const Phase<float>& p) {
-  float2 y;
-  y.x = dot2_fix(x.x, p.v.x, -x.y, p.v.y, p.half_e);
-  y.y = dot2_fix(x.x, p.v.y, x.y, p.v.x, p.half_e);
-  return y;
+  // dot2_fix for both components at once in paired FP32 operations: lane 0
+  // forms x.x c - x.y s, lane 1 x.x s + x.y c, each times (1 - e/2) with one
+  // final rounding.  Subtractions are fused multiply-adds by -1 and negated
+  // intermediates are carried instead of subtracted, so every lane performs
+  // the exact operations of the error-free transforms.
+  const float2 A = make_float2(x.x, x.x), NA = make_float2(-x.x, -x.x);
+  const float2 B = make_float2(-x.y, x.y), NB = make_float2(x.y, -x.y);
+  const float2 Cv = p.v, Sv = make_float2(p.v.y, p.v.x);
+  const float2 M1 = make_float2(-1.0f, -1.0f);
+  const float2 P = __fmul2_rn(A, Cv);
+  const float2 NPE = __ffma2_rn(NA, Cv, P);     // -(a c - p), exact
+  const float2 Q = __fmul2_rn(B, Sv);
+  const float2 NQE = __ffma2_rn(NB, Sv, Q);     // -(b s - q), exact
+  const float2 R = __fadd2_rn(P, Q);
+  const float2 BB = __ffma2_rn(P, M1, R);       // r - p
+  const float2 T1 = __ffma2_rn(BB, M1, R);      // r - bb
+  const float2 T2 = __ffma2_rn(T1, M1, P);      // p - (r - bb)
+  const float2 T3 = __ffma2_rn(BB, M1, Q);      // q - bb
+  const float2 RE = __fadd2_rn(T2, T3);         // two-sum error of r
+  const float2 S1 = __fadd2_rn(NPE, NQE);       // -(pe + qe)
+  const float2 U = __ffma2_rn(S1, M1, RE);      // re + pe + qe
+  const float2 LO = __ffma2_rn(make_float2(-p.half_e, -p.half_e), R, U);   // ... - h r
+  return __fadd2_rn(R, LO);
 }
 template <>
 __device__ __forceinline__ double2 apply_phase<double>(double2 x, const Phase<double>& p) {
@@ -1737,6 +1758,10 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
     s_c0[tid] = c0;
     s_touch[tid] = touch;
   }
+  // complex64 with at most 7 taps: the multiply-adds run as paired FP32
+  // operations, sum_k v_k (t_k.x, t_k.x) and sum_k v_k (t_k.y, t_k.y) in two
+  // accumulators combined at the end
+  constexpr bool PACK = sizeof(Real) == 4 && BV <= 3;
   C t[NTAP];
   {
     const C* tp = reinterpret_cast<const C*>(a.taps);
@@ -1783,19 +1808,38 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
     }
   }
   __syncthreads();
-  // Element ownership in the phase and stencil sweeps: contiguous tiles: one
-  // warp per slice, lane i, i + 32, ...; strided tiles: the column w = tid mod W
-  // fixed per thread, rows i = tid / W + k NT / W.  Every thread walks its
+  // Element ownership in the phase and stencil sweeps.  Contiguous tiles:
+  // work units of CH consecutive elements of one slice (unit u: slice u / nch,
+  // chunk u mod nch), taken by the warps in turn, lane l owning elements
+  // l, l + 32, ... of its unit; strided tiles: one unit per thread, the column
+  // w = tid mod W and rows i = tid / W + k NT / W.  Every thread walks its
   // kinetic phase turns by second differences along its elements.
+  constexpr int CH = 256;
   const int wsh = 31 - __clz(W);
-  const int sw0 = strided ? (tid & (W - 1)) : warp;             // first slice of this thread
-  const int swd = strided ? W : nwarp;                          // slice step (strided: one slice only)
-  const int ei0 = strided ? (tid >> wsh) : lane;                // first element
+  const int nch = (q + CH - 1) / CH;
+  const int u0 = strided ? 0 : warp;                            // first unit of this thread
+  const int ud = strided ? 1 : nwarp;                           // unit step
+  const int nunit = strided ? 1 : W * nch;
   const int eid = strided ? (NT >> wsh) : 32;                   // element step
   const int sstep = strided ? W : 1;                            // shared-memory step between neighbours
+  // unit u -> slice w, elements [i0, i1) owned with step eid from ei
+  auto unit = [&](int u, int& w, int& ei, int& i1) {
+    if (strided) {
+      w = tid & (W - 1);
+      ei = tid >> wsh;
+      i1 = q;
+    } else {
+      w = u / nch;
+      const int c = u - w * nch;
+      ei = c * CH + lane;
+      i1 = min(q, (c + 1) * CH);
+    }
+  };
   // ---- kinetic pre-phase (first pass of a call) or the pending lazy phase
   if (lazy || a.units_pre != 0) {
-    for (int w = sw0; w < W; w += swd) {
+    for (int u = u0; u < nunit; u += ud) {
+      int w, ei0, i1;
+      unit(u, w, ei0, i1);
       const int64_t sl = s_slice[w];
       if (sl >= 0) {
         KinWalk kw;
@@ -1803,7 +1847,7 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
         if (!lazy) kw.scale((uint64_t)0 - (uint64_t)a.units_pre);
         const int32_t tw = s_touch[w];
         C* p = sm + (strided ? (ei0 + H) * W + w : w * Ls + H + ei0);
-        for (int i = ei0; i < q; i += eid) {
+        for (int i = ei0; i < i1; i += eid) {
           if (lazy) {
             const int32_t t2 = CG ? __ldcg(a.touch_other + i) : a.touch_other[i];
             const int64_t units = (int64_t)a.now - (int64_t)(tw > t2 ? tw : t2);
@@ -1815,7 +1859,6 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
           kw.next();
         }
       }
-      if (strided) break;
     }
     __syncthreads();
   }
@@ -1831,7 +1874,9 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   // ---- y = x + sum_d c'_d x_{i-d}, post-phase, store
   {
     const bool post = !lazy && a.units_post != 0;
-    for (int w = sw0; w < W; w += swd) {
+    for (int u = u0; u < nunit; u += ud) {
+      int w, ei0, i1;
+      unit(u, w, ei0, i1);
       const int64_t sl = s_slice[w];
       if (sl >= 0) {
         KinWalk kw;
@@ -1840,14 +1885,26 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
         const C* sp = sm + (strided ? (ei0 + H) * W + w : w * Ls + H + ei0);
         C* gp = psi + sl * g.slice_stride + (int64_t)ei0 * g.ea;
         const int64_t gstep = (int64_t)eid * g.ea;
-        for (int i = ei0; i < q; i += eid) {
+        for (int i = ei0; i < i1; i += eid) {
           C acc = czero<C>();
+          if constexpr (PACK) {
+            float2 ax = make_float2(0.f, 0.f), ay = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int k = 0; k < NTAP; ++k) {
-            // tap k is d = k - BV: x_{i - d} sits (BV - k) steps from x_i
-            const C v = sp[(BV - k) * sstep];
-            acc.x = fma(t[k].x, v.x, fma(-t[k].y, v.y, acc.x));
-            acc.y = fma(t[k].x, v.y, fma(t[k].y, v.x, acc.y));
+            for (int k = 0; k < NTAP; ++k) {
+              const float2 v = *reinterpret_cast<const float2*>(sp + (BV - k) * sstep);
+              ax = __ffma2_rn(v, make_float2(t[k].x, t[k].x), ax);
+              ay = __ffma2_rn(v, make_float2(t[k].y, t[k].y), ay);
+            }
+            acc.x = ax.x - ay.y;
+            acc.y = ax.y + ay.x;
+          } else {
+#pragma unroll
+            for (int k = 0; k < NTAP; ++k) {
+              // tap k is d = k - BV: x_{i - d} sits (BV - k) steps from x_i
+              const C v = sp[(BV - k) * sstep];
+              acc.x = fma(t[k].x, v.x, fma(-t[k].y, v.y, acc.x));
+              acc.y = fma(t[k].x, v.y, fma(t[k].y, v.x, acc.y));
+            }
           }
           C y = cadd(sp[0], acc);
           if (post) y = apply_phase<Real>(y, phase_of<Real>(kw.q));
@@ -1857,7 +1914,6 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
           kw.next();
         }
       }
-      if (strided) break;
     }
   }
   if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
@@ -1984,8 +2040,8 @@ __device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsi
   }
 }
 
-template <typename Real, int BPT, bool STOCH, int MINB, int KIND>
-__global__ void __launch_bounds__(256, MINB)
+template <typename Real, int BPT, bool STOCH, int MINB, int KIND, int NTH = 256>
+__global__ void __launch_bounds__(NTH, MINB)
 batch_kernel(const BatchArgs b) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ PassArgs s_args;
@@ -2019,13 +2075,21 @@ batch_kernel(const BatchArgs b) {
     for (int q = 0; q < 3; ++q) s_now_off[q] = b.now_off[q];
   }
   __syncthreads();
+  // Thread 0 claims the next item one item ahead: the claim's round trip
+  // overlaps the current tile.  Items still start in claim order per CTA, and
+  // a CTA starts an item claimed early only after finishing the current one,
+  // so the earliest unfinished item always runs with its inputs complete.
+  long long claimed = -1;
+  if (threadIdx.x == 0 && *status == 0) claimed = (long long)atomicAdd(&b.counters[0], 1ull);
   for (;;) {
     if (threadIdx.x == 0) {
-      long long it = -1;
+      long long it = claimed;
       s_stop = 0;
       s_settle = 0;
-      if (*status == 0) it = (long long)atomicAdd(&b.counters[0], 1ull);
+      if (*status != 0) it = -1;
       s_item = (it >= 0 && it < total) ? it : -1;
+      claimed = -1;
+      if (s_item >= 0 && *status == 0) claimed = (long long)atomicAdd(&b.counters[0], 1ull);
       if (s_item >= 0) {
         unsigned long long need;
         int i;
@@ -2162,44 +2226,52 @@ batch_kernel(const BatchArgs b) {
   }
 }
 
-// Variants: (KIND 0, 3 CTAs per SM), (KIND 1, 3 or 4 CTAs per SM).
-template <typename Real, int KIND, int MINB>
-static cudaError_t launch_batch_v(const BatchArgs& b, int nthreads, int nblocks, size_t smem, cudaStream_t st) {
-  if (b.stoch) batch_kernel<Real, 2, true, MINB, KIND><<<nblocks, nthreads, smem, st>>>(b);
-  else batch_kernel<Real, 2, false, MINB, KIND><<<nblocks, nthreads, smem, st>>>(b);
+// Variants (threads per CTA, CTAs per SM the registers are budgeted for):
+// KIND 0: (256, 3); KIND 1 (compact-kernel tiles only): (256, 3), (256, 4),
+// (128, 6), (128, 8) for complex64 and (256, 3) for complex128.
+template <typename Real, int KIND, int MINB, int NTH>
+static cudaError_t launch_batch_v(const BatchArgs& b, int nblocks, size_t smem, cudaStream_t st) {
+  if (b.stoch) batch_kernel<Real, 2, true, MINB, KIND, NTH><<<nblocks, NTH, smem, st>>>(b);
+  else batch_kernel<Real, 2, false, MINB, KIND, NTH><<<nblocks, NTH, smem, st>>>(b);
   return cudaGetLastError();
 }
 
-template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
-                                                  cudaStream_t st) {
-  if (b.kind == 1) {
-    if (b.minb == 4) return launch_batch_v<Real, 1, 4>(b, nthreads, nblocks, smem, st);
-    return launch_batch_v<Real, 1, 3>(b, nthreads, nblocks, smem, st);
-  }
-  return launch_batch_v<Real, 0, 3>(b, nthreads, nblocks, smem, st);
-}
-
-template <typename Real, int KIND, int MINB>
-static cudaError_t batch_prepare_v(size_t max_smem, int nthreads, size_t smem, int* blocks_per_sm) {
+template <typename Real, int KIND, int MINB, int NTH>
+static cudaError_t batch_prepare_v(size_t max_smem, size_t smem, int* blocks_per_sm) {
   int a = 0, c = 0;
-  cudaError_t e = allow_smem(batch_kernel<Real, 2, false, MINB, KIND>, max_smem);
-  if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, MINB, KIND>, max_smem);
+  cudaError_t e = allow_smem(batch_kernel<Real, 2, false, MINB, KIND, NTH>, max_smem);
+  if (e == cudaSuccess) e = allow_smem(batch_kernel<Real, 2, true, MINB, KIND, NTH>, max_smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, MINB, KIND>, nthreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel<Real, 2, false, MINB, KIND, NTH>, NTH, smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, MINB, KIND>, nthreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, batch_kernel<Real, 2, true, MINB, KIND, NTH>, NTH, smem);
   *blocks_per_sm = a < c ? a : c;
   return e;
 }
 
+// Dispatch over the variants; a (kind, minb, nthreads) without a variant
+// returns cudaErrorInvalidValue.
+#define LS_BATCH_VARIANTS(F, ...)                                                                  \
+  if (kind == 0 && minb == 3 && nthreads == 256) return F<Real, 0, 3, 256>(__VA_ARGS__);          \
+  if (kind == 1 && minb == 3 && nthreads == 256) return F<Real, 1, 3, 256>(__VA_ARGS__);          \
+  if constexpr (sizeof(Real) == 4) {                                                               \
+    if (kind == 1 && minb == 4 && nthreads == 256) return F<Real, 1, 4, 256>(__VA_ARGS__);        \
+    if (kind == 1 && minb == 6 && nthreads == 128) return F<Real, 1, 6, 128>(__VA_ARGS__);        \
+    if (kind == 1 && minb == 8 && nthreads == 128) return F<Real, 1, 8, 128>(__VA_ARGS__);        \
+  }                                                                                                \
+  return cudaErrorInvalidValue;
+
+template <typename Real> cudaError_t launch_batch(const BatchArgs& b, int nthreads, int nblocks, size_t smem,
+                                                  cudaStream_t st) {
+  const int kind = b.kind, minb = b.minb;
+  LS_BATCH_VARIANTS(launch_batch_v, b, nblocks, smem, st)
+}
+
 template <typename Real> cudaError_t batch_prepare(size_t max_smem, int nthreads, size_t smem, int kind, int minb,
                                                    int* blocks_per_sm) {
-  if (kind == 1) {
-    if (minb == 4) return batch_prepare_v<Real, 1, 4>(max_smem, nthreads, smem, blocks_per_sm);
-    return batch_prepare_v<Real, 1, 3>(max_smem, nthreads, smem, blocks_per_sm);
-  }
-  return batch_prepare_v<Real, 0, 3>(max_smem, nthreads, smem, blocks_per_sm);
+  LS_BATCH_VARIANTS(batch_prepare_v, max_smem, smem, blocks_per_sm)
 }
+#undef LS_BATCH_VARIANTS
 
 #define LS_FOR_MODES(X, R, B) \
   X(R, B, MODE_STEP) X(R, B, MODE_LAZY) X(R, B, MODE_MEASURE) X(R, B, MODE_ADJOINT) X(R, B, MODE_KIN)

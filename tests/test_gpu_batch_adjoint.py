@@ -101,6 +101,66 @@ def test_batched_fast_tiles_parity(P, scheme, form, monkeypatch):
         O.use_fft(False)
 
 
+@pytest.mark.parametrize("cfg", ["256,3", "256,4", "128,6", "128,8"])
+def test_batched_compact_configurations_parity(P, cfg, monkeypatch):
+    """Every launch configuration of the compact-kernel batched kernel (threads
+    per CTA, CTAs per SM and the tile widths they imply) against the oracle,
+    deterministic and stochastic."""
+    monkeypatch.setenv("LSPLIT_STENCIL_CFG", cfg)
+    probs = uneven_batch()
+    b = P.Batch(probs, "c64")
+    assert (b.config()["threads"], b.config()["ctas_per_sm"]) == tuple(int(v) for v in cfg.split(","))
+    xs = [W.random_state((p.M2, p.M1), 90 + i) for i, p in enumerate(probs)]
+    for scheme in ("strang", "strang_stoch"):
+        psi = b.empty()
+        for i, x in enumerate(xs):
+            b.set_dense(psi, i, x)
+        b.step(psi, 3, 1e-2, scheme, seed=4, step0=1)
+        for i, p in enumerate(probs):
+            ref = O.step(p, xs[i], 1e-2, scheme, 3, seed=4 + i, step0=1)
+            assert rel(b.get_dense(psi, i), ref) < 3e-5, (cfg, scheme, i, rel(b.get_dense(psi, i), ref))
+
+
+def test_batched_autotuner_never_slower_than_default(P, monkeypatch):
+    """The autotuner times the compact-kernel configurations and the transform
+    forms on the first call and keeps the fastest: on the batched workload's
+    length classes (half-widths 16..512) the tuned launch is not slower than
+    the untuned default configuration (256 threads, 3 CTAs per SM), and both
+    give the same states."""
+    import torch
+    monkeypatch.delenv("LSPLIT_TUNE", raising=False)
+    monkeypatch.delenv("LSPLIT_STENCIL_CFG", raising=False)
+    probs = W.batch_1d(count=48, seed=4)
+    bt = P.Batch(probs, "c64")
+    pt = bt.empty()
+    bt.init_gaussian(pt, [0.0], 2.0, [1.0])
+    bt.step(pt, 4, 1e-3, "strang")
+    cfg = bt.config()
+    assert cfg["tuned"] and len(cfg["tune_ms"]) == 5, cfg
+    assert min(cfg["tune_ms"]) > 0
+    monkeypatch.setenv("LSPLIT_STENCIL_CFG", "256,3")
+    bd = P.Batch(probs, "c64")
+    pd = bd.empty()
+    bd.init_gaussian(pd, [0.0], 2.0, [1.0])
+    bd.step(pd, 4, 1e-3, "strang")
+    assert not bd.config()["tuned"]
+    assert rel(bt.get_dense(pt, 5), bd.get_dense(pd, 5)) < 3e-6
+
+    def timed(b, psi):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        b.step(psi, 4, 1e-3, "strang")
+        ev[0].record()
+        for _ in range(5):
+            b.step(psi, 4, 1e-3, "strang")
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1])
+    t_tuned = min(timed(bt, pt) for _ in range(2))
+    t_default = min(timed(bd, pd) for _ in range(2))
+    print("tuned", cfg, t_tuned, "default", t_default)
+    assert t_tuned <= 1.05 * t_default, (cfg, t_tuned, t_default)
+
+
 def test_batched_fused_walk_matches_unfused(P, monkeypatch):
     """Deterministic Strang in the persistent launch fuses adjacent layer-1
     factors of consecutive steps (fused tiles for the convolution-form
