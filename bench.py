@@ -544,6 +544,13 @@ def run_ours(args):
         subs["twisted2d-64^4"] = sub_single(
             P, O, "twisted2d-64^4 strang tau=1e-3 (134 MB)", W.twisted_2d(q=64), "c64", "strang", 1e-3, 5, 10,
             hbm, src, None, st, [0.0, 0.0], [1.0, 0.0])
+        os.environ["LSPLIT_TC2D"] = "1"
+        try:
+            subs["twisted2d-64^4-tensor-core"] = sub_single(
+                P, O, "twisted2d-64^4 strang tau=1e-3, layer-1 64x64 DFTs as split-BF16 tensor-core products",
+                W.twisted_2d(q=64), "c64", "strang", 1e-3, 5, 10, hbm, src, None, st, [0.0, 0.0], [1.0, 0.0])
+        finally:
+            os.environ.pop("LSPLIT_TC2D", None)
         del flush_buf
         bs = P.Batch(probs, "c64")
         ps = bs.empty()

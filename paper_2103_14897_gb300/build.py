@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     objs, jobs = [], []
-    for cu in ("lsplit_f32.cu", "lsplit_f64.cu", "lsplit_batch.cu", "lsplit_misc.cu", "lsplit_noalloc.cu", "lsplit_cn.cu", "lsplit_density.cu"):
+    for cu in ("lsplit_f32.cu", "lsplit_f64.cu", "lsplit_batch.cu", "lsplit_misc.cu", "lsplit_noalloc.cu", "lsplit_cn.cu", "lsplit_density.cu", "lsplit_tc2d.cu"):
         o = os.path.join(BUILD, cu.replace(".cu", ".o"))
         objs.append(o)
         jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

@@ -184,6 +184,9 @@ struct ls_ctx {
   int W[2] = {1, 1}, bpt[2] = {2, 2}, nt[2] = {64, 64};
   int fastW[2] = {0, 0};  // slices per CTA of the fast 1D pass (0: not applicable)
   bool fast2d[2] = {false, false};  // 64 x 64 slices on the fast 2D pass
+  bool tc2d = false;                // layer-1 64 x 64 slices on the tensor-core pass
+  DevBuf tcplanes;                  // its split-BF16 DFT matrix planes
+  int sms = 0;
   int fast_variant = 0;   // shared-buffer / register-budget variant of the fast pass
   DevBuf tw[2], twb[2], bm[2], bp[2], chirp[2], vgrid[2];
   std::vector<double> vhost[2];
@@ -467,6 +470,38 @@ void set_kinetic(ls_ctx* c, double u) {
   }
 }
 
+// bf16 with round-to-nearest-even of a float (finite values).
+uint16_t bf16_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float bf16_val(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// W[p][k] = exp(+2 pi i (p k mod 64) / 64) as high and low bf16 parts
+// (hi = bf16(x), lo = bf16(x - hi)): planes Re hi, Re lo, Im hi, Im lo.
+std::vector<uint16_t> dft64_split_planes() {
+  std::vector<uint16_t> pl((size_t)4 * 4096);
+  for (int p = 0; p < 64; ++p)
+    for (int k = 0; k < 64; ++k) {
+      const double ang = 2.0 * kPi * (double)((p * k) % 64) / 64.0;
+      const double v[2] = {std::cos(ang), std::sin(ang)};
+      for (int ri = 0; ri < 2; ++ri) {
+        const uint16_t hi = bf16_rn((float)v[ri]);
+        const uint16_t lo = bf16_rn((float)(v[ri] - (double)bf16_val(hi)));
+        pl[(size_t)(2 * ri) * 4096 + p * 64 + k] = hi;
+        pl[(size_t)(2 * ri + 1) * 4096 + p * 64 + k] = lo;
+      }
+    }
+  return pl;
+}
+
 // ---------------------------------------------------------------- validation
 int validate(const ls_problem* p) {
   if (!p) return fail(LS_ERR_INVALID, "problem is NULL");
@@ -649,6 +684,8 @@ lsk::PassArgs base_args(ls_ctx* c, int L, void* psi) {
 }
 
 cudaError_t launch(ls_ctx* c, const lsk::PassArgs& a0, int L, int64_t nitems, cudaStream_t st) {
+  if (L == 0 && c->tc2d && a0.mode == lsk::MODE_STEP && a0.list == nullptr)
+    return lsk::launch_tc2d(a0, c->tcplanes.p, (int)std::min<int64_t>(nitems, 2 * (int64_t)c->sms), st);
   if (a0.sB > 0 && (a0.mode == lsk::MODE_STEP || a0.mode == lsk::MODE_LAZY)) {
     lsk::PassArgs a = a0;
     a.W = c->stW[L];
@@ -1202,6 +1239,16 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     if (c->dtype == LS_C64) LS_CUDA(lsk::stencil_prepare<float>(block_max));
     else LS_CUDA(lsk::stencil_prepare<double>(block_max));
     for (int L = 0; L < 2; ++L) c->stW[L] = stencil_width(c->geom[L], c->esize, L == 1);
+    LS_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
+    // tensor-core form of the contiguous 64 x 64 layer (complex64)
+    if (c->dtype == LS_C64 && c->d == 2 && c->geom[0].qa == 64 && c->geom[0].qb == 64 &&
+        lsk::tc2d_smem_bytes() + 8192 <= (size_t)dev_max + static_reserve && getenv_flag("LSPLIT_TC2D")) {
+      LS_CUDA(lsk::tc2d_prepare(block_max));
+      const std::vector<uint16_t> pl = dft64_split_planes();
+      c->tcplanes.alloc(pl.size() * sizeof(uint16_t));
+      LS_CUDA(cudaMemcpy(c->tcplanes.p, pl.data(), pl.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+      c->tc2d = true;
+    }
     for (int L = 0; L < 2; ++L) {
       const lsk::LayerGeom& g = c->geom[L];
       const size_t sm = c->dtype == LS_C64 ? lsk::fast2d_smem_bytes<float>(g) : lsk::fast2d_smem_bytes<double>(g);

@@ -146,6 +146,14 @@ template <typename Real> cudaError_t fast2d_prepare(size_t max_smem);
 template <typename Real> cudaError_t launch_stencil(const PassArgs& a, int64_t ntiles, cudaStream_t st);
 template <typename Real> size_t stencil_smem_bytes(const LayerGeom& g, int W, int B);
 template <typename Real> cudaError_t stencil_prepare(size_t max_smem);
+// Tensor-core layer pass for contiguous 64 x 64 slices (complex64, MODE_STEP,
+// optionally the fused second factor in T2): the DFTs as split-BF16 matrix
+// products.  planes: 4 x 64 x 64 bf16 (row-major) with W[p][k] =
+// exp(+2 pi i p k / 64): Re hi, Re lo, Im hi, Im lo.  Persistent over the
+// slices with nblocks CTAs of 256 threads.
+cudaError_t launch_tc2d(const PassArgs& a, const void* planes, int nblocks, cudaStream_t st);
+cudaError_t tc2d_prepare(size_t max_smem);
+size_t tc2d_smem_bytes();
 cudaError_t launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
 cudaError_t launch_zero_f64(double* p, int64_t n, cudaStream_t st);
 

@@ -591,6 +591,55 @@ def test_twisted_64_slices_one_step(P):
     assert rel(ctx.to_dense(psi), ref) < 1e-5
 
 
+@pytest.mark.parametrize("scheme", ["strang", "lie", "strang_kp", "yoshida4"])
+def test_tensor_core_64x64_pass_parity(P, scheme, monkeypatch):
+    """The layer pass of contiguous 64 x 64 slices with the DFTs as split-BF16
+    matrix products on the tensor cores (fused Strang factors included):
+    against the oracle on small other layers, within the complex64 tolerance."""
+    monkeypatch.setenv("LSPLIT_TC2D", "1")
+    import dataclasses
+    base = W.twisted_2d(q=64, hmax=3)
+    for p in [dataclasses.replace(base, lo2=(-4, -4), q2=(8, 8), ecut=1e9, name="tc-64x64-8x8"),
+              dataclasses.replace(base, lo2=(-3, -2), q2=(8, 4), name="tc-64x64-cutoff")]:
+        ctx = P.Context(p, "c64")
+        x = W.random_state((p.M2, p.M1), 31)
+        psi = ctx.from_dense(x)
+        ctx.step(psi, 4, 1e-3, scheme)
+        O.use_fft(True)
+        try:
+            ref = O.step(p, x, 1e-3, scheme, 4)
+        finally:
+            O.use_fft(False)
+        assert rel(ctx.to_dense(psi), ref) < TOL1["c64"] * 3, (p.name, scheme, rel(ctx.to_dense(psi), ref))
+
+
+def test_tensor_core_64x64_full_size_and_100_steps(P, monkeypatch):
+    """64^4 twisted bilayer with the tensor-core layer pass: one Strang step
+    from the packet against the oracle, and 100 steps of a random state on a
+    64 x 64 x 8 x 8 box (rel-L2 and norm gates of the FP32 path)."""
+    monkeypatch.setenv("LSPLIT_TC2D", "1")
+    import dataclasses
+    p = W.twisted_2d(q=64)
+    ctx = P.Context(p, "c64")
+    psi = ctx.empty()
+    ctx.init_gaussian(psi, [0.0, 0.0], 2.0, [1.0, 0.0])
+    x = ctx.to_dense(psi)
+    ctx.step(psi, 1, 1e-3, "strang")
+    O.use_fft(True)
+    try:
+        assert rel(ctx.to_dense(psi), O.step(p, x, 1e-3, "strang", 1)) < 1e-5
+        q = dataclasses.replace(p, lo2=(-4, -4), q2=(8, 8), ecut=1e9, name="tc-100")
+        c2 = P.Context(q, "c64")
+        y = W.random_state((q.M2, q.M1), 32)
+        py = c2.from_dense(y)
+        c2.step(py, 100, 1e-3, "strang")
+        got = c2.to_dense(py)
+        assert rel(got, O.step(q, y, 1e-3, "strang", 100)) < 1e-4
+        assert abs(np.linalg.norm(got) - 1) < 1e-5
+    finally:
+        O.use_fft(False)
+
+
 def test_adjoint_parity(P):
     th1 = np.array([0.6, -0.3, 0.2])
     th2 = np.array([0.4, 0.25])
