@@ -26,6 +26,13 @@ Readings of passages the paper leaves open:
 * The stochastic variant (Algorithm 4 applied to the exponential sub-steps):
   each potential sub-step acts on a seeded random subset of p of the S slices,
   with duration scaled by S/p; the kinetic factors act on every element.
+* Shared periodic index (Example 3 of Sec. 5: periodic in y, incommensurate in
+  x): a problem with ``shared = 1`` lifts to three indices (m, n, p), p the
+  y index common to both layers, stored as a 2D problem whose layer-1 box is
+  (q1, 1) and whose layer-2 box is (q2, q3) with the second component p, so
+  that k = B1 m + B2 (n, p) = (G1 m + G2 n, G3 p).  A layer-1 factor acts on
+  the 2D slices (m, p) at fixed n, a layer-2 factor on (n, p) at fixed m; each
+  layer potential is a function of (x, y) with harmonics (h_x, h_y).
 """
 from __future__ import annotations
 
@@ -40,7 +47,8 @@ __all__ = [
     "toeplitz_potential", "apply_C", "apply_semi_implicit", "density_on_line",
     "splitmix64_next", "sample_slices", "observables", "gaussian_packet",
     "settle_noop", "adjoint", "overlap_loss", "SCHEMES", "coefficient_gradient", "use_fft",
-    "TRANSFORM", "sample_count", "expanded_factors",
+    "TRANSFORM", "sample_count", "expanded_factors", "layer_grid", "layer_slices", "from_layer_slices",
+    "n_slices",
 ]
 
 SCHEMES = ("lie", "strang", "strang_kp", "lie_stoch", "strang_stoch", "yoshida4", "cn_strang",
@@ -170,6 +178,57 @@ def _axis_dft(x: np.ndarray, q: Sequence[int], inverse: bool) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Slices of a layer (Sec. 3 Kronecker structure; Example 3's shared index)
+# --------------------------------------------------------------------------
+def _shared(prob) -> bool:
+    return bool(getattr(prob, "shared", 0))
+
+
+def layer_grid(prob, layer: int):
+    """(harmonics, coefficients, grid extents) of layer j's potential.  With a
+    shared index the grid is (q_j, q3): x on the layer's own cell, y on the
+    common period."""
+    h, c = (prob.v1_h, prob.v1_c) if layer == 1 else (prob.v2_h, prob.v2_c)
+    if _shared(prob):
+        q = (prob.q1[0], prob.q2[1]) if layer == 1 else (prob.q2[0], prob.q2[1])
+    else:
+        q = prob.q1 if layer == 1 else prob.q2
+    return h, c, tuple(q)
+
+
+def layer_slices(prob, phi: np.ndarray, layer: int) -> np.ndarray:
+    """The slices of layer j as the rows of a (slices, slice length) array:
+    without a shared index, rows of phi (layer 1) or columns (layer 2); with
+    one, the (m, p) planes at fixed n (layer 1, m fastest) or the (n, p) planes
+    at fixed m (layer 2, n fastest)."""
+    if not _shared(prob):
+        return phi if layer == 1 else phi.T
+    q1, q2, q3 = prob.q1[0], prob.q2[0], prob.q2[1]
+    Y = phi.reshape(q3, q2, q1)                       # [p, n, m]
+    if layer == 1:
+        return Y.transpose(1, 0, 2).reshape(q2, q3 * q1)
+    return Y.transpose(2, 0, 1).reshape(q1, q3 * q2)
+
+
+def from_layer_slices(prob, X: np.ndarray, layer: int) -> np.ndarray:
+    """Inverse of layer_slices."""
+    if not _shared(prob):
+        return X if layer == 1 else X.T.copy()
+    q1, q2, q3 = prob.q1[0], prob.q2[0], prob.q2[1]
+    if layer == 1:
+        Y = X.reshape(q2, q3, q1).transpose(1, 0, 2)
+    else:
+        Y = X.reshape(q1, q3, q2).transpose(1, 2, 0)
+    return np.ascontiguousarray(Y).reshape(q3 * q2, q1)
+
+
+def n_slices(prob, layer: int) -> int:
+    if _shared(prob):
+        return prob.q2[0] if layer == 1 else prob.q1[0]
+    return prob.M2 if layer == 1 else prob.M1
+
+
+# --------------------------------------------------------------------------
 # The factors of the splitting (Eq. (4.8) sub-problems; Algorithm 3 steps)
 # --------------------------------------------------------------------------
 def apply_K(prob, phi: np.ndarray, s: float, _kin=None) -> np.ndarray:
@@ -185,12 +244,8 @@ def apply_P(prob, phi: np.ndarray, layer: int, s: float,
 
     ``slices`` (optional): indices of the slices the factor acts on; the others
     are left unchanged (the stochastic variant)."""
-    if layer == 1:
-        q, h, c = prob.q1, prob.v1_h, prob.v1_c
-        X = phi
-    else:
-        q, h, c = prob.q2, prob.v2_h, prob.v2_c
-        X = phi.T
+    h, c, q = layer_grid(prob, layer)
+    X = layer_slices(prob, phi, layer)
     v = grid_potential(h, c, q) if _v is None else _v
     T = np.exp(-1j * (s * v))
     if slices is None:
@@ -205,7 +260,7 @@ def apply_P(prob, phi: np.ndarray, layer: int, s: float,
     else:
         Y = X.copy()
         Y[np.asarray(slices, dtype=np.int64)] = out_rows
-    return Y if layer == 1 else Y.T.copy()
+    return from_layer_slices(prob, Y, layer)
 
 
 def yoshida_weights() -> Tuple[float, float]:
@@ -403,7 +458,7 @@ def expanded_factors(prob, scheme: str, tau: float, nsteps: int, seed: int = 0,
                 continue
             layer, s = f[1], f[2]
             if stoch:
-                S = prob.M2 if layer == 1 else prob.M1
+                S = n_slices(prob, layer)
                 p = sample_count(S, frac_den)
                 g = (step0 + k) * npf + pi
                 sl = sample_slices(S, p, seed, g)
@@ -422,9 +477,9 @@ def step(prob, phi: np.ndarray, tau: float, scheme: str = "strang", nsteps: int 
         raise ValueError(scheme)
     phi = np.array(phi, dtype=np.complex128, copy=True)
     kin = kinetic_energy_diag(prob)
-    v1 = grid_potential(prob.v1_h, prob.v1_c, prob.q1)
-    v2 = grid_potential(prob.v2_h, prob.v2_c, prob.q2)
     mask = index_mask(prob) if project else None
+    v1 = grid_potential(*layer_grid(prob, 1))
+    v2 = grid_potential(*layer_grid(prob, 2))
     per = len(scheme_factors(scheme, tau))
     fl = expanded_factors(prob, scheme, tau, nsteps, seed, step0, frac_den)
     for i, f in enumerate(fl):
@@ -475,12 +530,13 @@ def observables(prob, phi: np.ndarray, chi: Optional[np.ndarray] = None) -> Dict
     a2 = np.abs(phi) ** 2
     out = {"norm": float(a2.sum()),
            "ekin": float((kinetic_energy_diag(prob) * a2).sum())}
-    v1 = grid_potential(prob.v1_h, prob.v1_c, prob.q1)
-    v2 = grid_potential(prob.v2_h, prob.v2_c, prob.q2)
-    psi1 = _axis_dft(phi, prob.q1, inverse=True)
-    psi2 = _axis_dft(phi.T, prob.q2, inverse=True)
-    out["epot1"] = float((np.abs(psi1) ** 2 * v1[None, :]).sum() / prob.M1)
-    out["epot2"] = float((np.abs(psi2) ** 2 * v2[None, :]).sum() / prob.M2)
+    epot = []
+    for layer in (1, 2):
+        h, c, q = layer_grid(prob, layer)
+        v = grid_potential(h, c, q)
+        psi = _axis_dft(layer_slices(prob, phi, layer), q, inverse=True)
+        epot.append(float((np.abs(psi) ** 2 * v[None, :]).sum() / int(np.prod(q))))
+    out["epot1"], out["epot2"] = epot
     out["energy"] = out["ekin"] + out["epot1"] + out["epot2"]
     k = wavevectors(prob)
     out["kmean"] = [float((k[..., i] * a2).sum()) for i in range(prob.d)]
@@ -509,8 +565,8 @@ def adjoint(prob, phi0: np.ndarray, tau: float, scheme: str, nsteps: int,
 
     Returns (loss, phi_T, g1, g2)."""
     kin = kinetic_energy_diag(prob)
-    v1 = grid_potential(prob.v1_h, prob.v1_c, prob.q1)
-    v2 = grid_potential(prob.v2_h, prob.v2_c, prob.q2)
+    v1 = grid_potential(*layer_grid(prob, 1))
+    v2 = grid_potential(*layer_grid(prob, 2))
     fl = expanded_factors(prob, scheme, tau, nsteps, seed, step0, frac_den)
     traj = [np.array(phi0, dtype=np.complex128)]
     phi = traj[0]
@@ -521,7 +577,7 @@ def adjoint(prob, phi0: np.ndarray, tau: float, scheme: str, nsteps: int,
             phi = apply_P(prob, phi, f[1], f[2], f[3], v1 if f[1] == 1 else v2)
         traj.append(phi)
     loss, lam = lam_T_fn(phi)
-    g = {1: np.zeros(prob.M1), 2: np.zeros(prob.M2)}
+    g = {j: np.zeros(int(np.prod(layer_grid(prob, j)[2]))) for j in (1, 2)}
     for idx in range(len(fl) - 1, -1, -1):
         f = fl[idx]
         out = traj[idx + 1]
@@ -529,10 +585,10 @@ def adjoint(prob, phi0: np.ndarray, tau: float, scheme: str, nsteps: int,
             lam = apply_K(prob, lam, -f[1], kin)
             continue
         layer, s, sl = f[1], f[2], f[3]
-        q = prob.q1 if layer == 1 else prob.q2
-        M = prob.M1 if layer == 1 else prob.M2
-        X_out = out if layer == 1 else out.T
-        X_lam = lam if layer == 1 else lam.T
+        q = layer_grid(prob, layer)[2]
+        M = int(np.prod(q))
+        X_out = layer_slices(prob, out, layer)
+        X_lam = layer_slices(prob, lam, layer)
         if sl is not None:
             X_out, X_lam = X_out[sl], X_lam[sl]
         psi = _axis_dft(X_out, q, inverse=True) / math.sqrt(M)

@@ -41,6 +41,9 @@ PINS = [
     lambda: pins.test_stochastic_steps_match_dense_sampled_factors("strang_stoch"),
     lambda: pins.test_stochastic_steps_match_dense_sampled_factors("lie_stoch"),
     pins.test_gaussian_packet_position_and_momentum,
+    pins.test_example3_free_particle_exact_phase,
+    pins.test_example3_y_independent_reduces_to_1d_planes,
+    pins.test_example3_one_step_and_order_against_dense,
 ]
 
 _orig_dft = L.dft_matrix
@@ -57,6 +60,8 @@ _orig_dens = L.density_on_line
 _orig_wv = L.wavevectors
 _orig_exp = L.expanded_factors
 _orig_gp = L.gaussian_packet
+_orig_lg = L.layer_grid
+_orig_ls = L.layer_slices
 
 
 def _stoch_scale_inverted(prob, scheme, tau, nsteps, seed=0, step0=0, frac_den=8):
@@ -117,6 +122,11 @@ MUTANTS = {
         for f in _orig_exp(prob, scheme, tau, nsteps, seed, step0, frac_den)]),
     "packet_x0_sign": ("gaussian_packet", lambda prob, x0, w, k0: _orig_gp(prob, -np.asarray(x0, dtype=float), w, k0)),
     "packet_k0_sign": ("gaussian_packet", lambda prob, x0, w, k0: _orig_gp(prob, x0, w, -np.asarray(k0, dtype=float))),
+    "shared_grid_extents_swapped": ("layer_grid", lambda prob, layer: (
+        lambda h, c, q: (h, c, q[::-1] if getattr(prob, "shared", 0) else q))(*_orig_lg(prob, layer))),
+    "shared_layer2_p_fastest": ("layer_slices", lambda prob, phi, layer: (
+        phi.reshape(prob.q2[1], prob.q2[0], prob.q1[0]).transpose(2, 1, 0).reshape(prob.q1[0], -1)
+        if getattr(prob, "shared", 0) and layer == 2 else _orig_ls(prob, phi, layer))),
     "cn_layer2_half": ("apply_C", lambda p, phi, layer, s, _kin=None:
                        _orig_C(p, phi, layer, s / 2 if layer == 2 else s, _kin)),
 }

@@ -787,3 +787,92 @@ def test_density_2d_single_plane_wave():
     k = p.B1 @ m + p.B2 @ n
     x = np.array([[0.3, -1.2], [4.0, 2.5]])
     np.testing.assert_allclose(O.lsplit.density_on_line(p, phi, x), (0.7 + 0.1j) * np.exp(1j * (x @ k)), atol=1e-13)
+
+
+# ---------------------------------------------------------------- shared periodic index (Example 3)
+def _example3_dense(p):
+    """Dense D, V1, V2 of a three-index problem (Example 3 of Sec. 5) built from
+    the index ranges and Fourier coefficients: phi[n + q2 p][m] flattened row
+    major; V1 couples (m, p) at fixed n, V2 couples (n, p) at fixed m, each
+    with periodic wrap in both of its indices."""
+    q1, q2, q3 = p.q1[0], p.q2[0], p.q2[1]
+    G1, G2, G3 = p.B1[0, 0], p.B2[0, 0], p.B2[1, 1]
+    m = np.arange(q1) + p.lo1[0]
+    n = np.arange(q2) + p.lo2[0]
+    pp = np.arange(q3) + p.lo2[1]
+    N = q1 * q2 * q3
+    idx = lambda mi, ni, pi: (ni + q2 * pi) * q1 + mi
+    kin = np.zeros(N)
+    V1 = np.zeros((N, N), dtype=np.complex128)
+    V2 = np.zeros((N, N), dtype=np.complex128)
+    for pi in range(q3):
+        for ni in range(q2):
+            for mi in range(q1):
+                kin[idx(mi, ni, pi)] = 0.5 * ((G1 * m[mi] + G2 * n[ni]) ** 2 + (G3 * pp[pi]) ** 2)
+                for (hx, hy), c in zip(p.v1_h, p.v1_c):
+                    V1[idx(mi, ni, pi), idx((mi - hx) % q1, ni, (pi - hy) % q3)] += c
+                for (hx, hy), c in zip(p.v2_h, p.v2_c):
+                    V2[idx(mi, ni, pi), idx(mi, (ni - hx) % q2, (pi - hy) % q3)] += c
+    return kin, V1, V2
+
+
+def test_example3_free_particle_exact_phase():
+    """V = 0 on the three-index lift: every scheme is the exact phase with
+    k = (G1 m + G2 n, G3 p) (Example 3's wavevectors, formed from the ranges)."""
+    p = W.example3(3, 2, 2)
+    z = p.with_potentials(v1_c=np.zeros(len(p.v1_c)), v2_c=np.zeros(len(p.v2_c)))
+    kin, _, _ = _example3_dense(z)
+    x = W.random_state((p.M2, p.M1), 41)
+    for scheme in ("strang", "lie", "strang_stoch"):
+        out = O.step(z, x, 0.013, scheme, 3, seed=2)
+        np.testing.assert_allclose(out.reshape(-1), np.exp(-1j * 0.039 * kin) * x.reshape(-1), atol=1e-12)
+
+
+def test_example3_y_independent_reduces_to_1d_planes():
+    """Potentials without y dependence: each plane p of the three-index lift is
+    an independent 1D bilayer (the 1D oracle) times the phase of its extra
+    kinetic energy (G3 p)^2 / 2."""
+    p = W.example3(4, 3, 2)
+    keep = lambda h, c: (h[h[:, 1] == 0], c[h[:, 1] == 0])
+    h1, c1 = keep(np.asarray(p.v1_h), np.asarray(p.v1_c))
+    h2, c2 = keep(np.asarray(p.v2_h), np.asarray(p.v2_c))
+    p = p.with_potentials(v1_c=c1, v2_c=c2, v1_h=h1, v2_h=h2)
+    x = W.random_state((p.M2, p.M1), 42)
+    tau, n = 0.02, 4
+    out = O.step(p, x, tau, "strang", n)
+    q1, q2, q3 = p.q1[0], p.q2[0], p.q2[1]
+    G1, G2, G3 = p.B1[0, 0], p.B2[0, 0], p.B2[1, 1]
+    one = W.Problem(1, np.array([[G1]]), np.array([[G2]]), (p.lo1[0],), (q1,), (p.lo2[0],), (q2,), 1e9,
+                    h1[:, :1], c1, h2[:, :1], c2)
+    for pi in range(q3):
+        y = p.lo2[1] + pi
+        rows = slice(pi * q2, (pi + 1) * q2)
+        ref = O.step(one, x[rows], tau, "strang", n) * np.exp(-0.5j * n * tau * (G3 * y) ** 2)
+        np.testing.assert_allclose(out[rows], ref, atol=1e-12)
+
+
+def test_example3_one_step_and_order_against_dense():
+    """One step of the three-index lift equals the dense factor product
+    (Strang order of Appendix A, V1 on (m, p) and V2 on (n, p)); Strang
+    converges to the dense exponential of H = D + V1 + V2 with slope 2; the
+    energy is the dense quadratic form."""
+    p = W.example3(2, 2, 2, s1=3.0, s2=2.0)
+    p.B1 = p.B1 / 3.0
+    p.B2 = p.B2 / 3.0
+    kin, V1, V2 = _example3_dense(p)
+    D = np.diag(kin)
+    E = lambda A, t: expm_herm(A, t)
+    x = W.random_state((p.M2, p.M1), 43)
+    t = 0.05
+    U = (E(D, t / 8) @ E(V1, t / 2) @ E(D, t / 8)) @ (E(D, t / 4) @ E(V2, t) @ E(D, t / 4)) \
+        @ (E(D, t / 8) @ E(V1, t / 2) @ E(D, t / 8))
+    np.testing.assert_allclose(O.step(p, x, t, "strang", 1).reshape(-1), U @ x.reshape(-1), atol=1e-12)
+    H = D + V1 + V2
+    T = 0.4
+    exact = E(H, T) @ x.reshape(-1)
+    ns = [8, 16, 32]
+    err = [np.linalg.norm(O.step(p, x, T / k, "strang", k).reshape(-1) - exact) for k in ns]
+    slope = np.polyfit(np.log([T / k for k in ns]), np.log(err), 1)[0]
+    assert abs(slope - 2) < 0.15, (slope, err)
+    v = x.reshape(-1)
+    assert abs(O.observables(p, x)["energy"] - np.vdot(v, H @ v).real) < 1e-10

@@ -55,6 +55,7 @@ class Problem:
     v2_h: np.ndarray
     v2_c: np.ndarray
     name: str = ""
+    shared: int = 0   # 1: the second layer-2 component is an index p common to both layers
 
     @property
     def M1(self) -> int:
@@ -176,6 +177,32 @@ def config_adjoint_1d(seed: int = 5, n_half: int = 256, n_params: int = 8):
     h1, c1 = _cos_coeffs(th[0], hs)
     h2, c2 = _cos_coeffs(th[1], hs)
     return p.with_potentials(c1, c2, h1, h2), th[0].copy(), th[1].copy()
+
+
+def example3(n1: int = 8, n2: int = 8, n3: int = 4, s1: float = 1.0, s2: float = 2.0,
+             beta: float = GOLDEN, ecut: float = 100.0, name: str = "") -> Problem:
+    """Example 3 of Sec. 5: a 2D system periodic in y and incommensurate in x,
+    H = -Laplacian/2 + s1 cos^2(beta x) cos^2(pi y / 2) + s2 cos^2(x) cos^2(pi y / 2).
+    Layer j is periodic in x with period pi / beta_j (beta_1 = beta, beta_2 = 1),
+    so G_j = 2 beta_j; both share the y period 2, G3 = pi.  With cos^2 = (1 + cos)/2
+    the coefficients of s_j cos^2(beta_j x) cos^2(pi y / 2) on the harmonics
+    (h_x, h_y) are s_j/4 (0, 0), s_j/8 (+-1, 0) and (0, +-1), s_j/16 (+-1, +-1).
+    Three-index lift (m, n, p): stored as a 2D problem with the shared index p
+    as the second layer-2 component; box m in [-n1, n1), n in [-n2, n2),
+    p in [-n3, n3) (even lengths)."""
+    def coeffs(s):
+        hs, cs = [], []
+        for hx in (-1, 0, 1):
+            for hy in (-1, 0, 1):
+                hs.append([hx, hy])
+                cs.append(s / 4.0 * (0.5 if hx else 1.0) * (0.5 if hy else 1.0))
+        return np.array(hs, dtype=np.int64), np.array(cs, dtype=np.complex128)
+    h1, c1 = coeffs(s1)
+    h2, c2 = coeffs(s2)
+    B1 = np.array([[2.0 * beta, 0.0], [0.0, 0.0]])
+    B2 = np.array([[2.0, 0.0], [0.0, math.pi]])
+    return Problem(2, B1, B2, (-n1, 0), (2 * n1, 1), (-n2, -n3), (2 * n2, 2 * n3), float(ecut), h1, c1, h2, c2,
+                   name or f"example3-{2 * n1}x{2 * n2}x{2 * n3}", shared=1)
 
 
 def cos_series_coeffs(theta: np.ndarray):
