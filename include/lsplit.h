@@ -107,6 +107,19 @@ enum { LS_LIE = 0, LS_STRANG = 1, LS_STRANG_KP = 2, LS_LIE_STOCH = 3, LS_STRANG_
  *                 time step (the truncated index set of Sec. 3 enforced during
  *                 the evolution).  The projection is not unitary: ls_adjoint
  *                 and the batched runner return LS_ERR_INVALID for it.
+ *   shared        0, or 1 for a three-index lift with an index common to both
+ *                 layers (Example 3 of Sec. 5: periodic in y, incommensurate in
+ *                 x).  The problem is then given as d = 2 with layer-1 box
+ *                 (q1[0], 1) (lo1[1] = 0) and layer-2 box (q2[0], q2[1]); the
+ *                 second layer-2 component is the shared index p, so that
+ *                 k = B1 (m, 0) + B2 (n, p).  Element (m, n, p) is at
+ *                 (n_lin + q2[0] p_lin) * pitch + m_lin.  A layer-1 factor acts
+ *                 on the 2D slices (m, p) at fixed n, a layer-2 factor on
+ *                 (n, p) at fixed m; potential j has harmonics (h_x, h_y) on the
+ *                 grid (q_j[0], q2[1]).  Needs power-of-two q1[0], q2[0], q2[1]
+ *                 with q1[0] q2[1] and q2[0] q2[1] at most 4096; the
+ *                 Crank-Nicolson and semi-implicit schemes and the batched
+ *                 runner return LS_ERR_INVALID.
  * Supported slice shapes: 1D any length (powers of two use a direct radix FFT,
  * others a Bluestein transform of power-of-two length >= 2q-2, at most 8192
  * for LS_C64 and 4096 for LS_C128; ls_create returns LS_ERR_INVALID beyond);
@@ -127,6 +140,7 @@ typedef struct ls_problem {
   int32_t dtype;
   int32_t frac_den;
   int32_t mask_mode;
+  int32_t shared;
 } ls_problem;
 
 enum { LS_MASK_INIT_ONLY = 0, LS_MASK_PROJECT_EACH_STEP = 1 };
@@ -223,7 +237,8 @@ int ls_samples(ls_ctx* ctx, int32_t layer, uint64_t seed, uint64_t g0, int32_t c
  * unitary, so phi_T is rebuilt back to phi_0 while lambda is pulled back), and
  * at every layer factor accumulates dL/dv_j(x_p) = 2 s Im(conj(mu_p) psi_p)
  * (mu, psi: unitary grid transforms of lambda and phi after the factor).
- * grad_v1_host (M1 doubles) and grad_v2_host (M2 doubles) receive the grid
+ * grad_v1_host and grad_v2_host (one double per point of the layer's grid:
+ * M1 and M2, or q_j[0] q2[1] with a shared index) receive the grid
  * gradients; grad_c1_host / grad_c2_host (2*nv doubles, may be NULL) receive
  * (dL/dRe vhat_h, dL/dIm vhat_h) for every coefficient.  On return psi_dev
  * holds the rebuilt phi_0 and lam_dev the gradient with respect to

@@ -44,6 +44,7 @@ class LsProblem(C.Structure):
         ("dtype", C.c_int32),
         ("frac_den", C.c_int32),
         ("mask_mode", C.c_int32),
+        ("shared", C.c_int32),
     ]
 
 
@@ -158,6 +159,7 @@ def make_problem_struct(prob, dtype: str = "c64", frac_den: int = 8, mask_mode: 
     s.dtype = LS_C64 if dtype == "c64" else LS_C128
     s.frac_den = int(frac_den)
     s.mask_mode = MASK_MODES[mask_mode]
+    s.shared = int(getattr(prob, "shared", 0))
     return s, keep
 
 
@@ -266,8 +268,12 @@ class Context:
 
     def adjoint(self, psi, lam, nsteps: int, tau: float, scheme: str = "strang", seed: int = 0, step0: int = 0,
                 stream=None):
-        g1 = np.zeros(self.M1)
-        g2 = np.zeros(self.M2)
+        if getattr(self.prob, "shared", 0):
+            g1 = np.zeros(self.prob.q1[0] * self.prob.q2[1])
+            g2 = np.zeros(self.prob.q2[0] * self.prob.q2[1])
+        else:
+            g1 = np.zeros(self.M1)
+            g2 = np.zeros(self.M2)
         c1 = np.zeros(2 * len(self.prob.v1_c))
         c2 = np.zeros(2 * len(self.prob.v2_c))
         P = C.POINTER(C.c_double)

@@ -451,6 +451,29 @@ void set_kinetic(ls_ctx* c, double u) {
         G22[a][b] += c->p.B2[i * d + a] * c->p.B2[i * d + b];
       }
   const double f = u / (4.0 * kPi);
+  if (c->p.shared) {
+    // |m g_m + n g_n + p g_p|^2 with g_m, g_n, g_p the columns of B1 (first)
+    // and B2 (both): own (a, b) = (m, p) or (n, p), other = n or m
+    const double gm[2] = {c->p.B1[0], c->p.B1[2]}, gn[2] = {c->p.B2[0], c->p.B2[2]},
+                 gp[2] = {c->p.B2[1], c->p.B2[3]};
+    auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1]; };
+    for (int L = 0; L < 2; ++L) {
+      lsk::LayerGeom& g = c->geom[L];
+      const double* ga = L == 0 ? gm : gn;   // own layer's index
+      const double* go = L == 0 ? gn : gm;   // the other layer's index
+      g.A_aa = to_fixed(f * dot(ga, ga));
+      g.A_ab = to_fixed(f * 2.0 * dot(ga, gp));
+      g.A_bb = to_fixed(f * dot(gp, gp));
+      g.X_aa = to_fixed(f * 2.0 * dot(ga, go));
+      g.X_ab = 0;
+      g.X_ba = to_fixed(f * 2.0 * dot(gp, go));
+      g.X_bb = 0;
+      g.C_aa = to_fixed(f * dot(go, go));
+      g.C_ab = 0;
+      g.C_bb = 0;
+    }
+    return;
+  }
   for (int L = 0; L < 2; ++L) {
     lsk::LayerGeom& g = c->geom[L];
     const double(*Go)[2] = (L == 0) ? G11 : G22;   // own
@@ -519,6 +542,17 @@ int validate(const ls_problem* p) {
   if (p->nv1 < 0 || p->nv2 < 0) return fail(LS_ERR_INVALID, "negative coefficient count");
   if ((p->nv1 > 0 && (!p->v1_h || !p->v1_c)) || (p->nv2 > 0 && (!p->v2_h || !p->v2_c)))
     return fail(LS_ERR_INVALID, "coefficient arrays are NULL");
+  if (p->shared != 0 && p->shared != 1) return fail(LS_ERR_INVALID, "shared must be 0 or 1");
+  if (p->shared) {
+    if (p->d != 2 || p->q1[1] != 1 || p->lo1[1] != 0)
+      return fail(LS_ERR_INVALID, "a shared index needs d = 2 with layer-1 box (q1[0], 1) and lo1[1] = 0");
+    if (!is_pow2(p->q1[0]) || !is_pow2(p->q2[0]) || !is_pow2(p->q2[1]) || p->q1[0] < 2 || p->q2[0] < 2 ||
+        p->q2[1] < 2)
+      return fail(LS_ERR_INVALID, "three-index slices need power-of-two extents >= 2");
+    if ((int64_t)p->q1[0] * p->q2[1] > 4096 || (int64_t)p->q2[0] * p->q2[1] > 4096)
+      return fail(LS_ERR_INVALID, "three-index slice larger than 4096 elements");
+    return LS_OK;
+  }
   for (int L = 0; L < 2; ++L) {
     const int32_t* q = L == 0 ? p->q1 : p->q2;
     if (p->d == 1) {
@@ -578,6 +612,28 @@ void build_geometry(ls_ctx* c) {
       g.slice_stride = 1;
       g.ea = c->pitch;
       g.eb = (int64_t)p.q2[0] * c->pitch;
+    }
+    if (p.shared) {
+      // three-index lift: layer 1 on (m, p) at fixed n, layer 2 on (n, p) at
+      // fixed m; element (m, n, p) at (n + q2 p) pitch + m
+      g.qa = L == 0 ? p.q1[0] : p.q2[0];
+      g.qb = p.q2[1];
+      g.M = g.qa * g.qb;
+      g.lo_a = L == 0 ? p.lo1[0] : p.lo2[0];
+      g.lo_b = p.lo2[1];
+      g.oqa = L == 0 ? p.q2[0] : p.q1[0];
+      g.olo_a = L == 0 ? p.lo2[0] : p.lo1[0];
+      g.olo_b = 0;
+      g.nslices = g.oqa;
+      g.np = g.qa;
+      g.npb = g.qb;
+      g.buf = g.M;
+      g.sb = g.buf + (g.buf >> 4) + 1;
+      if (c->dtype == LS_C64 && (g.sb & 1)) g.sb += 1;
+      g.slice_stride = L == 0 ? c->pitch : 1;
+      g.ea = L == 0 ? 1 : c->pitch;
+      g.eb = (int64_t)p.q2[0] * c->pitch;
+      g.shared_b = 1;
     }
   }
 }
@@ -782,8 +838,8 @@ int factors_per_step(int scheme) {
 lsk::SamplerArgs sampler_args(ls_ctx* c, int scheme, int& npf) {
   lsk::SamplerArgs sa;
   std::memset(&sa, 0, sizeof(sa));
-  sa.S1 = (int32_t)c->M2;
-  sa.S2 = (int32_t)c->M1;
+  sa.S1 = (int32_t)c->geom[0].nslices;
+  sa.S2 = (int32_t)c->geom[1].nslices;
   sa.p1 = std::max<int32_t>(1, sa.S1 / c->frac_den);
   sa.p2 = std::max<int32_t>(1, sa.S2 / c->frac_den);
   sa.Smax = std::max(sa.S1, sa.S2);
@@ -1201,8 +1257,8 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
         upload_c(c.get(), c->chirp[L], ch);
         g.chirp = c->chirp[L].p;
       }
-      c->vhost[L] = grid_potential(L == 0 ? c->h1 : c->h2, L == 0 ? c->c1 : c->c2, c->d,
-                                   L == 0 ? prob->q1 : prob->q2);
+      const int32_t gq[2] = {g.qa, g.qb};   // the layer's grid (with a shared index: (q_j, q3))
+      c->vhost[L] = grid_potential(L == 0 ? c->h1 : c->h2, L == 0 ? c->c1 : c->c2, c->d, gq);
       c->vgrid[L].alloc(c->vhost[L].size() * sizeof(double));
       LS_CUDA(cudaMemcpy(c->vgrid[L].p, c->vhost[L].data(), c->vhost[L].size() * sizeof(double),
                          cudaMemcpyHostToDevice));
@@ -1241,7 +1297,7 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     for (int L = 0; L < 2; ++L) c->stW[L] = stencil_width(c->geom[L], c->esize, L == 1);
     LS_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device));
     // tensor-core form of the contiguous 64 x 64 layer (complex64)
-    if (c->dtype == LS_C64 && c->d == 2 && c->geom[0].qa == 64 && c->geom[0].qb == 64 &&
+    if (c->dtype == LS_C64 && c->d == 2 && !c->p.shared && c->geom[0].qa == 64 && c->geom[0].qb == 64 &&
         lsk::tc2d_smem_bytes() + 8192 <= (size_t)dev_max + static_reserve && getenv_flag("LSPLIT_TC2D")) {
       LS_CUDA(lsk::tc2d_prepare(block_max));
       const std::vector<uint16_t> pl = dft64_split_planes();
@@ -1252,7 +1308,8 @@ int ls_create(const ls_problem* prob, ls_ctx** out) {
     for (int L = 0; L < 2; ++L) {
       const lsk::LayerGeom& g = c->geom[L];
       const size_t sm = c->dtype == LS_C64 ? lsk::fast2d_smem_bytes<float>(g) : lsk::fast2d_smem_bytes<double>(g);
-      c->fast2d[L] = g.d == 2 && g.qa == 64 && g.qb == 64 && sm <= (size_t)dev_max && !getenv_flag("LSPLIT_NO_FAST");
+      c->fast2d[L] = g.d == 2 && g.qa == 64 && g.qb == 64 && sm <= (size_t)dev_max && !getenv_flag("LSPLIT_NO_FAST") &&
+                     !c->p.shared;
     }
     for (int L = 0; L < 2; ++L) {
       const lsk::LayerGeom& g = c->geom[L];
@@ -1595,7 +1652,7 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
     } ks{c};
     c->keep = &keep;
     for (int L = 0; L < 2; ++L) {
-      const int64_t M = L == 0 ? c->M1 : c->M2;
+      const int64_t M = c->geom[L].M;   // the layer's grid
       if (c->grad[L].bytes < (size_t)M * sizeof(double)) c->grad[L].alloc((size_t)M * sizeof(double));
       LS_CUDA(lsk::launch_zero_f64((double*)c->grad[L].p, M, st));
     }
@@ -1657,8 +1714,8 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
       kin_all(-q.pre);
     }
     set_kinetic(c, u);  // the call's unit (the fourth-order sweep changed it per pass)
-    LS_CUDA(cudaMemcpyAsync(gv1, c->grad[0].p, c->M1 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LS_CUDA(cudaMemcpyAsync(gv2, c->grad[1].p, c->M2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaMemcpyAsync(gv1, c->grad[0].p, c->geom[0].M * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LS_CUDA(cudaMemcpyAsync(gv2, c->grad[1].p, c->geom[1].M * sizeof(double), cudaMemcpyDeviceToHost, st));
     LS_CUDA(cudaStreamSynchronize(st));
     // chain rule to the Fourier coefficients: v_p = Re sum_h c_h e^{2 pi i h.p/q}
     for (int L = 0; L < 2; ++L) {
@@ -1666,10 +1723,10 @@ int ls_adjoint(ls_ctx* c, void* psi, void* lam, int64_t n, double tau, int32_t s
       if (!gc) continue;
       const double* gv = L == 0 ? gv1 : gv2;
       const std::vector<int32_t>& h = L == 0 ? c->h1 : c->h2;
-      const int32_t* q = L == 0 ? c->p.q1 : c->p.q2;
+      const int32_t q[2] = {c->geom[L].qa, c->geom[L].qb};   // the layer's grid
       const int d = c->d;
       const size_t nh = h.size() / d;
-      const int64_t M = L == 0 ? c->M1 : c->M2;
+      const int64_t M = c->geom[L].M;
       for (size_t t = 0; t < nh; ++t) {
         double re = 0, im = 0;
         for (int64_t p = 0; p < M; ++p) {

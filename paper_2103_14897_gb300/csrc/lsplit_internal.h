@@ -27,6 +27,8 @@ struct LayerGeom {
   int64_t ea, eb;     // global element strides along a and b
   int lo_a, lo_b;     // own box lower bounds: signed index = lo + i
   int oqa, olo_a, olo_b;  // other box: slice index s -> (s % oqa + olo_a, s / oqa + olo_b)
+  int shared_b;       // 1: the b index is shared by both layers (three-index lift); the
+                      // other layer's slice of element (ia, ib) is then ia alone
   uint64_t A_aa, A_ab, A_bb;           // own quadratic form
   uint64_t X_aa, X_ab, X_ba, X_bb;     // cross: l_a = X_aa nu_a + X_ab nu_b, l_b = X_ba nu_a + X_bb nu_b
   uint64_t C_aa, C_ab, C_bb;           // other quadratic form

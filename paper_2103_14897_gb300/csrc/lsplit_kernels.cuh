@@ -494,7 +494,8 @@ __device__ __forceinline__ void pass_tile(const PassArgs& a, int64_t tile, unsig
       if (!measure) {
         int64_t units = a.units_pre;
         if (lazy || kin_touch) {
-          const int32_t t2 = CG ? __ldcg(a.touch_other + i) : a.touch_other[i];
+          const int oi = g.shared_b ? ia : i;   // the other layer's slice of this element
+          const int32_t t2 = CG ? __ldcg(a.touch_other + oi) : a.touch_other[oi];
           units = (int64_t)a.now - (int64_t)(s_touch[w] > t2 ? s_touch[w] : t2);
         }
         if (units != 0) {

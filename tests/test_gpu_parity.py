@@ -715,3 +715,60 @@ def test_error_codes(P):
         ctx.adjoint(psi, psi, 1, 1e-3, "cn_strang")
     with pytest.raises(P.LsplitError):
         ctx.adjoint(psi, psi, 1, 1e-3, "semi_implicit")
+
+
+def example3_problems():
+    """Example 3's three-index lift (periodic in y, incommensurate in x): the
+    paper's potentials s1 cos^2(beta x) cos^2(pi y/2) + s2 cos^2(x) cos^2(pi y/2)
+    with s = (1, 2) and (0.16, 8), boxes with a 2D (m, p) and (n, p) slice of
+    several shapes, the cutoff Ec = 100 and every mode kept."""
+    import dataclasses
+    return [W.example3(8, 4, 4), W.example3(4, 8, 2, s1=0.16, s2=8.0),
+            dataclasses.replace(W.example3(16, 2, 8), ecut=1e9, name="example3-32x4x16")]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp", "yoshida4", "lie_stoch", "strang_stoch"])
+def test_example3_three_index_parity(P, dtype, scheme):
+    """Three-index lift on the GPU: layer factors over the (m, p) and (n, p)
+    planes (2D slices sharing the y index), kinetic phases of
+    |(G1 m + G2 n, G3 p)|^2 / 2, lazy phases of the stochastic schemes keyed
+    by the other layer's x index; against the oracle."""
+    for p in example3_problems():
+        ctx = P.Context(p, dtype)
+        x = W.random_state((p.M2, p.M1), 33)
+        psi = ctx.from_dense(x)
+        ctx.step(psi, 3, 5e-3, scheme, seed=2, step0=1)
+        ref = O.step(p, x, 5e-3, scheme, 3, seed=2, step0=1)
+        assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 5, (p.name, scheme, rel(ctx.to_dense(psi), ref))
+
+
+def test_example3_state_observables_and_adjoint(P):
+    """Example 3: the packet initial state on the joint cutoff, observables
+    (energy with both layer potentials on their (x, y) grids), the mass after
+    200 Strang steps, the density at points of the plane, and the reverse
+    sweep's gradients against the oracle's adjoint."""
+    p = W.example3(8, 4, 4)
+    for dtype, tol in (("c64", 1e-5), ("c128", 1e-11)):
+        ctx = P.Context(p, dtype)
+        psi = ctx.empty()
+        ctx.init_gaussian(psi, [0.2, -0.3], 2.0, [1.0, 0.5])
+        x = O.gaussian_packet(p, [0.2, -0.3], 2.0, [1.0, 0.5])
+        assert rel(ctx.to_dense(psi), x) < tol
+        o, r = ctx.observables(psi), O.observables(p, ctx.to_dense(psi))
+        for k in ("norm", "ekin", "epot1", "epot2", "energy"):
+            assert abs(o[k] - r[k]) < tol * 10 * max(1.0, abs(r[k])), (dtype, k, o[k], r[k])
+        pts = np.array([[0.1, 0.2], [1.3, -0.7], [-2.5, 0.4]])
+        assert rel(ctx.density(psi, pts), O.density_on_line(p, ctx.to_dense(psi), pts)) < tol
+        ctx.step(psi, 200, 1e-3, "strang")
+        got = ctx.to_dense(psi)
+        assert rel(got, O.step(p, x, 1e-3, "strang", 200)) < (1e-4 if dtype == "c64" else 1e-10)
+        assert abs(np.linalg.norm(got) - 1) < (1e-5 if dtype == "c64" else 1e-12)
+        chi = O.gaussian_packet(p, [0.0, 0.0], 1.5, [0.5, 0.0])
+        L, phiT, g1, g2 = O.adjoint(p, x, 1e-2, "strang", 4, lambda f: O.overlap_loss(chi, f))
+        psi = ctx.from_dense(phiT)
+        lam = ctx.from_dense(O.overlap_loss(chi, phiT)[1])
+        gg1, gg2, _, _ = ctx.adjoint(psi, lam, 4, 1e-2, "strang")
+        sc = max(np.abs(g1).max(), np.abs(g2).max())
+        assert np.abs(gg1 - g1).max() < tol * 100 * sc and np.abs(gg2 - g2).max() < tol * 100 * sc, dtype
+        assert rel(ctx.to_dense(psi), x) < tol * 10
