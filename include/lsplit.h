@@ -290,19 +290,21 @@ int ls_batch_observables(ls_batch* batch, const void* psi_dev, ls_obs* out_host,
 /* Configuration of the compact-kernel batched launch (used when every factor
  * of every instance takes the compact-kernel form): *threads per CTA,
  * *ctas_per_sm the registers are budgeted for, *tile_bytes of shared memory
- * per tile, *tuned = 1 once the autotuner has chosen them; *threads = 0 when
- * it chose the transform (FFT) forms instead.  The autotuner runs inside the
- * first ls_batch_step of a (scheme, tau) whose factors all qualify for the
- * compact kernel (complex64 batches): it times the configurations (256, 3),
- * (256, 4), (128, 6), (128, 8) and the transform forms, two steps each, on a
- * library-allocated scratch copy of psi, keeps the fastest and records it for
- * the process (same shapes, dtype, scheme and tau reuse it).  tune_ms (may be
- * NULL) receives up to *ntimes of the last tuning's times in ms per two steps,
- * in that order; *ntimes is then set to the number recorded.  Environment:
- * LSPLIT_TUNE=0 keeps the default (128, 6); LSPLIT_STENCIL_CFG="threads,ctas"
+ * per tile, *tiles_per_item consecutive tiles per claimed work item, *tuned = 1
+ * once the autotuner has chosen them; *threads = 0 when it chose the transform
+ * (FFT) forms instead.  The autotuner runs inside the first ls_batch_step of a
+ * (scheme, tau) whose factors all qualify for the compact kernel (complex64
+ * batches): it times the configurations (threads, CTAs, tiles per item)
+ * (256, 3, 1), (256, 3, 2), (256, 4, 1), (128, 6, 1), (128, 6, 2), (128, 6, 4),
+ * (128, 8, 2) and the transform forms, two steps each, on a library-allocated
+ * scratch copy of psi, keeps the fastest and records it for the process (same
+ * shapes, dtype, scheme and tau reuse it).  tune_ms (may be NULL) receives up
+ * to *ntimes of the last tuning's times in ms per two steps, in that order;
+ * *ntimes is then set to the number recorded.  Environment: LSPLIT_TUNE=0
+ * keeps the default (128, 6, 1); LSPLIT_STENCIL_CFG="threads,ctas[,tiles]"
  * forces one. */
 int ls_batch_config(const ls_batch* batch, int32_t* threads, int32_t* ctas_per_sm, int64_t* tile_bytes,
-                    int32_t* tuned, float* tune_ms, int32_t* ntimes);
+                    int32_t* tiles_per_item, int32_t* tuned, float* tune_ms, int32_t* ntimes);
 /* Wait budget of one dependency wait (seconds, default 1) and a test hook that
  * makes one wait unsatisfiable (unmet_dependency != 0) to exercise the
  * timeout path. */

@@ -97,7 +97,7 @@ def load_library(path: str = LIB_PATH):
     lib.ls_batch_observables.argtypes = [vp, vp, C.POINTER(LsObs), vp]
     lib.ls_batch_debug.argtypes = [vp, i32, dbl]
     lib.ls_batch_config.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
-                                    C.POINTER(C.c_float), C.POINTER(i32)]
+                                    C.POINTER(i32), C.POINTER(C.c_float), C.POINTER(i32)]
     for name in EXPORTS[1:]:
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -372,11 +372,12 @@ class Batch:
     def config(self) -> dict:
         """ls_batch_config: the compact-kernel launch configuration and the
         autotuner's last timings (ms per two steps per candidate)."""
-        t, c, tb, tu, n = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(8)
-        ms = (C.c_float * 8)()
-        _check(_lib.ls_batch_config(self._h, C.byref(t), C.byref(c), C.byref(tb), C.byref(tu), ms, C.byref(n)))
-        return {"threads": t.value, "ctas_per_sm": c.value, "tile_bytes": tb.value, "tuned": bool(tu.value),
-                "tune_ms": [ms[k] for k in range(min(n.value, 8))]}
+        t, c, tb, sub, tu, n = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(16)
+        ms = (C.c_float * 16)()
+        _check(_lib.ls_batch_config(self._h, C.byref(t), C.byref(c), C.byref(tb), C.byref(sub), C.byref(tu), ms,
+                                    C.byref(n)))
+        return {"threads": t.value, "ctas_per_sm": c.value, "tile_bytes": tb.value, "tiles_per_item": sub.value,
+                "tuned": bool(tu.value), "tune_ms": [ms[k] for k in range(min(n.value, 16))]}
 
     def debug(self, unmet: bool, timeout_s: float = 1.0):
         _check(_lib.ls_batch_debug(self._h, 1 if unmet else 0, float(timeout_s)))

@@ -1765,6 +1765,7 @@ struct ls_batch {
   std::vector<int> Si1[2];    // the same for the compact-only kernel (KIND 1)
   int minb1 = 3;              // CTAs per SM of the compact-only kernel
   int nthreads1 = 256;        // its threads per CTA
+  int subtiles1 = 1;          // its tiles per work item
   size_t budget1 = 0;         // its tile budget (bytes of shared memory)
   size_t smem1 = 0;           // its dynamic shared memory
   int blocks1 = 0;            // its persistent grid
@@ -1916,7 +1917,10 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
           a.W = sw;
           a.strided = L == 1 ? 1 : 0;
           a.fast_logn = 0;
+          if (kind == 1) a.subtiles = b->subtiles1;
         }
+        // slices per work item (a compact-only item may cover several tiles)
+        const int64_t wi = (int64_t)a.W * (a.subtiles > 1 ? a.subtiles : 1);
         if (!stoch) {
           a.mode = lsk::MODE_STEP;
           a.T = phase_table(c, layer, ps[q].s);
@@ -1926,7 +1930,7 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
             a.fix0_re = ct.fix_re;
             a.fix0_im = ct.fix_im;
           }
-          tiles = (c->geom[L].nslices + a.W - 1) / a.W;
+          tiles = (c->geom[L].nslices + wi - 1) / wi;
         } else {
           const int64_t Sv = c->geom[L].nslices;
           const int32_t pv = sP[(size_t)i * npass + q];
@@ -1945,7 +1949,7 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
           int32_t* cols = rows + c->M2;
           a.touch_own = L == 0 ? rows : cols;
           a.touch_other = L == 0 ? cols : rows;
-          tiles = (pv + a.W - 1) / a.W;
+          tiles = (pv + wi - 1) / wi;
         }
         args[(size_t)q * ninst + i] = a;
         cum[(size_t)q * (ninst + 1) + i] = acc;
@@ -2075,9 +2079,10 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
 // Compact-only kernel configuration: threads per CTA, CTAs per SM and the
 // tile budget that lets that many CTAs share an SM; recomputes the tile widths,
 // shared memory and the persistent grid.
-void apply_compact_config(ls_batch* b, int nt, int mb) {
+void apply_compact_config(ls_batch* b, int nt, int mb, int sub) {
   b->nthreads1 = nt;
   b->minb1 = mb;
+  b->subtiles1 = sub;
   b->budget1 = mb == 3 ? kStencilTileBytes : mb == 4 ? kStencilTileBytes4 : mb == 6 ? 32 * 1024 : 22 * 1024;
   b->smem1 = 0;
   const size_t es = b->dtype == LS_C64 ? 8 : 16;
@@ -2123,7 +2128,10 @@ bool batch_all_compact(ls_batch* b, double tau, int32_t scheme) {
 // Process-wide record of tuned configurations, keyed by the batch's shapes,
 // dtype, scheme and time step.
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tuned;   // (threads, CTAs per SM); threads 0: transform forms
+struct TunedCfg {
+  int threads, ctas, sub;   // threads 0: the transform forms
+};
+std::map<std::string, TunedCfg> g_tuned;
 
 std::string tune_key(const ls_batch* b, double tau, int32_t scheme) {
   std::string k = std::to_string(b->dtype) + ":" + std::to_string(scheme) + ":";
@@ -2148,9 +2156,10 @@ void maybe_tune(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, c
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      if (it->second.first == 0) b->transform_form = true;
-      else if (it->second.first != b->nthreads1 || it->second.second != b->minb1)
-        apply_compact_config(b, it->second.first, it->second.second);
+      const TunedCfg& t = it->second;
+      if (t.threads == 0) b->transform_form = true;
+      else if (t.threads != b->nthreads1 || t.ctas != b->minb1 || t.sub != b->subtiles1)
+        apply_compact_config(b, t.threads, t.ctas, t.sub);
       b->tuned = 1;
       return;
     }
@@ -2161,12 +2170,14 @@ void maybe_tune(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, c
   scratch.alloc(bytes);
   LS_CUDA(cudaMemcpyAsync(scratch.p, psi, bytes, cudaMemcpyDeviceToDevice, st));
   LS_CUDA(cudaStreamSynchronize(st));
-  const int cand[5][2] = {{256, 3}, {256, 4}, {128, 6}, {128, 8}, {0, 0}};
+  constexpr int kCand = 8;
+  const int cand[kCand][3] = {{256, 3, 1}, {256, 3, 2}, {256, 4, 1}, {128, 6, 1},
+                              {128, 6, 2}, {128, 6, 4}, {128, 8, 2}, {0, 0, 0}};
   float best = 0.f;
   int bi = -1;
   b->tune_ms.clear();
-  for (int ci = 0; ci < 5; ++ci) {
-    if (cand[ci][0] > 0) apply_compact_config(b, cand[ci][0], cand[ci][1]);
+  for (int ci = 0; ci < kCand; ++ci) {
+    if (cand[ci][0] > 0) apply_compact_config(b, cand[ci][0], cand[ci][1], cand[ci][2]);
     b->transform_form = cand[ci][0] == 0;
     std::unique_ptr<ls_batch::Cached> g = build_batch_graph(b, scratch.p, 2, tau, scheme);
     cudaEvent_t e0, e1;
@@ -2196,11 +2207,11 @@ void maybe_tune(ls_batch* b, void* psi, int64_t n, double tau, int32_t scheme, c
   LS_CUDA(cudaMemsetAsync(b->status.p, 0, sizeof(int32_t), st));
   LS_CUDA(cudaStreamSynchronize(st));
   b->transform_form = cand[bi][0] == 0;
-  if (cand[bi][0] > 0) apply_compact_config(b, cand[bi][0], cand[bi][1]);
+  if (cand[bi][0] > 0) apply_compact_config(b, cand[bi][0], cand[bi][1], cand[bi][2]);
   b->tuned = 1;
   b->graphs.clear();
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tuned[key] = std::make_pair(cand[bi][0], cand[bi][1]);
+  g_tuned[key] = TunedCfg{cand[bi][0], cand[bi][1], cand[bi][2]};
 }
 
 }  // namespace
@@ -2227,10 +2238,12 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
       // (128, 6) until the autotuner picks; LSPLIT_STENCIL_CFG forces one and
       // turns the tuning off, as does LSPLIT_TUNE=0
       const char* cf = std::getenv("LSPLIT_STENCIL_CFG");
-      int nt = 128, mb = 6;
+      int nt = 128, mb = 6, sub = 1;
       if (cf) {
         b->tune = false;
-        if (std::sscanf(cf, "%d,%d", &nt, &mb) != 2) nt = 128, mb = 6;
+        const int got = std::sscanf(cf, "%d,%d,%d", &nt, &mb, &sub);
+        if (got < 2) nt = 128, mb = 6;
+        if (got < 3 || sub < 1 || sub > 8) sub = 1;
       }
       const char* tv = std::getenv("LSPLIT_TUNE");
       if (tv && tv[0] == '0') b->tune = false;
@@ -2238,6 +2251,7 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
       if (!((nt == 256 && (mb == 3 || mb == 4)) || (nt == 128 && (mb == 6 || mb == 8)))) nt = 128, mb = 6;
       b->nthreads1 = nt;
       b->minb1 = mb;
+      b->subtiles1 = sub;
       b->budget1 = mb == 3 ? kStencilTileBytes : mb == 4 ? kStencilTileBytes4 : mb == 6 ? 32 * 1024 : 22 * 1024;
     }
     LS_CUDA(cudaGetDevice(&b->device));
@@ -2390,9 +2404,10 @@ int ls_batch_observables(ls_batch* b, const void* psi, ls_obs* out, void* stream
   return LS_OK;
 }
 
-int ls_batch_config(const ls_batch* b, int32_t* threads, int32_t* ctas_per_sm, int64_t* tile_bytes, int32_t* tuned,
-                    float* tune_ms, int32_t* ntimes) {
+int ls_batch_config(const ls_batch* b, int32_t* threads, int32_t* ctas_per_sm, int64_t* tile_bytes,
+                    int32_t* tiles_per_item, int32_t* tuned, float* tune_ms, int32_t* ntimes) {
   if (!b) return fail(LS_ERR_STATE, "batch is NULL");
+  if (tiles_per_item) *tiles_per_item = b->subtiles1;
   if (threads) *threads = b->transform_form ? 0 : b->nthreads1;
   if (ctas_per_sm) *ctas_per_sm = b->minb1;
   if (tile_bytes) *tile_bytes = (int64_t)b->budget1;

@@ -85,6 +85,7 @@ struct PassArgs {
   // working precision; taps holds 2 sB + 1 complex Real values, d = -sB..sB.
   const void* taps;
   int32_t sB;
+  int32_t subtiles;        // batched compact-only kernel: consecutive tiles per work item (0 or 1: one)
 };
 
 constexpr int kStencilMaxB = 8;       // widest compact kernel (17 taps)

@@ -1733,6 +1733,8 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   const bool strided = a.strided != 0;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarp = NT >> 5;
+  // a tile past the last slice (the tail of a multi-tile work item) is empty
+  if (tile * W >= (a.list ? (int64_t)a.nlist : g.nslices)) return;
   C* sm = reinterpret_cast<C*>(smraw);
   int64_t* s_slice = g_tm.slice;
   uint64_t *s_la = g_tm.la, *s_c0 = g_tm.c0;
@@ -2029,11 +2031,17 @@ __device__ __forceinline__ bool batch_fast_tile(const PassArgs& a, int64_t tile,
 template <typename Real, int BPT, int MODE, int KIND>
 __device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   if constexpr (KIND == 1) {
-    switch (a.sB) {
-      case 2: stencil_tile<Real, MODE, true, 2>(a, tile, smraw); break;
-      case 3: stencil_tile<Real, MODE, true, 3>(a, tile, smraw); break;
-      case 5: stencil_tile<Real, MODE, true, 5>(a, tile, smraw); break;
-      default: stencil_tile<Real, MODE, true, 8>(a, tile, smraw); break;
+    // an item covers `subtiles` consecutive tiles, processed back to back
+    const int nsub = a.subtiles > 1 ? a.subtiles : 1;
+    for (int k = 0; k < nsub; ++k) {
+      if (k) __syncthreads();
+      const int64_t tk = tile * nsub + k;
+      switch (a.sB) {
+        case 2: stencil_tile<Real, MODE, true, 2>(a, tk, smraw); break;
+        case 3: stencil_tile<Real, MODE, true, 3>(a, tk, smraw); break;
+        case 5: stencil_tile<Real, MODE, true, 5>(a, tk, smraw); break;
+        default: stencil_tile<Real, MODE, true, 8>(a, tk, smraw); break;
+      }
     }
   } else {
     if (!batch_stencil_tile<Real, MODE>(a, tile, smraw) && !batch_fast_tile<Real, MODE>(a, tile, smraw))
@@ -2211,8 +2219,8 @@ batch_kernel(const BatchArgs b) {
       batch_tile<Real, BPT, MODE_STEP, KIND>(s_args, s_tile, smraw);
       if (b.fused && s_pass == 2 && s_args.Khat2 == nullptr) {
         // fused item without a fused tile body: the second factor on the same
-        // slices, after the first is complete in this CTA
-        __threadfence();
+        // slices, after the first is complete in this CTA (the barrier orders
+        // the CTA's own global writes before its reads)
         __syncthreads();
         const int* src = reinterpret_cast<const int*>(b.args + (size_t)4 * b.ninst + s_inst);
         int* dst = reinterpret_cast<int*>(&s_args);
@@ -2221,9 +2229,13 @@ batch_kernel(const BatchArgs b) {
         batch_tile<Real, BPT, MODE_STEP, KIND>(s_args, s_tile, smraw);
       }
     }
-    __threadfence();
+    // every thread's stores precede the barrier; thread 0 then fences at GPU
+    // scope and publishes the completed tile to the other CTAs
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&done[s_inst], 1ull);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd((unsigned long long*)&done[s_inst], 1ull);
+    }
   }
 }
 

@@ -101,7 +101,7 @@ def test_batched_fast_tiles_parity(P, scheme, form, monkeypatch):
         O.use_fft(False)
 
 
-@pytest.mark.parametrize("cfg", ["256,3", "256,4", "128,6", "128,8"])
+@pytest.mark.parametrize("cfg", ["256,3", "256,4", "128,6", "128,8", "128,6,2", "256,3,4"])
 def test_batched_compact_configurations_parity(P, cfg, monkeypatch):
     """Every launch configuration of the compact-kernel batched kernel (threads
     per CTA, CTAs per SM and the tile widths they imply) against the oracle,
@@ -109,7 +109,8 @@ def test_batched_compact_configurations_parity(P, cfg, monkeypatch):
     monkeypatch.setenv("LSPLIT_STENCIL_CFG", cfg)
     probs = uneven_batch()
     b = P.Batch(probs, "c64")
-    assert (b.config()["threads"], b.config()["ctas_per_sm"]) == tuple(int(v) for v in cfg.split(","))
+    want = [int(v) for v in cfg.split(",")] + [1]
+    assert (b.config()["threads"], b.config()["ctas_per_sm"], b.config()["tiles_per_item"]) == tuple(want[:3])
     xs = [W.random_state((p.M2, p.M1), 90 + i) for i, p in enumerate(probs)]
     for scheme in ("strang", "strang_stoch"):
         psi = b.empty()
@@ -136,7 +137,7 @@ def test_batched_autotuner_never_slower_than_default(P, monkeypatch):
     bt.init_gaussian(pt, [0.0], 2.0, [1.0])
     bt.step(pt, 4, 1e-3, "strang")
     cfg = bt.config()
-    assert cfg["tuned"] and len(cfg["tune_ms"]) == 5, cfg
+    assert cfg["tuned"] and len(cfg["tune_ms"]) == 8, cfg
     assert min(cfg["tune_ms"]) > 0
     monkeypatch.setenv("LSPLIT_STENCIL_CFG", "256,3")
     bd = P.Batch(probs, "c64")
