@@ -499,7 +499,9 @@ def run_ours(args):
     # the persistent batched kernel is the only kernel of a deterministic call
     # (one graph launch: a counter reset and the kernel)
     npass = {"lie": 2, "strang_kp": 2}.get(scheme.replace("_stoch", ""), 3)
-    roof = _hbm_roofline(16 * npass * dof * NI, t_ms / args.steps, hbm, src, _traffic(f"batch_kernel:{scheme}"),
+    tr = _traffic(f"batch_kernel:{scheme}")
+    traffic = int(tr["bytes_per_dof_step"] * dof * NI) if isinstance(tr, dict) else None
+    roof = _hbm_roofline(16 * npass * dof * NI, t_ms / args.steps, hbm, src, traffic,
                          f"batch_kernel: {npass} slice passes of 16 B per DOF per time step over {dof} DOF, "
                          f"{NI} time steps per launch; duration from CUDA events around each launch")
 
