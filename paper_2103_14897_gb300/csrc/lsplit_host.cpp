@@ -68,6 +68,12 @@ uint64_t to_fixed(double x) {
   return neg ? (uint64_t)0 - v : v;
 }
 
+// The scalar Lambda of an interaction-frame call as (arg in 2^-64 turns, 1 - |Lambda|).
+void lambda_parts(std::complex<double> lam, uint64_t& turns, double& def) {
+  turns = to_fixed(std::arg(lam) / (2.0 * kPi));
+  def = 1.0 - std::abs(lam);
+}
+
 bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 int log2i(int64_t x) {
   int l = 0;
@@ -146,6 +152,10 @@ struct CachedTab {
   double fix_re = 0, fix_im = 0;
   int B = 0;          // compact-kernel tables: half-width of the kept taps (0: not applicable)
   uint64_t used = 0;
+  // compact-kernel tables: the interaction-frame taps c'_d / (1 + c'_0)
+  // (zero centre) and 1 + c'_0, the factor's scalar part
+  std::shared_ptr<DevBuf> ipbuf;
+  std::complex<double> diag{1.0, 0.0};
 };
 constexpr size_t kTableCacheCap = 48;
 
@@ -361,6 +371,7 @@ CachedTab stencil_table(ls_ctx* c, int layer, double s) {
   if (it != c->stab.end()) {
     it->second.used = ++c->tab_clock;
     if (c->keep && it->second.buf) c->keep->push_back(it->second.buf);
+    if (c->keep && it->second.ipbuf) c->keep->push_back(it->second.ipbuf);
     return it->second;
   }
   CachedTab e;
@@ -378,10 +389,14 @@ CachedTab stencil_table(ls_ctx* c, int layer, double s) {
         if (d > B || d < -B) tail += std::abs(cp[j]);
       }
       if (tail <= eps) {
-        std::vector<cd> taps(2 * B + 1);
+        std::vector<cd> taps(2 * B + 1), iptaps(2 * B + 1);
         for (int k = 0; k <= 2 * B; ++k) taps[k] = cp[((k - B) % q + q) % q];
+        e.diag = 1.0 + cp[0];
+        for (int k = 0; k <= 2 * B; ++k) iptaps[k] = k == B ? cd(0, 0) : taps[k] / e.diag;
         e.buf = std::make_shared<DevBuf>();
         upload_c(c, *e.buf, taps);
+        e.ipbuf = std::make_shared<DevBuf>();
+        upload_c(c, *e.ipbuf, iptaps);
         e.B = B;
         break;
       }
@@ -389,6 +404,7 @@ CachedTab stencil_table(ls_ctx* c, int layer, double s) {
   }
   c->stab[key] = e;
   if (c->keep && e.buf) c->keep->push_back(e.buf);
+  if (c->keep && e.ipbuf) c->keep->push_back(e.ipbuf);
   evict_tables(c->stab);
   return e;
 }
@@ -1065,6 +1081,15 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     }
     ps.swap(merged);
   }
+  // Interaction frame: when every factor of a deterministic call takes the
+  // compact-kernel form, the call runs on psi~ = K(-t) psi and applies the
+  // kinetic factors once, at its end (with Lambda, the product of the
+  // factors' scalar parts).
+  bool ip = !stoch && c->d == 1 && (scheme == LS_LIE || scheme == LS_STRANG || scheme == LS_STRANG_KP) &&
+            !getenv_flag("LSPLIT_NO_IP");
+  for (size_t i = 0; i < ps.size() && ip; ++i) ip = !ps[i].fused && stencil_table(c, ps[i].layer, ps[i].s).B > 0;
+  int64_t t_acc = 0;
+  std::complex<double> lam(1.0, 0.0);
   for (size_t i = 0; i < ps.size(); ++i) {
     const PassSpec& q = ps[i];
     const int L = q.layer - 1;
@@ -1072,7 +1097,23 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
     const int32_t p = std::max<int32_t>(1, (int32_t)(S / c->frac_den));
     if (q.unit != 0) set_kinetic(c, q.unit);
     lsk::PassArgs a = base_args(c, L, psi);
-    if (!stoch) {
+    if (ip) {
+      a.mode = lsk::MODE_STEP;
+      a.T = phase_table(c, q.layer, q.s);
+      const CachedTab stt = stencil_table(c, q.layer, q.s);
+      a.taps = stt.ipbuf->p;
+      a.sB = stt.B;
+      a.ip = 1;
+      t_acc += q.pre;
+      a.ip_t = t_acc;
+      t_acc += q.post;
+      lam *= stt.diag;
+      if (i + 1 == ps.size()) {
+        a.units_post = t_acc;
+        lambda_parts(lam, a.lam_turns, a.lam_def);
+      }
+      LS_CUDA(launch(c, a, L, S, st));
+    } else if (!stoch) {
       a.mode = lsk::MODE_STEP;
       a.T = phase_table(c, q.layer, q.s);
       const CachedTab stt = q.fused ? CachedTab() : stencil_table(c, q.layer, q.s);
@@ -1892,6 +1933,27 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
         all_compact = b->Si1[L][i] > 0 && stencil_table(c, ps[q].layer, sdur).B > 0;
       }
     const int kind = all_compact ? 1 : 0;
+    // deterministic calls of the compact-only kernel run in the interaction
+    // frame (kinetic factors folded into the taps, applied once at the end)
+    const bool ip = kind == 1 && !stoch && (scheme == LS_LIE || scheme == LS_STRANG || scheme == LS_STRANG_KP) &&
+                    !getenv_flag("LSPLIT_NO_IP");
+    std::vector<std::complex<double>> lam(ninst, std::complex<double>(1.0, 0.0));
+    int32_t ip_step = 0;
+    if (ip) {
+      ba.ip = 1;
+      int32_t acc = 0;
+      for (int q = 0; q < npass; ++q) {
+        acc += ba.units[0][q][0];
+        ba.ip_off[q] = acc;
+        acc += ba.units[0][q][1];
+      }
+      ip_step = scheme == LS_STRANG ? 8 : scheme == LS_STRANG_KP ? 2 : 1;
+      ba.ip_step = ip_step;
+      const int32_t T = (int32_t)(ip_step * n);
+      std::memset(ba.units, 0, sizeof(ba.units));
+      ba.units[2][npass - 1][1] = T;
+      ba.units[3][npass - 1][1] = T;
+    }
     int32_t* touch = static_cast<int32_t*>(b->touch.p);
     for (int q = 0; q < npass; ++q) {
       const int layer = ps[q].layer, L = layer - 1;
@@ -1918,6 +1980,11 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
           a.strided = L == 1 ? 1 : 0;
           a.fast_logn = 0;
           if (kind == 1) a.subtiles = b->subtiles1;
+          if (ip) {
+            a.taps = stt.ipbuf->p;
+            a.ip = 1;
+            lam[i] *= stt.diag;
+          }
         }
         // slices per work item (a compact-only item may cover several tiles)
         const int64_t wi = (int64_t)a.W * (a.subtiles > 1 ? a.subtiles : 1);
@@ -1960,6 +2027,12 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
       ba.pass_items[q] = acc;
       ba.step_items += acc;
     }
+    if (ip)
+      for (int i = 0; i < ninst; ++i) {
+        lam[i] = std::pow(lam[i], (double)n);   // every factor of the call
+        lsk::PassArgs& a = args[(size_t)(npass - 1) * ninst + i];
+        lambda_parts(lam[i], a.lam_turns, a.lam_def);
+      }
     if (stoch) {
       int64_t acc = 0;
       for (int i = 0; i < ninst; ++i) {
@@ -1992,6 +2065,19 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
           a.units_post = post;
           return a;
         };
+        if (ip) {
+          // interaction frame: no kinetic factor but Lambda K(8n) after the last
+          fa[(size_t)0 * ninst + i] = with(l1, 0, 0);
+          fa[(size_t)1 * ninst + i] = with(l2, 0, 0);
+          fa[(size_t)2 * ninst + i] = with(l1, 0, 0);
+          lsk::PassArgs last = with(l1, 0, 8 * n);
+          lambda_parts(lam[i], last.lam_turns, last.lam_def);
+          fa[(size_t)3 * ninst + i] = last;
+          fa[(size_t)4 * ninst + i] = with(l1, 0, 0);
+          t1[i] = cum[(size_t)0 * (ninst + 1) + i + 1] - cum[(size_t)0 * (ninst + 1) + i];
+          t2[i] = cum[(size_t)1 * (ninst + 1) + i + 1] - cum[(size_t)1 * (ninst + 1) + i];
+          continue;
+        }
         fa[(size_t)0 * ninst + i] = with(l1, 1, 3);
         fa[(size_t)1 * ninst + i] = with(l2, 0, 3);
         lsk::PassArgs f = with(l1, 0, 2);
@@ -2009,6 +2095,13 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
         t2[i] = cum[(size_t)1 * (ninst + 1) + i + 1] - cum[(size_t)1 * (ninst + 1) + i];
       }
       args.swap(fa);
+      if (ip) {
+        ba.ip_off[0] = 1;
+        ba.ip_off[1] = 4;
+        ba.ip_off[2] = 7;
+        ba.ip_off[3] = 7;
+        ba.ip_off[4] = 9;
+      }
     }
     e->args = std::make_shared<DevBuf>();
     const size_t b_args = args.size() * sizeof(lsk::PassArgs), b_cum = cum.size() * sizeof(int64_t);

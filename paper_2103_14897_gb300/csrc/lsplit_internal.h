@@ -86,6 +86,18 @@ struct PassArgs {
   const void* taps;
   int32_t sB;
   int32_t subtiles;        // batched compact-only kernel: consecutive tiles per work item (0 or 1: one)
+  // Interaction frame of a call (MODE_STEP, compact-kernel form, ip = 1): the
+  // state is psi~ = K(-t) psi with t the kinetic units applied so far in the
+  // call, so P acts as K(-t) P K(t): taps c_d e^{-2 pi i t A d^2} times
+  // w_m^d, w_m = e^{2 pi i t (2 A m + l)}; taps holds c'_d / (1 + c'_0) with a
+  // zero centre (the scalar 1 + c'_0 of every factor is collected in Lambda).
+  // units_pre is 0; units_post, nonzero only in a call's last pass, is the
+  // call's total kinetic time T, applied with Lambda: psi = Lambda K(T) psi~.
+  int64_t ip_t;            // t: kinetic units before this factor, from the start of the call
+  uint64_t lam_turns;      // arg(Lambda) in 2^-64 turns
+  double lam_def;          // 1 - |Lambda|
+  int32_t ip;              // 1: interaction frame
+  int32_t pad_ip;
 };
 
 constexpr int kStencilMaxB = 8;       // widest compact kernel (17 taps)
@@ -195,6 +207,12 @@ struct BatchArgs {
   int32_t fused;
   const int64_t* tiles1;        // [ninst] layer-1 tiles of instance i
   const int64_t* tiles2;        // [ninst] layer-2 tiles of instance i
+  // interaction frame (compact-only kernel, deterministic schemes): the factor
+  // of an item of step k acts at t = k ip_step + ip_off[pass] kinetic units
+  // (fused walk: ip_off[kind], ip_off[4] for the second factor of a fused item)
+  int32_t ip;
+  int32_t ip_step;
+  int32_t ip_off[5];
 };
 
 // Slice samples of a batch: block b draws instance i = b / (nsteps * npf),

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lsplit_internal.h"
 
 namespace lsk {
@@ -1721,9 +1723,24 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <typename Real, int MODE, bool CG, int BV>
+// exp(2 pi i t / 2^64) to about 5e-7 absolute: the top 32 bits of t as a
+// float angle and the hardware sine and cosine.  Used only for factors that
+// multiply the small correction term of the interaction frame (taps of size
+// about s |v|), where this error is scaled far below the working precision.
+__device__ __forceinline__ float2 cis_fast(uint64_t t) {
+  const int32_t h = (int32_t)(uint32_t)(t >> 32);
+  float sn, cs;
+  __sincosf((float)h * 1.46291807926715968e-09f, &sn, &cs);   // 2 pi / 2^32
+  return make_float2(cs, sn);
+}
+template <typename Real> __device__ __forceinline__ typename CT<Real>::C cis_corr(uint64_t t);
+template <> __device__ __forceinline__ float2 cis_corr<float>(uint64_t t) { return cis_fast(t); }
+template <> __device__ __forceinline__ double2 cis_corr<double>(uint64_t t) { return phase_of<double>(t).v; }
+
+template <typename Real, int MODE, bool CG, int BV, bool IP = false>
 __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   using C = typename CT<Real>::C;
+  static_assert(!IP || MODE == MODE_STEP, "the interaction frame is a deterministic-step form");
   constexpr bool lazy = (MODE == MODE_LAZY);
   constexpr int NTAP = 2 * BV + 1;
   constexpr int H = stencil_halo(BV);
@@ -1766,7 +1783,7 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   // accumulators combined at the end
   constexpr bool PACK = sizeof(Real) == 4 && BV <= 3;
   C t[NTAP];
-  {
+  if constexpr (!IP) {
     const C* tp = reinterpret_cast<const C*>(a.taps);
 #pragma unroll
     for (int k = 0; k < NTAP; ++k) t[k] = tp[k];
@@ -1839,7 +1856,8 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
     }
   };
   // ---- kinetic pre-phase (first pass of a call) or the pending lazy phase
-  if (lazy || a.units_pre != 0) {
+  // (none in the interaction frame: psi~ = psi at the start of a call)
+  if (!IP && (lazy || a.units_pre != 0)) {
     for (int u = u0; u < nunit; u += ud) {
       int w, ei0, i1;
       unit(u, w, ei0, i1);
@@ -1865,15 +1883,118 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
     }
     __syncthreads();
   }
-  // ---- wrap halos: i in [-BV, 0) takes x_{i + q}, i in [q, q + BV) takes x_{i - q}
+  // ---- wrap halos: i in [-BV, 0) takes x_{i + q}, i in [q, q + BV) takes x_{i - q}.
+  // In the interaction frame a wrapped neighbour j' = j mod q is stored as
+  // x~_{j'} e^{2 pi i t (kappa(j) - kappa(j'))}, so that the taps' phases,
+  // written for the unwrapped index j, hold at the slice ends too.
   for (int e = tid; e < W * 2 * BV; e += NT) {
     const int w = e / (2 * BV), k = e - w * (2 * BV);
     const int dst = k < BV ? k - BV : q + (k - BV);
     const int src = k < BV ? q - BV + k : k - BV;
-    if (strided) sm[(dst + H) * W + w] = sm[(src + H) * W + w];
-    else sm[w * Ls + H + dst] = sm[w * Ls + H + src];
+    C v = strided ? sm[(src + H) * W + w] : sm[w * Ls + H + src];
+    if constexpr (IP) {
+      const int64_t mj = (int64_t)g.lo_a + dst, mk = (int64_t)g.lo_a + src;
+      const uint64_t turns =
+          (uint64_t)a.ip_t * ((uint64_t)(mj - mk) * (g.A_aa * (uint64_t)(mj + mk) + s_la[w]));
+      v = cmul(v, cis_corr<Real>(turns));
+    }
+    if (strided) sm[(dst + H) * W + w] = v;
+    else sm[w * Ls + H + dst] = v;
   }
   __syncthreads();
+  // ---- interaction frame: y = x + sum_{d != 0} c_d e^{-2 pi i t A d^2} w^d x_{i-d},
+  // w = e^{2 pi i t (2 A m + l)} per element; the pairs d, -d combine as
+  // w^d u + conj(w)^d v = cos(d a) (u + v) + i sin(d a) (u - v); the call's last
+  // pass applies Lambda K(T) with the error-free product
+  if constexpr (IP) {
+    const uint64_t tu = (uint64_t)a.ip_t;
+    const C* tp = reinterpret_cast<const C*>(a.taps);
+    C tf[NTAP];
+#pragma unroll
+    for (int d = 1; d <= BV; ++d) {
+      const C e = cis_corr<Real>((uint64_t)0 - tu * g.A_aa * (uint64_t)(d * d));
+      tf[BV + d] = cmul(tp[BV + d], e);
+      tf[BV - d] = cmul(tp[BV - d], e);
+    }
+    auto sweep = [&](auto post_c) {
+      constexpr bool POST = decltype(post_c)::value;
+      for (int u = u0; u < nunit; u += ud) {
+        int w, ei0, i1;
+        unit(u, w, ei0, i1);
+        const int64_t sl = s_slice[w];
+        if (sl < 0) continue;
+        const uint64_t twoA = 2 * g.A_aa;
+        uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(g.lo_a + ei0) + s_la[w]);
+        const uint64_t dphi = tu * twoA * (uint64_t)eid;
+        KinWalk kw;
+        if constexpr (POST) {
+          kw.init(g.A_aa, s_la[w], s_c0[w], g.lo_a + ei0, eid);
+          kw.scale((uint64_t)0 - (uint64_t)a.units_post);
+          kw.q += a.lam_turns;
+        }
+        const C* sp = sm + (strided ? (ei0 + H) * W + w : w * Ls + H + ei0);
+        C* gp = psi + sl * g.slice_stride + (int64_t)ei0 * g.ea;
+        const int64_t gstep = (int64_t)eid * g.ea;
+        for (int i = ei0; i < i1; i += eid) {
+          const C om = cis_corr<Real>(phi);
+          phi += dphi;
+          C od = om;
+          C S1 = czero<C>(), S2 = czero<C>();
+#pragma unroll
+          for (int d = 1; d <= BV; ++d) {
+            const C x1 = sp[-d * sstep], x2 = sp[d * sstep];
+            const C t1 = tf[BV + d], t2 = tf[BV - d];
+            C pa, pb, qa, qb;
+            if constexpr (sizeof(Real) == 4) {
+              const float2 p1 = __fmul2_rn(x1, make_float2(t1.x, t1.x));
+              pa = __ffma2_rn(x2, make_float2(t2.x, t2.x), p1);
+              pb = __ffma2_rn(x2, make_float2(-t2.x, -t2.x), p1);
+              const float2 q1 = __fmul2_rn(x1, make_float2(t1.y, t1.y));
+              qa = __ffma2_rn(x2, make_float2(t2.y, t2.y), q1);
+              qb = __ffma2_rn(x2, make_float2(-t2.y, -t2.y), q1);
+              S1 = __ffma2_rn(pa, make_float2(od.x, od.x), S1);
+              S1 = __ffma2_rn(qb, make_float2(-od.y, -od.y), S1);
+              S2 = __ffma2_rn(qa, make_float2(od.x, od.x), S2);
+              S2 = __ffma2_rn(pb, make_float2(od.y, od.y), S2);
+            } else {
+              pa.x = fma(x2.x, t2.x, x1.x * t1.x);
+              pa.y = fma(x2.y, t2.x, x1.y * t1.x);
+              pb.x = fma(x2.x, -t2.x, x1.x * t1.x);
+              pb.y = fma(x2.y, -t2.x, x1.y * t1.x);
+              qa.x = fma(x2.x, t2.y, x1.x * t1.y);
+              qa.y = fma(x2.y, t2.y, x1.y * t1.y);
+              qb.x = fma(x2.x, -t2.y, x1.x * t1.y);
+              qb.y = fma(x2.y, -t2.y, x1.y * t1.y);
+              S1.x = fma(od.x, pa.x, fma(-od.y, qb.x, S1.x));
+              S1.y = fma(od.x, pa.y, fma(-od.y, qb.y, S1.y));
+              S2.x = fma(od.x, qa.x, fma(od.y, pb.x, S2.x));
+              S2.y = fma(od.x, qa.y, fma(od.y, pb.y, S2.y));
+            }
+            if (d < BV) od = cmul(od, om);
+          }
+          C y = sp[0];
+          y.x += S1.x - S2.y;
+          y.y += S1.y + S2.x;
+          if constexpr (POST) {
+            Phase<Real> ph = phase_of<Real>(kw.q);
+            if constexpr (sizeof(Real) == 4) {
+              ph.half_e += (Real)a.lam_def;
+            } else {
+              ph.v.x *= 1.0 - a.lam_def;
+              ph.v.y *= 1.0 - a.lam_def;
+            }
+            y = apply_phase<Real>(y, ph);
+            kw.next();
+          }
+          *gp = y;
+          sp += eid * sstep;
+          gp += gstep;
+        }
+      }
+    };
+    if (a.units_post != 0) sweep(std::integral_constant<bool, true>());
+    else sweep(std::integral_constant<bool, false>());
+  } else
   // ---- y = x + sum_d c'_d x_{i-d}, post-phase, store
   {
     const bool post = !lazy && a.units_post != 0;
@@ -1922,11 +2043,11 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
 }
 
-template <typename Real, int MODE, int BV>
+template <typename Real, int MODE, int BV, bool IP = false>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(Real) == 4 ? 3 : 2)
 pass_stencil_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  stencil_tile<Real, MODE, false, BV>(a, (int64_t)blockIdx.x, smraw);
+  stencil_tile<Real, MODE, false, BV, IP>(a, (int64_t)blockIdx.x, smraw);
 }
 
 template <typename Real> size_t stencil_smem_bytes(const LayerGeom& g, int W, int B) {
@@ -1938,6 +2059,7 @@ template <typename Real, int BV>
 static cudaError_t launch_stencil_b(const PassArgs& a, int64_t ntiles, cudaStream_t st) {
   const size_t smem = stencil_smem_bytes<Real>(a.g, a.W, BV);
   if (a.mode == MODE_LAZY) pass_stencil_kernel<Real, MODE_LAZY, BV><<<(unsigned)ntiles, kStencilThreads, smem, st>>>(a);
+  else if (a.ip) pass_stencil_kernel<Real, MODE_STEP, BV, true><<<(unsigned)ntiles, kStencilThreads, smem, st>>>(a);
   else pass_stencil_kernel<Real, MODE_STEP, BV><<<(unsigned)ntiles, kStencilThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -1961,6 +2083,7 @@ template <typename Real> cudaError_t stencil_prepare(size_t max_smem) {
   cudaError_t e = cudaSuccess;
 #define LS_SPREP(BV)                                                                                   \
   if (e == cudaSuccess) e = allow_smem(pass_stencil_kernel<Real, MODE_STEP, BV>, max_smem);           \
+  if (e == cudaSuccess) e = allow_smem(pass_stencil_kernel<Real, MODE_STEP, BV, true>, max_smem);     \
   if (e == cudaSuccess) e = allow_smem(pass_stencil_kernel<Real, MODE_LAZY, BV>, max_smem);
   LS_SPREP(2) LS_SPREP(3) LS_SPREP(5) LS_SPREP(8)
 #undef LS_SPREP
@@ -1989,6 +2112,11 @@ __device__ __noinline__ void batch_stencil_tile_n(const PassArgs& a, int64_t til
 }
 
 // Compact-kernel tile of a batched work item (sB > 0); false: not this form.
+template <typename Real, int MODE, int BV, bool IP>
+__device__ __noinline__ void stencil_tile_call(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  stencil_tile<Real, MODE, true, BV, IP>(a, tile, smraw);
+}
+
 template <typename Real, int MODE>
 __device__ __forceinline__ bool batch_stencil_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   switch (a.sB) {
@@ -2036,11 +2164,15 @@ __device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsi
     for (int k = 0; k < nsub; ++k) {
       if (k) __syncthreads();
       const int64_t tk = tile * nsub + k;
+      // deterministic steps of the compact-only kernel run in the interaction
+      // frame; the wide kernels (rare: long tails) are calls, so that their
+      // registers do not weigh on the common narrow ones
+      constexpr bool IP = MODE == MODE_STEP;
       switch (a.sB) {
-        case 2: stencil_tile<Real, MODE, true, 2>(a, tk, smraw); break;
-        case 3: stencil_tile<Real, MODE, true, 3>(a, tk, smraw); break;
-        case 5: stencil_tile<Real, MODE, true, 5>(a, tk, smraw); break;
-        default: stencil_tile<Real, MODE, true, 8>(a, tk, smraw); break;
+        case 2: stencil_tile<Real, MODE, true, 2, IP>(a, tk, smraw); break;
+        case 3: stencil_tile<Real, MODE, true, 3, IP>(a, tk, smraw); break;
+        case 5: stencil_tile_call<Real, MODE, 5, IP>(a, tk, smraw); break;
+        default: stencil_tile_call<Real, MODE, 8, IP>(a, tk, smraw); break;
       }
     }
   } else {
@@ -2056,7 +2188,7 @@ batch_kernel(const BatchArgs b) {
   __shared__ PassArgs s_args;
   __shared__ long long s_item;
   __shared__ int s_stop, s_inst, s_pass;
-  __shared__ long long s_tile;
+  __shared__ long long s_tile, s_step;
   // fused Strang: [first L1] then per step [L2, fused L1 (last step: plain L1)]
   const long long steps_total = b.fused ? b.pass_items[0] + (long long)b.nsteps * (b.pass_items[0] + b.pass_items[1])
                                         : b.step_items * (long long)b.nsteps;
@@ -2116,13 +2248,16 @@ batch_kernel(const BatchArgs b) {
           s_pass = 0;
           s_tile = r - b.settle_cum[i];
           need = (unsigned long long)((long long)b.nsteps * b.tiles_step[i]);
+          s_step = 0;
         } else if (b.fused) {
           const long long I1 = s_pass_items[0], I2 = s_pass_items[1];
           long long r = s_item, nl1 = 0, nl2 = 0;
           int kind = 0, layer = 0;
+          s_step = 0;
           if (r >= I1) {
             r -= I1;
             const long long k = r / (I1 + I2);
+            s_step = k;
             r -= k * (I1 + I2);
             if (r < I2) {
               kind = 1;
@@ -2150,6 +2285,7 @@ batch_kernel(const BatchArgs b) {
           if (b.unmet && i == 0 && kind == 1 && nl2 == 0) need += 1;  // test hook
         } else {
           const long long k = s_item / b.step_items;
+          s_step = k;
           long long r = s_item - k * b.step_items;
           int p = 0;
           while (p + 1 < b.npass && r >= s_pass_items[p]) {
@@ -2210,6 +2346,7 @@ batch_kernel(const BatchArgs b) {
           s_args.units_post = s_units[var][p][1];
         }
       }
+      if (threadIdx.x == 0 && b.ip && !s_settle) s_args.ip_t = s_step * b.ip_step + b.ip_off[p];
       __syncthreads();
     }
     if constexpr (STOCH) {
@@ -2225,6 +2362,8 @@ batch_kernel(const BatchArgs b) {
         const int* src = reinterpret_cast<const int*>(b.args + (size_t)4 * b.ninst + s_inst);
         int* dst = reinterpret_cast<int*>(&s_args);
         for (int w = threadIdx.x; w < (int)(sizeof(PassArgs) / 4); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        if (threadIdx.x == 0 && b.ip) s_args.ip_t = s_step * b.ip_step + b.ip_off[4];
         __syncthreads();
         batch_tile<Real, BPT, MODE_STEP, KIND>(s_args, s_tile, smraw);
       }
