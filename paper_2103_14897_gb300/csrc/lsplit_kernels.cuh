@@ -1737,6 +1737,48 @@ template <typename Real> __device__ __forceinline__ typename CT<Real>::C cis_cor
 template <> __device__ __forceinline__ float2 cis_corr<float>(uint64_t t) { return cis_fast(t); }
 template <> __device__ __forceinline__ double2 cis_corr<double>(uint64_t t) { return phase_of<double>(t).v; }
 
+// Interaction-frame correction of one complex64 element,
+//   sum_{d=1..BV} [w^d t_d x_{m-d} + conj(w)^d t_{-d} x_{m+d}],  w = (c, s),
+// in paired FP32 operations on broadcast pairs of the tap factors:
+// with pa = x1 t1.x + x2 t2.x, pb = x1 t1.x - x2 t2.x, qa = x1 t1.y + x2 t2.y,
+// qb = x1 t1.y - x2 t2.y, the pair contributes (S1, S2) += (c_d pa - s_d qb,
+// c_d qa + s_d pb) and the sum is S1 + i S2.  cos 2a = 2 c^2 - 1 and
+// sin 2a = 2 c s give the second power; higher powers by products.
+template <int BV> struct IpTaps {
+  float2 t1x[BV], t1y[BV], nt1y[BV], t2x[BV], nt2x[BV], t2y[BV];
+};
+template <int BV>
+__device__ __forceinline__ float2 ip_corr_f(const float2* sp, int sstep, const IpTaps<BV>& T, float c, float s) {
+  float2 Cd = make_float2(c, c), Sd = make_float2(s, s);
+  float2 Sa = make_float2(0.f, 0.f), Sb = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int d = 1; d <= BV; ++d) {
+    const float2 x1 = sp[-d * sstep], x2 = sp[d * sstep];
+    const float2 p1 = __fmul2_rn(x1, T.t1x[d - 1]);
+    const float2 pa = __ffma2_rn(x2, T.t2x[d - 1], p1);
+    const float2 pb = __ffma2_rn(x2, T.nt2x[d - 1], p1);
+    const float2 q2 = __fmul2_rn(x2, T.t2y[d - 1]);
+    const float2 qa = __ffma2_rn(x1, T.t1y[d - 1], q2);
+    const float2 qbn = __ffma2_rn(x1, T.nt1y[d - 1], q2);   // -qb
+    Sa = __ffma2_rn(pa, Cd, Sa);
+    Sa = __ffma2_rn(qbn, Sd, Sa);
+    Sb = __ffma2_rn(qa, Cd, Sb);
+    Sb = __ffma2_rn(pb, Sd, Sb);
+    if (d < BV) {
+      if (d == 1) {
+        const float2 C2 = __fadd2_rn(Cd, Cd);
+        Sd = __fmul2_rn(C2, Sd);
+        Cd = __ffma2_rn(C2, Cd, make_float2(-1.f, -1.f));
+      } else {
+        const float cn = fmaf(Cd.x, c, -Sd.x * s), sn = fmaf(Sd.x, c, Cd.x * s);
+        Cd = make_float2(cn, cn);
+        Sd = make_float2(sn, sn);
+      }
+    }
+  }
+  return make_float2(Sa.x - Sb.y, Sa.y + Sb.x);
+}
+
 template <typename Real, int MODE, bool CG, int BV, bool IP = false>
 __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, unsigned char* smraw) {
   using C = typename CT<Real>::C;
@@ -1783,7 +1825,7 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   // accumulators combined at the end
   constexpr bool PACK = sizeof(Real) == 4 && BV <= 3;
   C t[NTAP];
-  if constexpr (!IP) {
+  {
     const C* tp = reinterpret_cast<const C*>(a.taps);
 #pragma unroll
     for (int k = 0; k < NTAP; ++k) t[k] = tp[k];
@@ -1803,7 +1845,6 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
       C* dst = sm + w * Ls + H;
       for (int j = lane; j < np2; j += 32) cp_async16(dst + PAIR * j, src + (int64_t)PAIR * j);
     }
-    cp_async_wait_all();
   } else if (!a.list) {
     // adjacent columns: one copy moves PAIR columns of a row; tiles start at a
     // multiple of W columns and never read past the row pitch
@@ -1814,7 +1855,6 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
       const int i = e >> wsh, k = e & (wp - 1);
       cp_async16(sm + (i + H) * W + PAIR * k, psi + s0 + (int64_t)i * g.ea + PAIR * k);
     }
-    cp_async_wait_all();
   } else {
     // sampled (scattered) columns: plain loads, the column fixed per thread
     const int wsh = 31 - __clz(W);
@@ -1827,6 +1867,19 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
       sm[(i + H) * W + w] = x;
     }
   }
+  // interaction frame: the tap factors c_d e^{-2 pi i t A d^2}, formed while
+  // the copies are in flight
+  C tf[NTAP];
+  if constexpr (IP) {
+    const uint64_t tu = (uint64_t)a.ip_t;
+#pragma unroll
+    for (int d = 1; d <= BV; ++d) {
+      const C e = cis_corr<Real>((uint64_t)0 - tu * g.A_aa * (uint64_t)(d * d));
+      tf[BV + d] = cmul(t[BV + d], e);
+      tf[BV - d] = cmul(t[BV - d], e);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
   // Element ownership in the phase and stencil sweeps.  Contiguous tiles:
   // work units of CH consecutive elements of one slice (unit u: slice u / nch,
@@ -1908,14 +1961,6 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   // pass applies Lambda K(T) with the error-free product
   if constexpr (IP) {
     const uint64_t tu = (uint64_t)a.ip_t;
-    const C* tp = reinterpret_cast<const C*>(a.taps);
-    C tf[NTAP];
-#pragma unroll
-    for (int d = 1; d <= BV; ++d) {
-      const C e = cis_corr<Real>((uint64_t)0 - tu * g.A_aa * (uint64_t)(d * d));
-      tf[BV + d] = cmul(tp[BV + d], e);
-      tf[BV - d] = cmul(tp[BV - d], e);
-    }
     auto sweep = [&](auto post_c) {
       constexpr bool POST = decltype(post_c)::value;
       for (int u = u0; u < nunit; u += ud) {
@@ -1992,8 +2037,84 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
         }
       }
     };
-    if (a.units_post != 0) sweep(std::integral_constant<bool, true>());
-    else sweep(std::integral_constant<bool, false>());
+    if (a.units_post != 0) {
+      sweep(std::integral_constant<bool, true>());
+    } else if constexpr (sizeof(Real) == 4) {
+      // complex64 passes other than a call's last: tap factors as broadcast
+      // pairs; rows as one flat range per warp (balanced across warps, a row
+      // change is a predicated jump of the pointers and the phase), columns
+      // one per thread
+      IpTaps<BV> T;
+#pragma unroll
+      for (int d = 1; d <= BV; ++d) {
+        const C t1 = tf[BV + d], t2 = tf[BV - d];
+        T.t1x[d - 1] = make_float2(t1.x, t1.x);
+        T.t1y[d - 1] = make_float2(t1.y, t1.y);
+        T.nt1y[d - 1] = make_float2(-t1.y, -t1.y);
+        T.t2x[d - 1] = make_float2(t2.x, t2.x);
+        T.nt2x[d - 1] = make_float2(-t2.x, -t2.x);
+        T.t2y[d - 1] = make_float2(t2.y, t2.y);
+      }
+      const uint64_t twoA = 2 * g.A_aa, Xa = g.X_aa;
+      const int lo = g.lo_a;
+      const int64_t s0 = tile * (int64_t)W, sstr = g.slice_stride, ea = g.ea;
+      const int64_t olo = g.olo_a;
+      const int Wv = (int)min((int64_t)W, g.nslices - s0);
+      float2* pg = reinterpret_cast<float2*>(psi);
+      const float2* smf = reinterpret_cast<const float2*>(sm);
+      if (!strided && q >= 32) {
+        const int total = Wv * q;
+        const int per = ((total + nwarp * 32 - 1) / (nwarp * 32)) * 32;
+        int e = warp * per + lane;
+        const int eend = min(total, (warp + 1) * per);
+        if (e < eend) {
+          int w = e / q, i = e - w * q;
+          const float2* sp = smf + w * Ls + H + i;
+          float2* gp = pg + (s0 + w) * sstr + i;
+          uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
+          const uint64_t dphi = tu * twoA * 32u;
+          const uint64_t dphix = tu * (Xa - twoA * (uint64_t)q);
+          const int jsm = Ls - q;
+          const int64_t jg = sstr - q;
+          for (; e < eend; e += 32) {
+            const float2 cs = cis_fast(phi);
+            const float2 corr = ip_corr_f<BV>(sp, 1, T, cs.x, cs.y);
+            const float2 x0 = sp[0];
+            __stcg(gp, make_float2(x0.x + corr.x, x0.y + corr.y));
+            i += 32;
+            const bool cr = i >= q;
+            i = cr ? i - q : i;
+            sp += cr ? 32 + jsm : 32;
+            gp += cr ? 32 + jg : 32;
+            phi += cr ? dphi + dphix : dphi;
+          }
+        }
+      } else if (!strided) {
+        sweep(std::integral_constant<bool, false>());
+      } else {
+        const int w = tid & (W - 1);
+        if (w < Wv) {
+          int i = tid >> wsh;
+          const float2* sp = smf + (i + H) * W + w;
+          float2* gp = pg + (s0 + w) + (int64_t)i * ea;
+          uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
+          const uint64_t dphi = tu * twoA * (uint64_t)eid;
+          const int dsp = eid * W;
+          const int64_t dg = (int64_t)eid * ea;
+          for (; i < q; i += eid) {
+            const float2 cs = cis_fast(phi);
+            const float2 corr = ip_corr_f<BV>(sp, W, T, cs.x, cs.y);
+            const float2 x0 = sp[0];
+            __stcg(gp, make_float2(x0.x + corr.x, x0.y + corr.y));
+            sp += dsp;
+            gp += dg;
+            phi += dphi;
+          }
+        }
+      }
+    } else {
+      sweep(std::integral_constant<bool, false>());
+    }
   } else
   // ---- y = x + sum_d c'_d x_{i-d}, post-phase, store
   {
@@ -2164,6 +2285,7 @@ __device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsi
     for (int k = 0; k < nsub; ++k) {
       if (k) __syncthreads();
       const int64_t tk = tile * nsub + k;
+
       // deterministic steps of the compact-only kernel run in the interaction
       // frame; the wide kernels (rare: long tails) are calls, so that their
       // registers do not weigh on the common narrow ones
