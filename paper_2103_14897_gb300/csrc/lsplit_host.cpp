@@ -1085,8 +1085,8 @@ void enqueue_step(ls_ctx* c, void* psi, int64_t n, double tau, int scheme, cudaS
   // compact-kernel form, the call runs on psi~ = K(-t) psi and applies the
   // kinetic factors once, at its end (with Lambda, the product of the
   // factors' scalar parts).
-  bool ip = !stoch && c->d == 1 && (scheme == LS_LIE || scheme == LS_STRANG || scheme == LS_STRANG_KP) &&
-            !getenv_flag("LSPLIT_NO_IP");
+  bool ip = !stoch && c->d == 1 && c->dtype == LS_C64 &&
+            (scheme == LS_LIE || scheme == LS_STRANG || scheme == LS_STRANG_KP) && !getenv_flag("LSPLIT_NO_IP");
   for (size_t i = 0; i < ps.size() && ip; ++i) ip = !ps[i].fused && stencil_table(c, ps[i].layer, ps[i].s).B > 0;
   int64_t t_acc = 0;
   std::complex<double> lam(1.0, 0.0);
@@ -1933,10 +1933,11 @@ std::unique_ptr<ls_batch::Cached> build_batch_graph(ls_batch* b, void* psi, int6
         all_compact = b->Si1[L][i] > 0 && stencil_table(c, ps[q].layer, sdur).B > 0;
       }
     const int kind = all_compact ? 1 : 0;
-    // deterministic calls of the compact-only kernel run in the interaction
-    // frame (kinetic factors folded into the taps, applied once at the end)
-    const bool ip = kind == 1 && !stoch && (scheme == LS_LIE || scheme == LS_STRANG || scheme == LS_STRANG_KP) &&
-                    !getenv_flag("LSPLIT_NO_IP");
+    // deterministic complex64 calls of the compact-only kernel run in the
+    // interaction frame (kinetic factors folded into the taps, applied once at
+    // the end): that kernel's deterministic tile body is this form
+    const bool ip = kind == 1 && !stoch && b->dtype == LS_C64 &&
+                    (scheme == LS_LIE || scheme == LS_STRANG || scheme == LS_STRANG_KP);
     std::vector<std::complex<double>> lam(ninst, std::complex<double>(1.0, 0.0));
     int32_t ip_step = 0;
     if (ip) {

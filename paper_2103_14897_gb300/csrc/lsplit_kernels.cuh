@@ -1721,6 +1721,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16_raw(unsigned sa, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // exp(2 pi i t / 2^64) to about 5e-7 absolute: the top 32 bits of t as a
@@ -1841,20 +1844,28 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
     for (int w = warp; w < W; w += nwarp) {
       const int64_t sl = s_slice[w];
       if (sl < 0) continue;
-      const C* src = psi + sl * g.slice_stride;
-      C* dst = sm + w * Ls + H;
-      for (int j = lane; j < np2; j += 32) cp_async16(dst + PAIR * j, src + (int64_t)PAIR * j);
+      // lane j copies bytes [16 j, 16 j + 16) of each 512-byte run
+      unsigned sa = (unsigned)__cvta_generic_to_shared(sm + w * Ls + H) + 16u * lane;
+      const char* ga = reinterpret_cast<const char*>(psi + sl * g.slice_stride) + 16 * lane;
+#pragma unroll 4
+      for (int j = lane; j < np2; j += 32, sa += 512u, ga += 512) cp_async16_raw(sa, ga);
     }
   } else if (!a.list) {
     // adjacent columns: one copy moves PAIR columns of a row; tiles start at a
     // multiple of W columns and never read past the row pitch
+    // (NT is a multiple of wp, so each thread keeps its copy column k and
+    // steps NT / wp rows)
     const int wp = W / PAIR;
     const int wsh = 31 - __clz(wp);
     const int64_t s0 = tile * (int64_t)W;
-    for (int e = tid; e < q * wp; e += NT) {
-      const int i = e >> wsh, k = e & (wp - 1);
-      cp_async16(sm + (i + H) * W + PAIR * k, psi + s0 + (int64_t)i * g.ea + PAIR * k);
-    }
+    const int k = tid & (wp - 1), di = NT >> wsh;
+    int i = tid >> wsh;
+    unsigned sa = (unsigned)__cvta_generic_to_shared(sm + (i + H) * W + PAIR * k);
+    const char* ga = reinterpret_cast<const char*>(psi + s0 + (int64_t)i * g.ea + PAIR * k);
+    const unsigned dsa = (unsigned)(di * W * (int)sizeof(C));
+    const int64_t dga = (int64_t)di * g.ea * (int64_t)sizeof(C);
+#pragma unroll 4
+    for (; i < q; i += di, sa += dsa, ga += dga) cp_async16_raw(sa, ga);
   } else {
     // sampled (scattered) columns: plain loads, the column fixed per thread
     const int wsh = 31 - __clz(W);
@@ -2286,10 +2297,12 @@ __device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsi
       if (k) __syncthreads();
       const int64_t tk = tile * nsub + k;
 
-      // deterministic steps of the compact-only kernel run in the interaction
-      // frame; the wide kernels (rare: long tails) are calls, so that their
-      // registers do not weigh on the common narrow ones
-      constexpr bool IP = MODE == MODE_STEP;
+      // deterministic complex64 steps of the compact-only kernel run in the
+      // interaction frame (complex128 keeps the exact per-pass phases: its
+      // phase evaluation costs the same either way); the wide kernels (rare:
+      // long tails) are calls, so that their registers do not weigh on the
+      // common narrow ones
+      constexpr bool IP = MODE == MODE_STEP && sizeof(Real) == 4;
       switch (a.sB) {
         case 2: stencil_tile<Real, MODE, true, 2, IP>(a, tk, smraw); break;
         case 3: stencil_tile<Real, MODE, true, 3, IP>(a, tk, smraw); break;

@@ -427,6 +427,36 @@ def test_long_run_1000_steps_long_slices(P, form, monkeypatch):
         O.use_fft(False)
 
 
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp"])
+def test_interaction_frame_matches_physical_frame(P, scheme, monkeypatch):
+    """Deterministic complex64 calls whose factors all take the compact-kernel
+    form run in the interaction frame (kinetic factors folded into the taps,
+    applied once at the call's end); LSPLIT_NO_IP=1 applies them per pass.
+    Same operator: both agree with each other to rounding and with the oracle,
+    on odd, even and 2049-long slices (wrapped neighbours at both ends), for
+    one call of 1 and of 7 steps."""
+    O.use_fft(True)
+    try:
+        for p in problems_1d()[1:] + long_slice_boxes():
+            x = W.random_state((p.M2, p.M1), 27)
+            for n, tau in [(1, 1e-3), (7, 5e-4)]:
+                got = {}
+                for frame in ("interaction", "physical"):
+                    if frame == "physical":
+                        monkeypatch.setenv("LSPLIT_NO_IP", "1")
+                    else:
+                        monkeypatch.delenv("LSPLIT_NO_IP", raising=False)
+                    ctx = P.Context(p, "c64")
+                    psi = ctx.from_dense(x)
+                    ctx.step(psi, n, tau, scheme)
+                    got[frame] = ctx.to_dense(psi)
+                ref = O.step(p, x, tau, scheme, n)
+                assert rel(got["interaction"], got["physical"]) < 2e-6, (p.name, n)
+                assert rel(got["interaction"], ref) < TOL1["c64"] * (1 if n == 1 else 3), (p.name, n)
+    finally:
+        O.use_fft(False)
+
+
 def test_project_each_step_mode(P):
     """mask_mode "project": every step ends with the projection onto the joint
     cutoff of Sec. 3 (the oracle's project=True); members keep the scheme's
