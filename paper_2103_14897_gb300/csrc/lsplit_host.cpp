@@ -693,6 +693,16 @@ bool getenv_flag(const char* name) {
 // 0: the layer has no compact-kernel pass (2D slices, or LSPLIT_NO_STENCIL).
 constexpr size_t kStencilTileBytes = 68 * 1024;
 constexpr size_t kStencilTileBytes4 = 48 * 1024;
+// Tile budget of the compact-only kernel for a given number of CTAs per SM
+// (next to the kernel's static shared memory and the per-CTA reserve).
+size_t compact_budget(int ctas_per_sm) {
+  switch (ctas_per_sm) {
+    case 3: return kStencilTileBytes;
+    case 4: return kStencilTileBytes4;
+    case 6: return 32 * 1024;
+    default: return 22 * 1024;   // 8
+  }
+}
 int stencil_width(const lsk::LayerGeom& g, size_t esize, bool strided, size_t budget = kStencilTileBytes) {
   if (g.d != 1 || g.qa < 7 || getenv_flag("LSPLIT_NO_STENCIL")) return 0;
   const int64_t row = ((int64_t)g.qa + 2 * lsk::kStencilMaxB + 1) & ~(int64_t)1;
@@ -2177,7 +2187,7 @@ void apply_compact_config(ls_batch* b, int nt, int mb, int sub) {
   b->nthreads1 = nt;
   b->minb1 = mb;
   b->subtiles1 = sub;
-  b->budget1 = mb == 3 ? kStencilTileBytes : mb == 4 ? kStencilTileBytes4 : mb == 6 ? 32 * 1024 : 22 * 1024;
+  b->budget1 = compact_budget(mb);
   b->smem1 = 0;
   const size_t es = b->dtype == LS_C64 ? 8 : 16;
   for (int L = 0; L < 2; ++L)
@@ -2346,7 +2356,7 @@ int ls_batch_create(const ls_problem* probs, int32_t count, ls_batch** out) {
       b->nthreads1 = nt;
       b->minb1 = mb;
       b->subtiles1 = sub;
-      b->budget1 = mb == 3 ? kStencilTileBytes : mb == 4 ? kStencilTileBytes4 : mb == 6 ? 32 * 1024 : 22 * 1024;
+      b->budget1 = compact_budget(mb);
     }
     LS_CUDA(cudaGetDevice(&b->device));
     int64_t total = 0;
