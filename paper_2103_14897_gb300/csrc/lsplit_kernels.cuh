@@ -2048,13 +2048,12 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
         }
       }
     };
-    if (a.units_post != 0) {
-      sweep(std::integral_constant<bool, true>());
-    } else if constexpr (sizeof(Real) == 4) {
-      // complex64 passes other than a call's last: tap factors as broadcast
-      // pairs; rows as one flat range per warp (balanced across warps, a row
-      // change is a predicated jump of the pointers and the phase), columns
-      // one per thread
+    const bool post = a.units_post != 0;
+    if constexpr (sizeof(Real) == 4) {
+      // complex64: tap factors as broadcast pairs; rows as one flat range per
+      // warp (balanced across warps, a row change is a predicated jump of the
+      // pointers and the phase), columns one per thread.  The call's last pass
+      // (POST) also applies Lambda K(T) per element with the exact phase.
       IpTaps<BV> T;
 #pragma unroll
       for (int d = 1; d <= BV; ++d) {
@@ -2066,19 +2065,36 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
         T.nt2x[d - 1] = make_float2(-t2.x, -t2.x);
         T.t2y[d - 1] = make_float2(t2.y, t2.y);
       }
-      const uint64_t twoA = 2 * g.A_aa, Xa = g.X_aa;
+      const uint64_t twoA = 2 * g.A_aa, Xa = g.X_aa, A = g.A_aa, Ca = g.C_aa;
       const int lo = g.lo_a;
       const int64_t s0 = tile * (int64_t)W, sstr = g.slice_stride, ea = g.ea;
       const int64_t olo = g.olo_a;
       const int Wv = (int)min((int64_t)W, g.nslices - s0);
+      const uint64_t negT = (uint64_t)0 - (uint64_t)a.units_post;
       float2* pg = reinterpret_cast<float2*>(psi);
       const float2* smf = reinterpret_cast<const float2*>(sm);
-      if (!strided && q >= 32) {
-        const int total = Wv * q;
-        const int per = ((total + nwarp * 32 - 1) / (nwarp * 32)) * 32;
-        int e = warp * per + lane;
-        const int eend = min(total, (warp + 1) * per);
-        if (e < eend) {
+      // the exact Lambda K(T) of the last pass, on a walk of kappa along the element's line
+      auto finish = [&](float2 y, const KinWalk& kw) {
+        Phase<float> ph = phase_of<float>(kw.q);
+        ph.half_e += (float)a.lam_def;
+        return apply_phase<float>(y, ph);
+      };
+      auto walk_at = [&](int w, int i, int step) {
+        KinWalk kw;
+        const uint64_t ua = (uint64_t)(s0 + w + olo);
+        kw.init(A, Xa * ua, Ca * (ua * ua), lo + i, step);
+        kw.scale(negT);
+        kw.q += a.lam_turns;
+        return kw;
+      };
+      auto fast = [&](auto post_c) {
+        constexpr bool POST = decltype(post_c)::value;
+        if (!strided) {
+          const int total = Wv * q;
+          const int per = ((total + nwarp * 32 - 1) / (nwarp * 32)) * 32;
+          int e = warp * per + lane;
+          const int eend = min(total, (warp + 1) * per);
+          if (e >= eend) return;
           int w = e / q, i = e - w * q;
           const float2* sp = smf + w * Ls + H + i;
           float2* gp = pg + (s0 + w) * sstr + i;
@@ -2087,24 +2103,33 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
           const uint64_t dphix = tu * (Xa - twoA * (uint64_t)q);
           const int jsm = Ls - q;
           const int64_t jg = sstr - q;
+          KinWalk kw;
+          if constexpr (POST) kw = walk_at(w, i, 32);
           for (; e < eend; e += 32) {
             const float2 cs = cis_fast(phi);
             const float2 corr = ip_corr_f<BV>(sp, 1, T, cs.x, cs.y);
             const float2 x0 = sp[0];
-            __stcg(gp, make_float2(x0.x + corr.x, x0.y + corr.y));
+            float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
+            if constexpr (POST) y = finish(y, kw);
+            __stcg(gp, y);
             i += 32;
             const bool cr = i >= q;
             i = cr ? i - q : i;
             sp += cr ? 32 + jsm : 32;
             gp += cr ? 32 + jg : 32;
             phi += cr ? dphi + dphix : dphi;
+            if constexpr (POST) {
+              if (cr) {
+                ++w;
+                if (e + 32 < eend) kw = walk_at(w, i, 32);
+              } else {
+                kw.next();
+              }
+            }
           }
-        }
-      } else if (!strided) {
-        sweep(std::integral_constant<bool, false>());
-      } else {
-        const int w = tid & (W - 1);
-        if (w < Wv) {
+        } else {
+          const int w = tid & (W - 1);
+          if (w >= Wv) return;
           int i = tid >> wsh;
           const float2* sp = smf + (i + H) * W + w;
           float2* gp = pg + (s0 + w) + (int64_t)i * ea;
@@ -2112,19 +2137,35 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
           const uint64_t dphi = tu * twoA * (uint64_t)eid;
           const int dsp = eid * W;
           const int64_t dg = (int64_t)eid * ea;
+          KinWalk kw;
+          if constexpr (POST) kw = walk_at(w, i, eid);
           for (; i < q; i += eid) {
             const float2 cs = cis_fast(phi);
             const float2 corr = ip_corr_f<BV>(sp, W, T, cs.x, cs.y);
             const float2 x0 = sp[0];
-            __stcg(gp, make_float2(x0.x + corr.x, x0.y + corr.y));
+            float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
+            if constexpr (POST) {
+              y = finish(y, kw);
+              kw.next();
+            }
+            __stcg(gp, y);
             sp += dsp;
             gp += dg;
             phi += dphi;
           }
         }
+      };
+      if (!strided && q < 32) {
+        if (post) sweep(std::integral_constant<bool, true>());
+        else sweep(std::integral_constant<bool, false>());
+      } else if (post) {
+        fast(std::integral_constant<bool, true>());
+      } else {
+        fast(std::integral_constant<bool, false>());
       }
     } else {
-      sweep(std::integral_constant<bool, false>());
+      if (post) sweep(std::integral_constant<bool, true>());
+      else sweep(std::integral_constant<bool, false>());
     }
   } else
   // ---- y = x + sum_d c'_d x_{i-d}, post-phase, store

@@ -544,6 +544,32 @@ def test_long_run_1000_steps(P):
     assert abs(np.linalg.norm(got) - 1) < 1e-5
 
 
+@pytest.mark.parametrize("calls", [1, 100])
+def test_packet_1000_steps_long_rows(P, calls):
+    """The Gaussian packet on a 2049 x 65 box (seeded U(0.5, 2) amplitudes as
+    the 2049^2 workload): every row holds one dominant element whose
+    neighbours are many orders smaller, the case where rounding in the
+    interaction frame could repeat from pass to pass.  1000 Strang steps of
+    tau = 5e-4 as one call or as 100 calls of 10: rel-L2 <= 1e-4 and
+    | ||psi|| - 1 | <= 1e-5 against the oracle."""
+    base = W.config_scale_1d()
+    p = W.bilayer_1d(1024, 32, base.v1_c[0].real * 2, base.v2_c[0].real * 2, ecut=base.ecut, name="2049x65")
+    O.use_fft(True)
+    try:
+        ctx = P.Context(p, "c64")
+        x = O.gaussian_packet(p, [0.0], 2.0, [1.0])
+        psi = ctx.from_dense(x)
+        for _ in range(calls):
+            ctx.step(psi, 1000 // calls, 5e-4, "strang")
+        ref = O.step(p, x, 5e-4, "strang", 1000)
+        got = ctx.to_dense(psi)
+        print(p.name, calls, "calls: 1000-step rel-L2", rel(got, ref), "norm-1", np.linalg.norm(got) - 1)
+        assert rel(got, ref) < 1e-4
+        assert abs(np.linalg.norm(got) - 1) < 1e-5
+    finally:
+        O.use_fft(False)
+
+
 def test_fast_and_generic_paths_agree(P, monkeypatch):
     """The compact-kernel pass, the register-resident fast pass and the
     generic pass compute the same step (each is also checked against the
