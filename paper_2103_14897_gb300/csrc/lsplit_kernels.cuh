@@ -2216,10 +2216,190 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
   if (lazy && tid < W && s_slice[tid] >= 0) a.touch_own[s_slice[tid]] = a.now;
 }
 
+// Interaction-frame compact tile for complex64 (rows of length >= 32, or
+// columns), with one CTA barrier per tile (after the copies).  Slice indices
+// and kinetic coefficients come from the tile index.  Each warp (rows) or
+// thread (columns) writes the wrapped halo entries it reads itself; another
+// writer of the same entry writes the same value, so no barrier separates the
+// halo from the sweep.  Rows are swept as one balanced flat range per warp (a
+// row change is a predicated jump of the pointers and the phase), columns one
+// per thread; the call's last pass applies Lambda K(T) with the exact phase.
+template <int BV>
+__device__ __forceinline__ void stencil_tile_ipf(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  constexpr int H = stencil_halo(BV);
+  const LayerGeom& g = a.g;
+  const int W = a.W, q = g.qa;
+  const bool strided = a.strided != 0;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = NT >> 5;
+  const int64_t s0 = tile * (int64_t)W;
+  if (s0 >= g.nslices) return;
+  const int Wv = (int)min((int64_t)W, g.nslices - s0);
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int Ls = stencil_row_len(q, BV);
+  float2 t[2 * BV + 1];
+  {
+    const float2* tp = reinterpret_cast<const float2*>(a.taps);
+#pragma unroll
+    for (int k = 0; k <= 2 * BV; ++k) t[k] = tp[k];
+  }
+  float2* pg = reinterpret_cast<float2*>(a.psi);
+  const int64_t sstr = g.slice_stride, ea = g.ea;
+  // ---- copies (16 bytes = two elements each) global -> shared through L2
+  if (!strided) {
+    const int np2 = (q + 1) / 2;
+    for (int w = warp; w < Wv; w += nwarp) {
+      unsigned sa = (unsigned)__cvta_generic_to_shared(sm + w * Ls + H) + 16u * lane;
+      const char* ga = reinterpret_cast<const char*>(pg + (s0 + w) * sstr) + 16 * lane;
+#pragma unroll 4
+      for (int j = lane; j < np2; j += 32, sa += 512u, ga += 512) cp_async16_raw(sa, ga);
+    }
+  } else {
+    const int wp = W / 2;
+    const int wsh = 31 - __clz(wp);
+    const int k = tid & (wp - 1), di = NT >> wsh;
+    int i = tid >> wsh;
+    unsigned sa = (unsigned)__cvta_generic_to_shared(sm + (i + H) * W + 2 * k);
+    const char* ga = reinterpret_cast<const char*>(pg + s0 + (int64_t)i * ea + 2 * k);
+    const unsigned dsa = (unsigned)(di * W * 8);
+    const int64_t dga = (int64_t)di * ea * 8;
+#pragma unroll 4
+    for (; i < q; i += di, sa += dsa, ga += dga) cp_async16_raw(sa, ga);
+  }
+  const uint64_t tu = (uint64_t)a.ip_t, A = g.A_aa, twoA = 2 * g.A_aa, Xa = g.X_aa, Ca = g.C_aa;
+  const int lo = g.lo_a;
+  const int64_t olo = g.olo_a;
+  // tap factors c_d e^{-2 pi i t A d^2} as broadcast pairs, while the copies fly
+  IpTaps<BV> T;
+#pragma unroll
+  for (int d = 1; d <= BV; ++d) {
+    const float2 e = cis_fast((uint64_t)0 - tu * A * (uint64_t)(d * d));
+    const float2 t1 = cmul(t[BV + d], e), t2 = cmul(t[BV - d], e);
+    T.t1x[d - 1] = make_float2(t1.x, t1.x);
+    T.t1y[d - 1] = make_float2(t1.y, t1.y);
+    T.nt1y[d - 1] = make_float2(-t1.y, -t1.y);
+    T.t2x[d - 1] = make_float2(t2.x, t2.x);
+    T.nt2x[d - 1] = make_float2(-t2.x, -t2.x);
+    T.t2y[d - 1] = make_float2(t2.y, t2.y);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // halo entry k of line w: i in [-BV, 0) takes x_{i + q}, i in [q, q + BV)
+  // takes x_{i - q}, times e^{2 pi i t (kappa(i) - kappa(i mod q))}
+  auto fill_halo = [&](int w, int k) {
+    const int dst = k < BV ? k - BV : q + (k - BV);
+    const int src = k < BV ? q - BV + k : k - BV;
+    const int64_t mj = (int64_t)lo + dst, mk = (int64_t)lo + src;
+    const uint64_t la = Xa * (uint64_t)(s0 + w + olo);
+    const float2 f = cis_fast(tu * ((uint64_t)(mj - mk) * (A * (uint64_t)(mj + mk) + la)));
+    if (strided) sm[(dst + H) * W + w] = cmul(sm[(src + H) * W + w], f);
+    else sm[w * Ls + H + dst] = cmul(sm[w * Ls + H + src], f);
+  };
+  const uint64_t negT = (uint64_t)0 - (uint64_t)a.units_post;
+  auto walk_at = [&](int w, int i, int step) {
+    KinWalk kw;
+    const uint64_t ua = (uint64_t)(s0 + w + olo);
+    kw.init(A, Xa * ua, Ca * (ua * ua), lo + i, step);
+    kw.scale(negT);
+    kw.q += a.lam_turns;
+    return kw;
+  };
+  auto finish = [&](float2 y, const KinWalk& kw) {
+    Phase<float> ph = phase_of<float>(kw.q);
+    ph.half_e += (float)a.lam_def;
+    return apply_phase<float>(y, ph);
+  };
+  auto sweep = [&](auto post_c) {
+    constexpr bool POST = decltype(post_c)::value;
+    if (!strided) {
+      const int total = Wv * q;
+      const int per = ((total + nwarp * 32 - 1) / (nwarp * 32)) * 32;
+      int e = warp * per + lane;
+      const int e0 = warp * per, e1 = min(total, (warp + 1) * per);
+      if (e0 >= e1) return;
+      // the halos of every row this warp's range touches
+      const int wa = e0 / q, wb = (e1 - 1) / q;
+      for (int r = lane; r < (wb - wa + 1) * 2 * BV; r += 32) fill_halo(wa + r / (2 * BV), r % (2 * BV));
+      __syncwarp();
+      if (e >= e1) return;
+      int w = e / q, i = e - w * q;
+      const float2* sp = sm + w * Ls + H + i;
+      float2* gp = pg + (s0 + w) * sstr + i;
+      uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
+      const uint64_t dphi = tu * twoA * 32u;
+      const uint64_t dphix = tu * (Xa - twoA * (uint64_t)q);
+      const int jsm = Ls - q;
+      const int64_t jg = sstr - q;
+      KinWalk kw;
+      if constexpr (POST) kw = walk_at(w, i, 32);
+      for (; e < e1; e += 32) {
+        const float2 cs = cis_fast(phi);
+        const float2 corr = ip_corr_f<BV>(sp, 1, T, cs.x, cs.y);
+        const float2 x0 = sp[0];
+        float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
+        if constexpr (POST) y = finish(y, kw);
+        __stcg(gp, y);
+        i += 32;
+        const bool cr = i >= q;
+        i = cr ? i - q : i;
+        sp += cr ? 32 + jsm : 32;
+        gp += cr ? 32 + jg : 32;
+        phi += cr ? dphi + dphix : dphi;
+        if constexpr (POST) {
+          if (cr) {
+            ++w;
+            if (e + 32 < e1) kw = walk_at(w, i, 32);
+          } else {
+            kw.next();
+          }
+        }
+      }
+    } else {
+      const int wsh = 31 - __clz(W);
+      const int w = tid & (W - 1);
+      if (w >= Wv) return;
+#pragma unroll
+      for (int k = 0; k < 2 * BV; ++k) fill_halo(w, k);
+      const int eid = NT >> wsh;
+      int i = tid >> wsh;
+      const float2* sp = sm + (i + H) * W + w;
+      float2* gp = pg + (s0 + w) + (int64_t)i * ea;
+      uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
+      const uint64_t dphi = tu * twoA * (uint64_t)eid;
+      const int dsp = eid * W;
+      const int64_t dg = (int64_t)eid * ea;
+      KinWalk kw;
+      if constexpr (POST) kw = walk_at(w, i, eid);
+      for (; i < q; i += eid) {
+        const float2 cs = cis_fast(phi);
+        const float2 corr = ip_corr_f<BV>(sp, W, T, cs.x, cs.y);
+        const float2 x0 = sp[0];
+        float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
+        if constexpr (POST) {
+          y = finish(y, kw);
+          kw.next();
+        }
+        __stcg(gp, y);
+        sp += dsp;
+        gp += dg;
+        phi += dphi;
+      }
+    }
+  };
+  if (a.units_post != 0) sweep(std::integral_constant<bool, true>());
+  else sweep(std::integral_constant<bool, false>());
+}
+
 template <typename Real, int MODE, int BV, bool IP = false>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(Real) == 4 ? 3 : 2)
 pass_stencil_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  if constexpr (IP && sizeof(Real) == 4 && BV <= 3) {
+    if (a.strided || a.g.qa >= 32) {
+      stencil_tile_ipf<BV>(a, (int64_t)blockIdx.x, smraw);
+      return;
+    }
+  }
   stencil_tile<Real, MODE, false, BV, IP>(a, (int64_t)blockIdx.x, smraw);
 }
 
@@ -2344,9 +2524,16 @@ __device__ __forceinline__ void batch_tile(const PassArgs& a, int64_t tile, unsi
       // long tails) are calls, so that their registers do not weigh on the
       // common narrow ones
       constexpr bool IP = MODE == MODE_STEP && sizeof(Real) == 4;
+      const bool ipf = IP && (a.strided || a.g.qa >= 32);
       switch (a.sB) {
-        case 2: stencil_tile<Real, MODE, true, 2, IP>(a, tk, smraw); break;
-        case 3: stencil_tile<Real, MODE, true, 3, IP>(a, tk, smraw); break;
+        case 2:
+          if (ipf) stencil_tile_ipf<2>(a, tk, smraw);
+          else stencil_tile<Real, MODE, true, 2, IP>(a, tk, smraw);
+          break;
+        case 3:
+          if (ipf) stencil_tile_ipf<3>(a, tk, smraw);
+          else stencil_tile<Real, MODE, true, 3, IP>(a, tk, smraw);
+          break;
         case 5: stencil_tile_call<Real, MODE, 5, IP>(a, tk, smraw); break;
         default: stencil_tile_call<Real, MODE, 8, IP>(a, tk, smraw); break;
       }
