@@ -2314,44 +2314,39 @@ __device__ __forceinline__ void stencil_tile_ipf(const PassArgs& a, int64_t tile
     if (!strided) {
       const int total = Wv * q;
       const int per = ((total + nwarp * 32 - 1) / (nwarp * 32)) * 32;
-      int e = warp * per + lane;
       const int e0 = warp * per, e1 = min(total, (warp + 1) * per);
       if (e0 >= e1) return;
       // the halos of every row this warp's range touches
       const int wa = e0 / q, wb = (e1 - 1) / q;
       for (int r = lane; r < (wb - wa + 1) * 2 * BV; r += 32) fill_halo(wa + r / (2 * BV), r % (2 * BV));
       __syncwarp();
-      if (e >= e1) return;
-      int w = e / q, i = e - w * q;
-      const float2* sp = sm + w * Ls + H + i;
-      float2* gp = pg + (s0 + w) * sstr + i;
-      uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
+      // lane l takes the elements e0 + l + 32 k < e1, row by row
       const uint64_t dphi = tu * twoA * 32u;
-      const uint64_t dphix = tu * (Xa - twoA * (uint64_t)q);
-      const int jsm = Ls - q;
-      const int64_t jg = sstr - q;
-      KinWalk kw;
-      if constexpr (POST) kw = walk_at(w, i, 32);
-      for (; e < e1; e += 32) {
-        const float2 cs = cis_fast(phi);
-        const float2 corr = ip_corr_f<BV>(sp, 1, T, cs.x, cs.y);
-        const float2 x0 = sp[0];
-        float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
-        if constexpr (POST) y = finish(y, kw);
-        __stcg(gp, y);
-        i += 32;
-        const bool cr = i >= q;
-        i = cr ? i - q : i;
-        sp += cr ? 32 + jsm : 32;
-        gp += cr ? 32 + jg : 32;
-        phi += cr ? dphi + dphix : dphi;
-        if constexpr (POST) {
-          if (cr) {
-            ++w;
-            if (e + 32 < e1) kw = walk_at(w, i, 32);
-          } else {
+      for (int w = wa; w <= wb; ++w) {
+        const int rs = max(e0, w * q), re = min(e1, (w + 1) * q);
+        // first element of this lane in [rs, re)
+        const int ef = rs + ((e0 + lane - rs) & 31);
+        if (ef >= re) continue;
+        int i = ef - w * q;
+        const int iend = re - w * q;
+        const float2* sp = sm + w * Ls + H + i;
+        float2* gp = pg + (s0 + w) * sstr + i;
+        uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
+        KinWalk kw;
+        if constexpr (POST) kw = walk_at(w, i, 32);
+        for (; i < iend; i += 32) {
+          const float2 cs = cis_fast(phi);
+          const float2 corr = ip_corr_f<BV>(sp, 1, T, cs.x, cs.y);
+          const float2 x0 = sp[0];
+          float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
+          if constexpr (POST) {
+            y = finish(y, kw);
             kw.next();
           }
+          __stcg(gp, y);
+          sp += 32;
+          gp += 32;
+          phi += dphi;
         }
       }
     } else {
