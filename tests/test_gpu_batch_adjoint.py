@@ -53,6 +53,27 @@ def test_batched_runner_parity(P, dtype, tol, scheme, form, monkeypatch):
         assert rel(b.get_dense(psi, i), ref) < tol * 4
 
 
+@pytest.mark.parametrize("scheme", ["strang", "lie", "strang_kp"])
+def test_batched_interaction_frame_long_call(P, scheme):
+    """Deterministic complex64 calls of the compact-only kernel run in the
+    interaction frame: one call of 300 steps (Lambda raised to the 300th power,
+    the exact K(T) once at the end) on Gaussian packets, then a second call of
+    1 step, against the oracle: rel-L2 <= 1e-4 and the norm within 1e-5."""
+    probs = uneven_batch()
+    b = P.Batch(probs, "c64")
+    psi = b.empty()
+    xs = [O.gaussian_packet(p, [0.0], 2.0, [1.0]) for p in probs]
+    for i, x in enumerate(xs):
+        b.set_dense(psi, i, x)
+    b.step(psi, 300, 1e-3, scheme)
+    b.step(psi, 1, 1e-3, scheme)
+    for i, p in enumerate(probs):
+        ref = O.step(p, xs[i], 1e-3, scheme, 301)
+        got = b.get_dense(psi, i)
+        assert rel(got, ref) < 1e-4, (i, p.name, rel(got, ref))
+        assert abs(np.linalg.norm(got) - 1) < 1e-5
+
+
 @pytest.mark.parametrize("form", ["compact", "fft"])
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
 @pytest.mark.parametrize("scheme", ["strang_stoch", "lie_stoch"])
