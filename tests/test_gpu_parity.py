@@ -799,6 +799,27 @@ def test_example3_three_index_parity(P, dtype, scheme):
         assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 5, (p.name, scheme, rel(ctx.to_dense(psi), ref))
 
 
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("scheme", ["lie", "strang", "strang_kp", "yoshida4", "strang_stoch"])
+def test_trilayer_parity(P, dtype, scheme):
+    """Three incommensurate 1D layers (workloads.trilayer_1d): layers 1 and 3
+    act on different lifted indices and commute, so their factors run together
+    on the (m, p) planes and layer 2 on the (n, p) planes; kinetic phases of
+    (b1 m + b2 n + b3 p)^2 / 2.  16 x 16 x 8 and 64 x 64 x 64 boxes (the
+    dedicated 64 x 64 passes), against the oracle."""
+    O.use_fft(True)
+    try:
+        for p in (W.trilayer_1d(8, 8, 4), W.trilayer_1d(32, 32, 32, 1.4, 0.9, 1.1, ecut=400.0)):
+            ctx = P.Context(p, dtype)
+            x = W.random_state((p.M2, p.M1), 34)
+            psi = ctx.from_dense(x)
+            ctx.step(psi, 3, 2e-3, scheme, seed=3, step0=1)
+            ref = O.step(p, x, 2e-3, scheme, 3, seed=3, step0=1)
+            assert rel(ctx.to_dense(psi), ref) < TOL1[dtype] * 5, (p.name, scheme, rel(ctx.to_dense(psi), ref))
+    finally:
+        O.use_fft(False)
+
+
 def test_example3_state_observables_and_adjoint(P):
     """Example 3: the packet initial state on the joint cutoff, observables
     (energy with both layer potentials on their (x, y) grids), the mass after

@@ -876,3 +876,70 @@ def test_example3_one_step_and_order_against_dense():
     assert abs(slope - 2) < 0.15, (slope, err)
     v = x.reshape(-1)
     assert abs(O.observables(p, x)["energy"] - np.vdot(v, H @ v).real) < 1e-10
+
+
+# ---------------------------------------------------------------- three layers
+def _trilayer_dense(n, a, L):
+    """Dense D, V1, V2, V3 of three 1D layers lifted to (m, n, p), built from
+    the layer periods and cosine amplitudes alone: k = sum_j (2 pi / L_j) i_j,
+    V_j = (a_j / 2)(S_j + S_j^-1) with S_j the periodic shift along index j
+    (the pseudo-spectral matrix of a_j cos(2 pi x / L_j), Eq. (3.6) with wrap);
+    phi[n + q2 p][m] flattened row major."""
+    q = [2 * x for x in n]
+    idx = lambda i, j, k: (j + q[1] * k) * q[0] + i
+    N = q[0] * q[1] * q[2]
+    rng = [np.arange(qq) - qq // 2 for qq in q]
+    b = [2 * np.pi / x for x in L]
+    kin = np.zeros(N)
+    V = [np.zeros((N, N)) for _ in range(3)]
+    for k in range(q[2]):
+        for j in range(q[1]):
+            for i in range(q[0]):
+                r = idx(i, j, k)
+                kin[r] = 0.5 * (b[0] * rng[0][i] + b[1] * rng[1][j] + b[2] * rng[2][k]) ** 2
+                for s_ in (1, -1):
+                    V[0][r, idx((i + s_) % q[0], j, k)] += a[0] / 2
+                    V[1][r, idx(i, (j + s_) % q[1], k)] += a[1] / 2
+                    V[2][r, idx(i, j, (k + s_) % q[2])] += a[2] / 2
+    return kin, V
+
+
+def test_trilayer_free_particle_exact_phase():
+    """V = 0 for three layers: every scheme is the exact phase with
+    k = b1 m + b2 n + b3 p (the trilayer mapping's wavevector)."""
+    n, L = (3, 2, 2), (1.0, W.GOLDEN, np.sqrt(2) / 2)
+    p = W.trilayer_1d(*n, 0.0, 0.0, 0.0, *L)
+    kin, _ = _trilayer_dense(n, (0, 0, 0), L)
+    x = W.random_state((p.M2, p.M1), 61)
+    for scheme in ("lie", "strang", "strang_kp", "yoshida4"):
+        got = O.step(p, x, 0.01, scheme, 3).reshape(-1)
+        np.testing.assert_allclose(got, np.exp(-1j * 0.03 * kin) * x.reshape(-1), atol=1e-12)
+
+
+def test_trilayer_one_step_and_order_against_dense():
+    """One Strang step of the trilayer mapping equals the dense product with
+    the commuting layers 1 and 3 as one factor, exp(-i s (V1 + V3)) =
+    exp(-i s V1) exp(-i s V3); Strang converges to the dense exponential of
+    H = D + V1 + V2 + V3 with slope 2; the energy is the dense quadratic form."""
+    n, a, L = (2, 2, 2), (1.3, 0.9, 0.7), (1.0, W.GOLDEN, np.sqrt(2) / 2)
+    p = W.trilayer_1d(*n, *a, *L)
+    kin, (V1, V2, V3) = _trilayer_dense(n, a, L)
+    D = np.diag(kin) / 9.0
+    p.B1 = p.B1 / 3.0
+    p.B2 = p.B2 / 3.0
+    E = lambda A, t: expm_herm(A, t)
+    np.testing.assert_allclose(E(V1, 0.3) @ E(V3, 0.3), E(V1 + V3, 0.3), atol=1e-12)
+    x = W.random_state((p.M2, p.M1), 62)
+    t = 0.05
+    U = (E(D, t / 8) @ E(V1 + V3, t / 2) @ E(D, t / 8)) @ (E(D, t / 4) @ E(V2, t) @ E(D, t / 4)) \
+        @ (E(D, t / 8) @ E(V1 + V3, t / 2) @ E(D, t / 8))
+    np.testing.assert_allclose(O.step(p, x, t, "strang", 1).reshape(-1), U @ x.reshape(-1), atol=1e-12)
+    H = D + V1 + V2 + V3
+    T = 0.4
+    exact = E(H, T) @ x.reshape(-1)
+    ns = [16, 32, 64]
+    err = [np.linalg.norm(O.step(p, x, T / k, "strang", k).reshape(-1) - exact) for k in ns]
+    slope = np.polyfit(np.log([T / k for k in ns]), np.log(err), 1)[0]
+    assert abs(slope - 2) < 0.15, (slope, err)
+    v = x.reshape(-1)
+    assert abs(O.observables(p, x)["energy"] - np.vdot(v, H @ v).real) < 1e-10

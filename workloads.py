@@ -205,6 +205,29 @@ def example3(n1: int = 8, n2: int = 8, n3: int = 4, s1: float = 1.0, s2: float =
                    name or f"example3-{2 * n1}x{2 * n2}x{2 * n3}", shared=1)
 
 
+def trilayer_1d(n1: int = 8, n2: int = 8, n3: int = 4, a1: float = 1.0, a2: float = 0.8, a3: float = 0.6,
+                L1: float = 1.0, L2: float = GOLDEN, L3: float = math.sqrt(2.0) / 2.0, ecut: float = 1e9,
+                name: str = "") -> Problem:
+    """Three incommensurate 1D layers, v_j = a_j cos(2 pi x / L_j), lifted to
+    three indices (m, n, p) with k = b1 m + b2 n + b3 p, b_j = 2 pi / L_j.
+    V1 acts along m, V2 along n, V3 along p, and V1, V3 act on different
+    indices, so exp(-i s (V1 + V3)) = exp(-i s V1) exp(-i s V3) exactly.  The
+    problem is stored as a shared-index problem: layer "1" on the (m, p) planes
+    carries V1 on the first harmonic component and V3 on the second, layer "2"
+    on the (n, p) planes carries V2; the wavevector is the 2-vector (k, 0), so
+    B1 = [[b1, 0], [0, 0]] and B2 = [[b2, b3], [0, 0]].  Boxes m in [-n1, n1),
+    n in [-n2, n2), p in [-n3, n3) (even lengths)."""
+    b1, b2, b3 = (2.0 * math.pi / L for L in (L1, L2, L3))
+    h1 = np.array([[1, 0], [-1, 0], [0, 1], [0, -1]], dtype=np.int64)
+    c1 = np.array([a1 / 2, a1 / 2, a3 / 2, a3 / 2], dtype=np.complex128)
+    h2 = np.array([[1, 0], [-1, 0]], dtype=np.int64)
+    c2 = np.array([a2 / 2, a2 / 2], dtype=np.complex128)
+    B1 = np.array([[b1, 0.0], [0.0, 0.0]])
+    B2 = np.array([[b2, b3], [0.0, 0.0]])
+    return Problem(2, B1, B2, (-n1, 0), (2 * n1, 1), (-n2, -n3), (2 * n2, 2 * n3), float(ecut), h1, c1, h2, c2,
+                   name or f"trilayer1d-{2 * n1}x{2 * n2}x{2 * n3}", shared=1)
+
+
 def cos_series_coeffs(theta: np.ndarray):
     """Coefficient list of sum_{h>=1} theta_h cos(2 pi h x / L)."""
     hs = list(range(1, len(theta) + 1))
