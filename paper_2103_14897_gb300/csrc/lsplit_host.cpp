@@ -1645,6 +1645,7 @@ int ls_density(ls_ctx* c, const void* psi, const double* x, int64_t nx, double* 
       d.e2 = e2.p;
       d.t = t.p;
       d.out = static_cast<double*>(ob.p) + 2 * j0;
+      d.simt = getenv_flag("LSPLIT_DENSITY_SIMT") ? 1 : 0;
       if (c->dtype == LS_C64) LS_CUDA(lsk::launch_density<float>(d, st));
       else LS_CUDA(lsk::launch_density<double>(d, st));
       LS_CUDA(cudaStreamSynchronize(st));

@@ -299,6 +299,7 @@ struct DensityArgs {
   const uint64_t* f2;                 // [2 nx]: the same with B2
   void *e1, *e2, *t;
   double* out;
+  int32_t simt;                       // complex64: 1 forces the CUDA-core contraction
 };
 template <typename Real> cudaError_t launch_density(const DensityArgs& d, cudaStream_t st);
 
