@@ -273,6 +273,25 @@ def test_step_parity_semi_implicit(P, dtype, scheme):
         c2.step(c2.empty(), 1, 1e-3, scheme)
 
 
+def test_density_tensor_core_matches_cuda_cores(P, monkeypatch):
+    """The complex64 contraction of ls_density in split TF32 on the tensor cores
+    against the FP32 CUDA-core form and the oracle: 1000 points (16 CTA rows of
+    64 with a ragged last one) on boxes of 65 x 65 and 513 x 25 (ragged m slabs
+    and n tiles); agreement within 1e-6 relative."""
+    x = np.linspace(-30.0, 30.0, 1000)
+    for p in [W.config_small_1d(), W.bilayer_1d(256, 12, 1.0, 1.4, ecut=1e9)]:
+        ctx = P.Context(p, "c64")
+        phi = W.random_state((p.M2, p.M1), 19)
+        psi = ctx.from_dense(phi)
+        monkeypatch.delenv("LSPLIT_DENSITY_SIMT", raising=False)
+        tc = ctx.density(psi, x)
+        monkeypatch.setenv("LSPLIT_DENSITY_SIMT", "1")
+        simt = ctx.density(psi, x)
+        ref = O.density_on_line(p, phi, x)
+        assert rel(tc, simt) < 1e-6, (p.name, rel(tc, simt))
+        assert rel(tc, ref) < 1e-6, (p.name, rel(tc, ref))
+
+
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
 def test_density_on_line_parity(P, dtype, tol):
     """psi(x) from the plane-wave expansion: exact fixed-point phase tables,
