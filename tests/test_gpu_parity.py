@@ -277,7 +277,10 @@ def test_density_tensor_core_matches_cuda_cores(P, monkeypatch):
     """The complex64 contraction of ls_density in split TF32 on the tensor cores
     against the FP32 CUDA-core form and the oracle: 1000 points (16 CTA rows of
     64 with a ragged last one) on boxes of 65 x 65 and 513 x 25 (ragged m slabs
-    and n tiles); agreement within 1e-6 relative."""
+    and n tiles).  Tolerance: the complex64 density gate, 1e-5; the dropped
+    lo*lo term is 2^-22 relative per product, and a random full-spectrum
+    state's sums cancel (|psi(x)| is far below the sum of the term moduli),
+    which raises the relative error of the result to about 1e-6."""
     x = np.linspace(-30.0, 30.0, 1000)
     for p in [W.config_small_1d(), W.bilayer_1d(256, 12, 1.0, 1.4, ecut=1e9)]:
         ctx = P.Context(p, "c64")
@@ -288,8 +291,8 @@ def test_density_tensor_core_matches_cuda_cores(P, monkeypatch):
         monkeypatch.setenv("LSPLIT_DENSITY_SIMT", "1")
         simt = ctx.density(psi, x)
         ref = O.density_on_line(p, phi, x)
-        assert rel(tc, simt) < 1e-6, (p.name, rel(tc, simt))
-        assert rel(tc, ref) < 1e-6, (p.name, rel(tc, ref))
+        assert rel(tc, simt) < 1e-5, (p.name, rel(tc, simt))
+        assert rel(tc, ref) < 1e-5, (p.name, rel(tc, ref))
 
 
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-5), ("c128", 1e-11)])
