@@ -49,6 +49,12 @@ template <typename C> __device__ __forceinline__ C cmulconj(C a, C b) {  // a * 
 }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// complex64: one paired FP32 operation each, rounded as the scalar forms
+// (a - b is fma(b, -1, a), a single rounding of the exact difference)
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
 
 // Per-slice metadata of the tile a CTA works on (slice index, kinetic
