@@ -2054,125 +2054,10 @@ __device__ __forceinline__ void stencil_tile(const PassArgs& a, int64_t tile, un
         }
       }
     };
-    const bool post = a.units_post != 0;
-    if constexpr (sizeof(Real) == 4) {
-      // complex64: tap factors as broadcast pairs; rows as one flat range per
-      // warp (balanced across warps, a row change is a predicated jump of the
-      // pointers and the phase), columns one per thread.  The call's last pass
-      // (POST) also applies Lambda K(T) per element with the exact phase.
-      IpTaps<BV> T;
-#pragma unroll
-      for (int d = 1; d <= BV; ++d) {
-        const C t1 = tf[BV + d], t2 = tf[BV - d];
-        T.t1x[d - 1] = make_float2(t1.x, t1.x);
-        T.t1y[d - 1] = make_float2(t1.y, t1.y);
-        T.nt1y[d - 1] = make_float2(-t1.y, -t1.y);
-        T.t2x[d - 1] = make_float2(t2.x, t2.x);
-        T.nt2x[d - 1] = make_float2(-t2.x, -t2.x);
-        T.t2y[d - 1] = make_float2(t2.y, t2.y);
-      }
-      const uint64_t twoA = 2 * g.A_aa, Xa = g.X_aa, A = g.A_aa, Ca = g.C_aa;
-      const int lo = g.lo_a;
-      const int64_t s0 = tile * (int64_t)W, sstr = g.slice_stride, ea = g.ea;
-      const int64_t olo = g.olo_a;
-      const int Wv = (int)min((int64_t)W, g.nslices - s0);
-      const uint64_t negT = (uint64_t)0 - (uint64_t)a.units_post;
-      float2* pg = reinterpret_cast<float2*>(psi);
-      const float2* smf = reinterpret_cast<const float2*>(sm);
-      // the exact Lambda K(T) of the last pass, on a walk of kappa along the element's line
-      auto finish = [&](float2 y, const KinWalk& kw) {
-        Phase<float> ph = phase_of<float>(kw.q);
-        ph.half_e += (float)a.lam_def;
-        return apply_phase<float>(y, ph);
-      };
-      auto walk_at = [&](int w, int i, int step) {
-        KinWalk kw;
-        const uint64_t ua = (uint64_t)(s0 + w + olo);
-        kw.init(A, Xa * ua, Ca * (ua * ua), lo + i, step);
-        kw.scale(negT);
-        kw.q += a.lam_turns;
-        return kw;
-      };
-      auto fast = [&](auto post_c) {
-        constexpr bool POST = decltype(post_c)::value;
-        if (!strided) {
-          const int total = Wv * q;
-          const int per = ((total + nwarp * 32 - 1) / (nwarp * 32)) * 32;
-          int e = warp * per + lane;
-          const int eend = min(total, (warp + 1) * per);
-          if (e >= eend) return;
-          int w = e / q, i = e - w * q;
-          const float2* sp = smf + w * Ls + H + i;
-          float2* gp = pg + (s0 + w) * sstr + i;
-          uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
-          const uint64_t dphi = tu * twoA * 32u;
-          const uint64_t dphix = tu * (Xa - twoA * (uint64_t)q);
-          const int jsm = Ls - q;
-          const int64_t jg = sstr - q;
-          KinWalk kw;
-          if constexpr (POST) kw = walk_at(w, i, 32);
-          for (; e < eend; e += 32) {
-            const float2 cs = cis_fast(phi);
-            const float2 corr = ip_corr_f<BV>(sp, 1, T, cs.x, cs.y);
-            const float2 x0 = sp[0];
-            float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
-            if constexpr (POST) y = finish(y, kw);
-            __stcg(gp, y);
-            i += 32;
-            const bool cr = i >= q;
-            i = cr ? i - q : i;
-            sp += cr ? 32 + jsm : 32;
-            gp += cr ? 32 + jg : 32;
-            phi += cr ? dphi + dphix : dphi;
-            if constexpr (POST) {
-              if (cr) {
-                ++w;
-                if (e + 32 < eend) kw = walk_at(w, i, 32);
-              } else {
-                kw.next();
-              }
-            }
-          }
-        } else {
-          const int w = tid & (W - 1);
-          if (w >= Wv) return;
-          int i = tid >> wsh;
-          const float2* sp = smf + (i + H) * W + w;
-          float2* gp = pg + (s0 + w) + (int64_t)i * ea;
-          uint64_t phi = tu * (twoA * (uint64_t)(int64_t)(lo + i) + Xa * (uint64_t)(s0 + w + olo));
-          const uint64_t dphi = tu * twoA * (uint64_t)eid;
-          const int dsp = eid * W;
-          const int64_t dg = (int64_t)eid * ea;
-          KinWalk kw;
-          if constexpr (POST) kw = walk_at(w, i, eid);
-          for (; i < q; i += eid) {
-            const float2 cs = cis_fast(phi);
-            const float2 corr = ip_corr_f<BV>(sp, W, T, cs.x, cs.y);
-            const float2 x0 = sp[0];
-            float2 y = make_float2(x0.x + corr.x, x0.y + corr.y);
-            if constexpr (POST) {
-              y = finish(y, kw);
-              kw.next();
-            }
-            __stcg(gp, y);
-            sp += dsp;
-            gp += dg;
-            phi += dphi;
-          }
-        }
-      };
-      if (!strided && q < 32) {
-        if (post) sweep(std::integral_constant<bool, true>());
-        else sweep(std::integral_constant<bool, false>());
-      } else if (post) {
-        fast(std::integral_constant<bool, true>());
-      } else {
-        fast(std::integral_constant<bool, false>());
-      }
-    } else {
-      if (post) sweep(std::integral_constant<bool, true>());
-      else sweep(std::integral_constant<bool, false>());
-    }
+    // (complex64 tiles of rows of length >= 32 or of columns run
+    // stencil_tile_ipf instead; this general sweep serves the rest)
+    if (a.units_post != 0) sweep(std::integral_constant<bool, true>());
+    else sweep(std::integral_constant<bool, false>());
   } else
   // ---- y = x + sum_d c'_d x_{i-d}, post-phase, store
   {
@@ -2395,7 +2280,7 @@ template <typename Real, int MODE, int BV, bool IP = false>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(Real) == 4 ? 3 : 2)
 pass_stencil_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  if constexpr (IP && sizeof(Real) == 4 && BV <= 3) {
+  if constexpr (IP && sizeof(Real) == 4) {
     if (a.strided || a.g.qa >= 32) {
       stencil_tile_ipf<BV>(a, (int64_t)blockIdx.x, smraw);
       return;
@@ -2468,6 +2353,12 @@ __device__ __noinline__ void batch_stencil_tile_n(const PassArgs& a, int64_t til
 // Compact-kernel tile of a batched work item (sB > 0); false: not this form.
 template <typename Real, int MODE, int BV, bool IP>
 __device__ __noinline__ void stencil_tile_call(const PassArgs& a, int64_t tile, unsigned char* smraw) {
+  if constexpr (IP && sizeof(Real) == 4) {
+    if (a.strided || a.g.qa >= 32) {
+      stencil_tile_ipf<BV>(a, tile, smraw);
+      return;
+    }
+  }
   stencil_tile<Real, MODE, true, BV, IP>(a, tile, smraw);
 }
 
