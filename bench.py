@@ -232,12 +232,22 @@ def profile_case(args):
     batch : 64 uneven instances of the batched workload, one persistent launch;
     batch256: the whole 256-instance batched workload (the headline);
     bench : the 2049 x 2049 bench workload itself (33.8 MB, L2-resident like
-            the timed bench), one ls_step call of --steps steps."""
+            the timed bench), one ls_step call of --steps steps;
+    density: psi at 4096 points of a line on the 2049 x 2049 box (the
+            tensor-core contraction of ls_density)."""
     import torch
     import __graft_entry__ as G
     G.build()
     import paper_2103_14897_gb300 as P
     kind = args.profile_case
+    if kind == "density":
+        p = W.config_scale_1d()
+        ctx = P.Context(p, "c64")
+        psi = ctx.empty()
+        ctx.init_gaussian(psi, [0.0], 2.0, [1.0])
+        v = ctx.density(psi, np.linspace(-50.0, 50.0, 4096))
+        print(json.dumps({"workload": "density 4096 points on bilayer1d-2049x2049", "max_abs": float(np.abs(v).max())}))
+        return
     if kind in ("batch", "batch256"):
         probs = W.batch_1d(count=64 if kind == "batch" else 256, seed=4)
         b = P.Batch(probs, "c64")
@@ -601,7 +611,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--suite", action="store_true", help="throughput lines of the secondary workloads")
-    ap.add_argument("--profile-case", choices=["1d", "2d", "batch", "batch256", "bench"], default=None,
+    ap.add_argument("--profile-case", choices=["1d", "2d", "batch", "batch256", "bench", "density"], default=None,
                     help="run an ncu target (array larger than L2) instead of the bench workload")
     args = ap.parse_args()
     if args.warmup < 3:
